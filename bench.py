@@ -1,0 +1,366 @@
+"""Benchmark: c-LSQR + Tikhonov/GCV through the C ABI on synthetic deblurring.
+
+A step is one whole solve: itermax c-LSQR iterations (Algorithm 6) on one
+observed tensor, then GCV on the projected bidiagonal and X_reg = V_k (*) y
+(Algorithm 5's projection), all on the GPU, replayed as one CUDA graph.
+
+Default workload: two-sided A *c X *c B, 256 x 256 x 3, Gaussian blurs
+(sigma 3 and 2, half-band 8), noise 1e-3, 50 iterations.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tcprod|reference]
+                  [--workload two_sided_256|colour_64|video_512]
+
+Prints one JSON line (rank 0). Under torchrun each rank solves its own
+replica (independent problems, no collective on the data path): "weak"
+scaling, value = iterations/s summed over ranks (all ranks' iterations over
+the slowest rank's time).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "LSQR-c iters/s & solves/s at matched rel. error (BF16/TF32 vs FP32); % roofline"
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flop x clock (GB300 unit counts).
+FP32_LANES = 152 * 128
+
+WORKLOADS = {
+    "two_sided_256": dict(kind="two_sided", n=256, n3=3, iters=50, seed=1),
+    "colour_64": dict(kind="colour", n=64, n3=3, iters=30, seed=0),
+    "video_512": dict(kind="video", n=512, n3=64, iters=50, seed=2),
+}
+
+
+def make_problem(name):
+    from paper_2103_11847_gb300 import inputs
+    w = WORKLOADS[name]
+    if w["kind"] == "two_sided":
+        return inputs.two_sided_deblur(n=w["n"], n3=w["n3"], seed=w["seed"])
+    if w["kind"] == "colour":
+        return inputs.colour_deblur(n=w["n"], seed=w["seed"])
+    return inputs.video_deblur(n=w["n"], frames=w["n3"], seed=w["seed"])
+
+
+def product_flops(n1, n2, s, n3, two_sided):
+    """Algorithmic flops of one c-product: the n3 slice GEMMs (the mode-3
+    transforms are O(n3 log n3) per tube with a fast DCT and are not counted)."""
+    f = 2.0 * n1 * n2 * s * n3
+    if two_sided:
+        f += 2.0 * n1 * s * s * n3
+    return f
+
+
+def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True):
+    """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu)."""
+    per_product = (2 if two_sided else 1) if fused else (4 if two_sided else 3)
+    init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
+    per_iter = 2 * per_product + 2
+    tail = (3 if keep_basis else 0) + 1
+    return init + iters * per_iter + tail
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 6:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4)
+                          if r[2 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": FALLBACK_HBM_GBS, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------- CPU oracle ----
+
+def cpu_worker(workload, budget_s):
+    """Time the FP64 oracle's c-LSQR on this host (run in a child process)."""
+    from oracle import cproduct as cp
+    from oracle import krylov as kr
+    from paper_2103_11847_gb300 import inputs
+    w = make_problem(workload)
+    A = w["A"].astype(np.float32).astype(np.float64)
+    B = w["B"].astype(np.float32).astype(np.float64) if w["B"] is not None else None
+    op = lambda X: cp.cprod(A, X, B)
+    adj = lambda Y: cp.cprod_adjoint(A, Y, B)
+    C = inputs.scale_noise(op(w["X_true"]), w["G"], w["nu"]).astype(np.float32).astype(np.float64)
+    iters = WORKLOADS[workload]["iters"]
+    sample = max(2, min(iters, 10))
+    kr.lsqr(op, adj, C, itermax=2)  # warm-up
+    done, t0 = 0, time.perf_counter()
+    while True:
+        kr.lsqr(op, adj, C, itermax=sample)
+        done += sample
+        el = time.perf_counter() - t0
+        if el > budget_s:
+            break
+    print(json.dumps({"iters": done, "seconds": el, "sample_iters": sample}))
+
+
+def cpu_baseline(workload, budget_s=12.0):
+    cores = len(os.sched_getaffinity(0))
+    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
+               MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", workload,
+                        "--cpu-budget", str(budget_s)], capture_output=True, text=True, env=env,
+                       timeout=600)
+    out = json.loads(r.stdout.strip().splitlines()[-1])
+    value = out["iters"] / out["seconds"]
+    return {"value": value, "unit": "LSQR iterations/s", "cores": cores, "kind": "oracle",
+            "sample": (f"{out['iters']} c-LSQR iterations of the {workload} workload in runs of "
+                       f"{out['sample_iters']} (FP64 NumPy oracle, {out['seconds']:.1f} s)")}
+
+
+# ---------------------------------------------------------------- GPU arm ----
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, local, world
+
+
+def run_gpu(args):
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    wl = WORKLOADS[args.workload]
+    w = make_problem(args.workload)
+    n3, n1, n2 = w["A"].shape
+    two = w["B"] is not None
+    s = w["B"].shape[1] if two else w["X_true"].shape[2]
+    iters = wl["iters"]
+    dev = torch.device("cuda", local)
+    A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+    B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
+    Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
+    G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
+    plan = tcprod.Plan(A, B, s=s)
+    # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
+    Cc = plan.cprod(Xt)
+    C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
+    X = torch.empty(plan.xshape(), device=dev)
+    Xr = torch.empty(plan.xshape(), device=dev)
+    info = tcprod.new_info()
+    st = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+    def solve():
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+
+    for _ in range(max(args.warmup, 3)):
+        solve()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    clocks = ClockSampler(local)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(args.steps):
+        flush.zero_()  # evict the L2 between timed steps (outside the events)
+        starts[i].record(st)
+        solve()
+        ends[i].record(st)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+
+    # dominant kernels: the slice GEMMs of one product, timed alone on the stream
+    fl = product_flops(n1, n2, s, n3, two)
+    reps = 200
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    tmpY = torch.empty(plan.yshape(), device=dev)
+    for _ in range(10):
+        tcprod.tc_cprod(plan.handle, Xr, tmpY)
+    e0.record(st)
+    for _ in range(reps):
+        tcprod.tc_cprod(plan.handle, Xr, tmpY)
+    e1.record(st)
+    torch.cuda.synchronize()
+    prod_ms = e0.elapsed_time(e1) / reps
+    clk = clocks.stop()
+
+    # end to end through the public API: pinned host C in, X_reg out, every step
+    C_host = C.cpu().pin_memory()
+    Xr_host = torch.empty(plan.xshape(), dtype=torch.float32).pin_memory()
+    info_host = torch.empty(info.numel(), dtype=torch.uint8).pin_memory()
+    Cdev = torch.empty_like(C)
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    ee0.record(st)
+    for _ in range(e2e_steps):
+        Cdev.copy_(C_host, non_blocking=True)
+        tcprod.tc_lsqr_c(plan.handle, Cdev, X, Xr, iters, 0.0, None, None, info)
+        Xr_host.copy_(Xr, non_blocking=True)
+        info_host.copy_(info, non_blocking=True)
+    ee1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
+    inf = tcprod.read_info(info)
+
+    t_max = total_ms
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    value = world * args.steps * iters / (t_max / 1000.0)
+    if rank == 0:
+        peaks, src = load_peaks()
+        sm_max = peaks.get("sm_max_mhz", 2070.0)
+        fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12
+        achieved = fl / (prod_ms * 1e-3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
+            "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded image + Gaussian blur + 1e-3 noise)",
+            "config": {"workload": f"{args.workload}: c-LSQR {iters} it + Tikhonov/GCV, "
+                                   f"A {n1}x{n2}x{n3}" + (f", B {s}x{s}x{n3}" if two else "")
+                                   + f", X {n2}x{s}x{n3}",
+                       "precision": "fp32", "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": {"kernel": "k_slice_gemm (all GEMM stages of one c-product)",
+                         "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                        f"({src} max clock)",
+                         "launch_ms": prod_ms},
+            "e2e": {"value": iters / (e2e_ms / 1000.0) * world, "unit": "LSQR iterations/s",
+                    "h2d_bytes_per_step": int(C.numel() * 4),
+                    "d2h_bytes_per_step": int(Xr.numel() * 4 + info.numel())},
+            "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4),
+            "clocks": clk,
+            "solve": {"iters": inf["iters"], "status": inf["status"], "lambda": inf["lam"],
+                      "resid": inf["resid"],
+                      "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+                      "rel_err_lsqr": float((X - Xt).norm() / Xt.norm())},
+        }
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args.workload)
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    wl = WORKLOADS[args.workload]
+    cb_steps = []
+    cores = len(os.sched_getaffinity(0))
+    budget = 4.0  # seconds of oracle work per step (the worker warms up first)
+    t0 = time.perf_counter()
+    total_iters = 0
+    for _ in range(args.steps):
+        cb = cpu_baseline(args.workload, budget_s=budget)
+        cb_steps.append(cb)
+        total_iters += 1
+    el = time.perf_counter() - t0
+    value = statistics.median(c["value"] for c in cb_steps)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": el * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded image + Gaussian blur)",
+        "config": {"workload": f"{args.workload}: c-LSQR {wl['iters']} it (FP64 NumPy oracle "
+                               "on the host cores; each step a bounded sample)"},
+        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
+                         "unit": "LSQR iterations/s", "sample": cb_steps[0]["sample"]},
+        "e2e": {"value": value, "unit": "LSQR iterations/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tcprod", choices=["tcprod", "reference"])
+    ap.add_argument("--workload", default="two_sided_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", default=None)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker, args.cpu_budget)
+        return
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

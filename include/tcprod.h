@@ -1,0 +1,163 @@
+/*
+ * tcprod.h -- C ABI of the GB300 (sm_103a) cosine-product Krylov library.
+ *
+ * The library solves min_X || M(X) - C ||_F with M(X) = A *c X or
+ * M(X) = A *c X *c B (eq. (eq2), §1 of El Ichi, El Guide, Jbilou,
+ * "Discrete cosine transform LSQR and GMRES methods for multidimensional
+ * ill-posed problems", arXiv 2103.11847), by the tensor Golub-Kahan, LSQR and
+ * GMRES methods of §3, regularised by Tikhonov with the GCV choice of lambda.
+ *
+ * Conventions for every call below.
+ *  - Tensors are FP32 in device memory, owned by the caller, laid out
+ *    slice-major: a tensor of size rows x cols x n3 is n3 consecutive frontal
+ *    slices, each rows x cols row-major (element (i, j, k) at k*rows*cols +
+ *    i*cols + j).
+ *  - Sizes: A is n1 x n2 x n3, X is n2 x s x n3, C and Y are n1 x s x n3, B is
+ *    s x s x n3 (two-sided only).
+ *  - The c-product is Definition 2.1 (ten(mat(A) mat(X))), computed through
+ *    the mode-3 transform M = W^{-1} C_{n3} (I + Z) of Remark 2.1: A~ = A x_3 M
+ *    is formed once per plan and kept resident; each product transforms the
+ *    operand, multiplies the n3 frontal slices and transforms back.
+ *  - "Adjoint" means the adjoint for the inner product of Definition 2.2,
+ *    X -> M^T [ A~_k^T (M^{-T} Y)_k (B~_k^T) ]; this is the A^T *c that
+ *    Algorithms 4 and 6 use.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t; NULL is the
+ *    legacy default stream) unless it says otherwise. Arguments are checked on
+ *    the host before anything is launched.
+ *  - Return value: TC_OK (0) or a negative tc_status. Device-side outcomes of a
+ *    solve (convergence, breakdown, non-finite values) are reported in the
+ *    tc_solve_info the solve writes to device memory.
+ *  - A plan may be used from one host thread at a time; calls on one plan
+ *    that overlap on the GPU (different streams) race on its workspaces.
+ */
+#ifndef TCPROD_H
+#define TCPROD_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ABI-identical to cudaStream_t. */
+typedef struct CUstream_st* tc_stream_t;
+
+typedef struct tc_plan tc_plan;
+
+typedef enum {
+  TC_OK = 0,
+  TC_EINVAL = -1,      /* bad argument (null pointer, size, misaligned, ...) */
+  TC_ECUDA = -2,       /* a CUDA runtime call failed (see tc_last_error) */
+  TC_EBREAKDOWN = -3,  /* a Krylov process broke down (alpha, beta or h = 0) */
+  TC_ENONFINITE = -4,  /* a norm or inner product was NaN or Inf */
+  TC_ETIMEOUT = -5,    /* a bounded device wait gave up */
+  TC_ENOMEM = -6,      /* device allocation failed */
+  TC_EUNSUPPORTED = -7 /* valid request this build does not implement */
+} tc_status;
+
+typedef enum {
+  TC_FP32 = 0, /* slice GEMMs in FP32 (FFMA)                         */
+  TC_TF32 = 1, /* slice GEMMs on tensor cores, TF32 in, FP32 accumulate */
+  TC_BF16 = 2  /* slice GEMMs on tensor cores, BF16 in, FP32 accumulate */
+} tc_precision;
+
+typedef enum {
+  TC_GCV_PAPER = 0, /* eq. (gcv2) as printed (square-matrix form)           */
+  TC_GCV_FULL = 1   /* GCV of the (k+1) x k projected least-squares problem */
+} tc_gcv_variant;
+
+typedef struct {
+  int precision;   /* tc_precision */
+  int gcv_variant; /* tc_gcv_variant */
+  int use_graphs;  /* nonzero: solves replay a captured CUDA graph */
+  int reserved[5]; /* must be zero */
+} tc_opts;
+
+/* Outcome of a solve, written to DEVICE memory by the solve (copy it back
+ * after the stream synchronises). */
+typedef struct {
+  int iters;     /* LSQR iterations / GMRES Arnoldi steps / GK steps done */
+  int status;    /* 0 ran to itermax, 1 converged (residual < tol),
+                    TC_EBREAKDOWN or TC_ENONFINITE */
+  int cycles;    /* GMRES restart cycles */
+  int pad;
+  double resid;  /* LSQR: |phibar_{k+1}| = ||C - M(X_k)||_F (§3.3);
+                    GMRES: ||C - M(X)||_F at the last check */
+  double lambda; /* Tikhonov parameter used (NaN if none) */
+  double gcv;    /* GCV value at lambda (NaN if none) */
+  double beta1;  /* ||C||_F */
+} tc_solve_info;
+
+/* Library version string and the message of the last TC_ECUDA on this thread. */
+const char* tc_version(void);
+const char* tc_last_error(void);
+
+/* Plan: validates sizes, copies nothing back, forms A~ = A x_3 M (and B~)
+ * once with its slice transposes, and keeps them with its workspaces in
+ * device memory it allocates (freed by tc_plan_destroy).
+ *   A: device, n1 x n2 x n3.   B: device s x s x n3, or NULL for A *c X.
+ *   opts: may be NULL (FP32, paper GCV, graphs on).
+ * Sizes must be >= 1; n3 <= 256. Synchronises `stream` before returning.
+ * Source: Remark 2.1 and eqs. (dft9), (dft8), §2.2. */
+int tc_plan_create(tc_plan** plan, int n1, int n2, int s, int n3,
+                   const float* A, const float* B, const tc_opts* opts,
+                   tc_stream_t stream);
+int tc_plan_destroy(tc_plan* plan);
+
+/* Y = A *c X [*c B] (Definition 2.1 via Algorithm 1 with M).
+ *   X: device n2 x s x n3 (read).  Y: device n1 x s x n3 (written).
+ * X and Y must not overlap. */
+int tc_cprod(tc_plan* plan, const float* X, float* Y, tc_stream_t stream);
+
+/* X = adjoint(Y) (the A^T *c of Algorithms 4 and 6).
+ *   Y: device n1 x s x n3 (read).  X: device n2 x s x n3 (written). */
+int tc_cprod_adjoint(tc_plan* plan, const float* Y, float* X, tc_stream_t stream);
+
+/* Tensor Golub-Kahan bidiagonalisation, Algorithm 4 (§3.2), one step per call.
+ *   U: device, (mmax+1) consecutive tensors n1 x s x n3 (U_1 .. U_{mmax+1}).
+ *   V: device, (mmax+1) consecutive tensors n2 x s x n3 (V_1 .. V_{mmax+1}).
+ *   alpha, beta: device double[mmax+1]; alpha[j-1] = alpha_j, beta[j-1] = beta_j.
+ * tc_gkb_init writes beta_1 = ||C||_F, U_1 = C/beta_1, alpha_1, V_1.
+ * tc_gkb_step(j), 1 <= j <= mmax, reads U_j, V_j, alpha_j, beta_j and writes
+ * U_{j+1}, beta_{j+1}, V_{j+1}, alpha_{j+1}. A zero beta or alpha (breakdown)
+ * leaves the new basis tensor zero; the caller sees it in beta/alpha. */
+int tc_gkb_init(tc_plan* plan, const float* C, float* U, float* V,
+                double* alpha, double* beta, int mmax, tc_stream_t stream);
+int tc_gkb_step(tc_plan* plan, int j, float* U, float* V, double* alpha,
+                double* beta, int mmax, tc_stream_t stream);
+
+/* DC-LSQR, Algorithm 6 (§3.3), from X_0 = 0, then optionally Tikhonov/GCV on
+ * the projected bidiagonal C~_k (§3.2, eqs. (normeq2), (gcv2), (xmlsqr)).
+ *   C: device n1 x s x n3.   X: device n2 x s x n3, the LSQR iterate X_k.
+ *   X_reg: device n2 x s x n3 or NULL. If given, the basis V_1..V_k is kept and
+ *     X_reg = V_k (*) y_lambda with lambda = `lambda` if it is >= 0, else the
+ *     GCV minimiser (opts.gcv_variant).
+ *   itermax: 1 .. 4096.  tol: stop when |phibar_{j+1}| < tol (0: never).
+ *   phibar_hist: device double[itermax] or NULL: |phibar_{j+1}| per iteration.
+ *   info: device tc_solve_info (required). */
+int tc_lsqr_c(tc_plan* plan, const float* C, float* X, float* X_reg,
+              int itermax, double tol, double lambda, double* phibar_hist,
+              tc_solve_info* info, tc_stream_t stream);
+
+/* Restarted DC-GMRES(m) with Tikhonov/GCV, Algorithms 2 and 3 (§3.1).
+ * Needs a square operator: n1 == n2 (the input and output shapes agree).
+ *   C: device n1 x s x n3.  X0: device or NULL (zero).  X: device, the result.
+ *   m: restart length 1 .. 256.  itermax: total Arnoldi steps.
+ *   lambda >= 0 fixes lambda; < 0 chooses it by GCV each cycle.
+ *   info: device tc_solve_info (required). */
+int tc_gmres_c(tc_plan* plan, const float* C, const float* X0, float* X,
+               int m, int itermax, double tol, double lambda,
+               tc_solve_info* info, tc_stream_t stream);
+
+/* Tikhonov solution of a projected problem with GCV (§3.1, eqs. (leastsq),
+ * (tikho2), (gcv2)): y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
+ *   H: device double, (k+1) x k row-major (Hessenberg or lower bidiagonal).
+ *   k: 1 .. 256.   beta: device double scalar.
+ *   lambda_in >= 0 fixes lambda; < 0 minimises GCV (variant tc_gcv_variant).
+ *   lambda_out: device double.  y: device double[k].  gcv_out: device or NULL. */
+int tc_tikhonov_gcv(const double* H, int k, const double* beta, int variant,
+                    double lambda_in, double* lambda_out, double* y,
+                    double* gcv_out, tc_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TCPROD_H */

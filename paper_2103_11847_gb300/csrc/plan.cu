@@ -1,0 +1,288 @@
+// Plans and the two products of the library (Algorithm 1 with the transform M
+// of Remark 2.1, and its adjoint), plus the error strings of the C ABI.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "tc_device.cuh"
+
+namespace {
+thread_local char g_err[512] = "";
+
+// Orthonormal DCT-II matrix C_n (eq. (dft1), §2.1), 0-based indices.
+void dct2(int n, std::vector<double>& C) {
+  const double pi = 3.14159265358979323846;
+  C.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      C[(size_t)i * n + j] = std::sqrt((i == 0 ? 1.0 : 2.0) / n) *
+                             std::cos(i * (2.0 * j + 1.0) * pi / (2.0 * n));
+}
+
+// M = W^{-1} C (I + Z) and its inverse M^{-1} = (I + Z)^{-1} C^T W in FP64
+// (Remark 2.1). (I + Z)^{-1} is upper triangular with entries (-1)^{c-r}, so
+// the inverse is formed in closed form rather than by a factorisation.
+void transform_pair(int n, std::vector<double>& M, std::vector<double>& Mi) {
+  std::vector<double> C;
+  dct2(n, C);
+  M.assign((size_t)n * n, 0.0);
+  Mi.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) {
+    const double w = C[(size_t)i * n];
+    for (int j = 0; j < n; ++j) {
+      const double cij = C[(size_t)i * n + j] + (j > 0 ? C[(size_t)i * n + j - 1] : 0.0);
+      M[(size_t)i * n + j] = cij / w;
+    }
+  }
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      double s = 0.0;
+      for (int r = i; r < n; ++r) s += (((r - i) & 1) ? -1.0 : 1.0) * C[(size_t)j * n + r];
+      Mi[(size_t)i * n + j] = s * C[(size_t)j * n];
+    }
+}
+
+__global__ void k_transpose_slices(const float* __restrict__ in, float* out, int R, int Cc) {
+  __shared__ float t[32][33];
+  const size_t so = (size_t)blockIdx.z * R * Cc;
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int r = r0 + i, c = c0 + threadIdx.x;
+    if (r < R && c < Cc) t[i][threadIdx.x] = in[so + (size_t)r * Cc + c];
+  }
+  __syncthreads();
+  for (int i = threadIdx.y; i < 32; i += 8) {
+    const int c = c0 + i, r = r0 + threadIdx.x;
+    if (r < R && c < Cc) out[so + (size_t)c * R + r] = t[threadIdx.x][i];
+  }
+}
+
+int transpose_slices(const float* in, float* out, int R, int Cc, int n3, cudaStream_t st) {
+  dim3 grid((Cc + 31) / 32, (R + 31) / 32, n3);
+  k_transpose_slices<<<grid, dim3(32, 8), 0, st>>>(in, out, R, Cc);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+template <class T>
+int dalloc(T** p, size_t n) {
+  if (n == 0) n = 1;
+  cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
+  if (e != cudaSuccess) {
+    tc_set_error("cudaMalloc", e);
+    return TC_ENOMEM;
+  }
+  return TC_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+bool fused(const tc_plan* p) { return p->n3 <= TC_MAX_FUSED; }
+}  // namespace
+
+void tc_set_error(const char* what, cudaError_t e) {
+  std::snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
+}
+
+extern "C" const char* tc_last_error(void) { return g_err; }
+extern "C" const char* tc_version(void) { return "tcprod 0.1 (sm_103a)"; }
+
+Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status) {
+  Red r;
+  r.out = out;
+  r.sqrt_out = sqrt_out;
+  r.other = other;
+  r.partials = p->scratch.partials;
+  r.ticket = p->scratch.tickets;
+  r.status = status;
+  return r;
+}
+
+// Y = A *c X [*c B] with the epilogue `ep` on the last stage.
+int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st) {
+  const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  Epi mid;
+  mid.skip = ep.skip;
+  if (fused(p)) {
+    if (!p->two_sided)
+      return launch_slice_gemm(p->Ah, X, Y, n1, s, n2, n3, p->hM, p->hMinv, ep, st);
+    TC_TRY(launch_slice_gemm(p->Ah, X, p->tmp1, n1, s, n2, n3, p->hM, nullptr, mid, st));
+    return launch_slice_gemm(p->tmp1, p->Bh, Y, n1, s, s, n3, nullptr, p->hMinv, ep, st);
+  }
+  TC_TRY(launch_mode3(X, p->tmp1, p->dM, n3, (size_t)n2 * s, mid, st));
+  TC_TRY(launch_slice_gemm(p->Ah, p->tmp1, p->tmp2, n1, s, n2, n3, nullptr, nullptr, mid, st));
+  const float* src = p->tmp2;
+  if (p->two_sided) {
+    TC_TRY(launch_slice_gemm(p->tmp2, p->Bh, p->tmp1, n1, s, s, n3, nullptr, nullptr, mid, st));
+    src = p->tmp1;
+  }
+  return launch_mode3(src, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
+}
+
+// X = M^T [ A~_k^T (M^{-T} Y)_k (B~_k^T) ] with the epilogue `ep` on the last stage.
+int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st) {
+  const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  Epi mid;
+  mid.skip = ep.skip;
+  if (fused(p)) {
+    if (!p->two_sided)
+      return launch_slice_gemm(p->AhT, Y, X, n2, s, n1, n3, p->hMinvT, p->hMT, ep, st);
+    TC_TRY(launch_slice_gemm(p->AhT, Y, p->tmp1, n2, s, n1, n3, p->hMinvT, nullptr, mid, st));
+    return launch_slice_gemm(p->tmp1, p->BhT, X, n2, s, s, n3, nullptr, p->hMT, ep, st);
+  }
+  TC_TRY(launch_mode3(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, mid, st));
+  TC_TRY(launch_slice_gemm(p->AhT, p->tmp1, p->tmp2, n2, s, n1, n3, nullptr, nullptr, mid, st));
+  const float* src = p->tmp2;
+  if (p->two_sided) {
+    TC_TRY(launch_slice_gemm(p->tmp2, p->BhT, p->tmp1, n2, s, s, n3, nullptr, nullptr, mid, st));
+    src = p->tmp1;
+  }
+  return launch_mode3(src, X, p->dMT, n3, (size_t)n2 * s, ep, st);
+}
+
+namespace {
+int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
+  const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  std::vector<double> M, Mi;
+  transform_pair(n3, M, Mi);
+  // M Mi must be the identity; anything else is a bug in the closed forms.
+  for (int i = 0; i < n3; ++i)
+    for (int j = 0; j < n3; ++j) {
+      double t = 0.0;
+      for (int r = 0; r < n3; ++r) t += M[(size_t)i * n3 + r] * Mi[(size_t)r * n3 + j];
+      if (std::fabs(t - (i == j ? 1.0 : 0.0)) > 1e-9) return TC_EINVAL;
+    }
+  const size_t nn = (size_t)n3 * n3;
+  std::vector<float> fM(nn), fMi(nn), fMiT(nn), fMT(nn);
+  for (int i = 0; i < n3; ++i)
+    for (int j = 0; j < n3; ++j) {
+      fM[(size_t)i * n3 + j] = (float)M[(size_t)i * n3 + j];
+      fMi[(size_t)i * n3 + j] = (float)Mi[(size_t)i * n3 + j];
+      fMiT[(size_t)i * n3 + j] = (float)Mi[(size_t)j * n3 + i];
+      fMT[(size_t)i * n3 + j] = (float)M[(size_t)j * n3 + i];
+    }
+  if (n3 <= TC_MAX_FUSED) {
+    std::memcpy(p->hM, fM.data(), nn * sizeof(float));
+    std::memcpy(p->hMinv, fMi.data(), nn * sizeof(float));
+    std::memcpy(p->hMinvT, fMiT.data(), nn * sizeof(float));
+    std::memcpy(p->hMT, fMT.data(), nn * sizeof(float));
+  }
+  TC_TRY(dalloc(&p->dM, nn));
+  TC_TRY(dalloc(&p->dMinv, nn));
+  TC_TRY(dalloc(&p->dMinvT, nn));
+  TC_TRY(dalloc(&p->dMT, nn));
+  TC_CUDA(cudaMemcpyAsync(p->dM, fM.data(), nn * 4, cudaMemcpyHostToDevice, st));
+  TC_CUDA(cudaMemcpyAsync(p->dMinv, fMi.data(), nn * 4, cudaMemcpyHostToDevice, st));
+  TC_CUDA(cudaMemcpyAsync(p->dMinvT, fMiT.data(), nn * 4, cudaMemcpyHostToDevice, st));
+  TC_CUDA(cudaMemcpyAsync(p->dMT, fMT.data(), nn * 4, cudaMemcpyHostToDevice, st));
+
+  const size_t TA = (size_t)n3 * n1 * n2;
+  TC_TRY(dalloc(&p->Ah, TA));
+  TC_TRY(dalloc(&p->AhT, TA));
+  Epi none;
+  TC_TRY(launch_mode3(A, p->Ah, p->dM, n3, (size_t)n1 * n2, none, st));
+  TC_TRY(transpose_slices(p->Ah, p->AhT, n1, n2, n3, st));
+  if (B) {
+    const size_t TB = (size_t)n3 * s * s;
+    TC_TRY(dalloc(&p->Bh, TB));
+    TC_TRY(dalloc(&p->BhT, TB));
+    TC_TRY(launch_mode3(B, p->Bh, p->dM, n3, (size_t)s * s, none, st));
+    TC_TRY(transpose_slices(p->Bh, p->BhT, s, s, n3, st));
+  }
+  p->tmp_elems = p->Tx > p->Ty ? p->Tx : p->Ty;
+  TC_TRY(dalloc(&p->tmp1, p->tmp_elems));
+  TC_TRY(dalloc(&p->tmp2, p->tmp_elems));
+  // partials: one per CTA of the largest reducing launch (vector passes are
+  // capped at 152*32 CTAs, transform passes use P/128, fused GEMMs tiles).
+  size_t np = 152 * 32 + 64;
+  const size_t big = (p->tmp_elems / n3 + 127) / 128 + 64;
+  if (big > np) np = big;
+  const size_t tiles = (size_t)((n1 > n2 ? n1 : n2) + 31) / 32 * ((s + 31) / 32) * n3 + 64;
+  if (tiles > np) np = tiles;
+  TC_TRY(dalloc(&p->scratch.partials, np));
+  TC_TRY(dalloc(&p->scratch.tickets, 16));
+  p->scratch.npartials = np;
+  TC_CUDA(cudaMemsetAsync(p->scratch.tickets, 0, 16 * sizeof(unsigned), st));
+  TC_CUDA(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  TC_CUDA(cudaStreamSynchronize(st));
+  return TC_OK;
+}
+}  // namespace
+
+extern "C" int tc_plan_destroy(tc_plan* p) {
+  if (!p) return TC_EINVAL;
+  if (p->lsqr_graph) cudaGraphExecDestroy(p->lsqr_graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  float* fs[] = {p->Ah, p->AhT, p->Bh, p->BhT, p->dM, p->dMinv, p->dMinvT, p->dMT,
+                 p->tmp1, p->tmp2, p->lsqr_U, p->lsqr_V, p->lsqr_W, p->basis, p->gm_basis};
+  for (float* f : fs) dfree(f);
+  dfree(p->scratch.partials);
+  dfree(p->scratch.tickets);
+  dfree(p->dscal);
+  dfree(p->iflags);
+  dfree(p->gm_dscal);
+  dfree(p->gm_flags);
+  delete p;
+  return TC_OK;
+}
+
+extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, const float* A,
+                              const float* B, const tc_opts* opts, tc_stream_t stream) {
+  if (!out || !A) return TC_EINVAL;
+  *out = nullptr;
+  if (n1 < 1 || n2 < 1 || s < 1 || n3 < 1 || n3 > TC_MAX_N3) return TC_EINVAL;
+  if ((long long)n1 * n2 * n3 > (1LL << 34) || (long long)(n1 > n2 ? n1 : n2) * s * n3 > (1LL << 34))
+    return TC_EINVAL;
+  tc_opts o{};
+  o.precision = TC_FP32;
+  o.gcv_variant = TC_GCV_PAPER;
+  o.use_graphs = 1;
+  if (opts) {
+    o = *opts;
+    for (int r : o.reserved)
+      if (r != 0) return TC_EINVAL;
+    if (o.precision != TC_FP32 && o.precision != TC_TF32 && o.precision != TC_BF16)
+      return TC_EINVAL;
+    if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
+  }
+  if (o.precision != TC_FP32) return TC_EUNSUPPORTED;
+  static int inited = 0;
+  if (!inited) {
+    TC_TRY(tc_kernels_init());
+    inited = 1;
+  }
+  tc_plan* p = new (std::nothrow) tc_plan();
+  if (!p) return TC_ENOMEM;
+  p->n1 = n1; p->n2 = n2; p->s = s; p->n3 = n3;
+  p->two_sided = (B != nullptr);
+  p->opts = o;
+  p->Tx = (size_t)n2 * s * n3;
+  p->Ty = (size_t)n1 * s * n3;
+  if (cudaGetDevice(&p->device) != cudaSuccess) {
+    delete p;
+    return TC_ECUDA;
+  }
+  const int r = plan_build(p, A, B, (cudaStream_t)stream);
+  if (r != TC_OK) {
+    tc_plan_destroy(p);
+    return r;
+  }
+  *out = p;
+  return TC_OK;
+}
+
+extern "C" int tc_cprod(tc_plan* p, const float* X, float* Y, tc_stream_t stream) {
+  if (!p || !X || !Y || (const void*)X == (const void*)Y) return TC_EINVAL;
+  Epi ep;
+  return cprod_epi(p, X, Y, ep, (cudaStream_t)stream);
+}
+
+extern "C" int tc_cprod_adjoint(tc_plan* p, const float* Y, float* X, tc_stream_t stream) {
+  if (!p || !X || !Y || (const void*)X == (const void*)Y) return TC_EINVAL;
+  Epi ep;
+  return adjoint_epi(p, Y, X, ep, (cudaStream_t)stream);
+}

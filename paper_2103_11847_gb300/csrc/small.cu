@@ -1,0 +1,291 @@
+// The projected problem in FP64 on one CTA (§3.1 eqs. (leastsq), (tikho2),
+// (gcv2); §3.2 eqs. (normeq2), (leastsq0)):
+//   1. one-sided Jacobi SVD of the (k+1) x k matrix H (Hestenes rotations,
+//      round-robin pair order, warps rotate disjoint column pairs),
+//      sigma_i = ||h_i||, g~_i = beta * (first row of H V)_i / sigma_i;
+//   2. GCV(lambda) of eq. (gcv2) ("paper") or of the rectangular problem
+//      ("full", with g~_{k+1}^2 = beta^2 - sum g~_i^2), minimised on 200
+//      log-spaced points in [1e-3 sigma_min, sigma_max] (first minimum on
+//      ties), then 40 golden-section steps in log(lambda) between the grid
+//      neighbours; the grid point is kept if the refinement is not lower;
+//   3. y from the normal equations (H^T H + lambda^2 I) y = beta H^T e_1 by
+//      Cholesky.
+// GB300 runs FP64 at a small fraction of its FP32 rate, so everything here is
+// O(k^2)..O(k^3) work on k <= TC_MAX_PROJ numbers.
+#include "tc_device.cuh"
+
+namespace {
+
+constexpr int NT = 256;
+constexpr int NGRID = 200;
+constexpr int NGOLD = 40;
+constexpr int MAX_SWEEPS = 40;
+
+__device__ double gcv_eval(const double* sig, const double* g, int k, double gnull2,
+                           double lam, int variant) {
+  const double l2 = lam * lam;
+  double num = 0.0, den = 0.0;
+  if (variant == TC_GCV_FULL) {
+    for (int i = 0; i < k; ++i) {
+      const double d = sig[i] * sig[i] + l2;
+      const double r = l2 * g[i] / d;
+      num += r * r;
+      den += l2 / d;
+    }
+    num += gnull2;
+    den += 1.0;
+    return num / (den * den);
+  }
+  for (int i = 0; i < k; ++i) {
+    const double d = sig[i] * sig[i] + l2;
+    const double r = g[i] / d;
+    num += r * r;
+    den += 1.0 / d;
+  }
+  return num / (den * den);
+}
+
+__device__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Dynamic shared memory: Hs[(k+1) * kk] (column-major working copy, kk = k
+// rounded up to even), reused as the k x k normal matrix afterwards.
+__global__ void __launch_bounds__(NT)
+k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
+               const double* beta_p, int variant, double lambda_in, double* lambda_out,
+               double* y, double* gcv_out, const int* skip) {
+  if (skip && *skip) return;
+  extern __shared__ double dsm[];
+  __shared__ double sig[TC_MAX_PROJ], g[TC_MAX_PROJ];
+  __shared__ double vals[NGRID];
+  __shared__ double grid[NGRID];
+  __shared__ int sh_rot;
+  __shared__ double sh_misc[8];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int k = kdev ? min(*kdev, kmax) : kmax;
+  const double beta = *beta_p;
+  if (k <= 0) {
+    if (tid == 0) {
+      *lambda_out = nan("");
+      if (gcv_out) *gcv_out = nan("");
+    }
+    return;
+  }
+  const int rows = k + 1;
+  const int kk = k + (k & 1);
+  double* Hs = dsm;  // column c at Hs + c*rows
+  for (int idx = tid; idx < rows * kk; idx += NT) {
+    const int c = idx / rows, r = idx % rows;
+    Hs[idx] = (c < k) ? H[(size_t)r * ld + c] : 0.0;
+  }
+  __syncthreads();
+
+  // ---- 1. one-sided Jacobi -------------------------------------------------
+  const int npairs = kk / 2;
+  for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
+    if (tid == 0) sh_rot = 0;
+    __syncthreads();
+    for (int rnd = 0; rnd < kk - 1; ++rnd) {
+      for (int pi = warp; pi < npairs; pi += NT / 32) {
+        // circle method: player 0 fixed, the others rotate by rnd
+        const int a = (pi == 0) ? 0 : ((pi - 1 + rnd) % (kk - 1)) + 1;
+        const int b = ((kk - 2 - pi + rnd) % (kk - 1)) + 1;
+        double* xp = Hs + (size_t)a * rows;
+        double* xq = Hs + (size_t)b * rows;
+        double al = 0.0, be = 0.0, ga = 0.0;
+        for (int r = lane; r < rows; r += 32) {
+          const double u = xp[r], v = xq[r];
+          al += u * u;
+          be += v * v;
+          ga += u * v;
+        }
+        al = warp_sum_d(al);
+        be = warp_sum_d(be);
+        ga = warp_sum_d(ga);
+        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+          const double zeta = (be - al) / (2.0 * ga);
+          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+          const double c = 1.0 / sqrt(1.0 + t * t);
+          const double s = c * t;
+          for (int r = lane; r < rows; r += 32) {
+            const double u = xp[r], v = xq[r];
+            xp[r] = c * u - s * v;
+            xq[r] = s * u + c * v;
+          }
+          if (lane == 0) sh_rot = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int any = sh_rot;
+    __syncthreads();
+    if (!any) break;
+  }
+  for (int c = warp; c < k; c += NT / 32) {
+    const double* x = Hs + (size_t)c * rows;
+    double s2 = 0.0;
+    for (int r = lane; r < rows; r += 32) s2 += x[r] * x[r];
+    s2 = warp_sum_d(s2);
+    if (lane == 0) {
+      const double sv = sqrt(s2);
+      sig[c] = sv;
+      g[c] = (sv > 0.0) ? beta * x[0] / sv : 0.0;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double smax = 0.0, smin = 1e308, gs = 0.0;
+    for (int i = 0; i < k; ++i) {
+      smax = fmax(smax, sig[i]);
+      smin = fmin(smin, sig[i]);
+      gs += g[i] * g[i];
+    }
+    sh_misc[0] = smax;
+    sh_misc[1] = smin;
+    sh_misc[2] = fmax(beta * beta - gs, 0.0);
+  }
+  __syncthreads();
+  const double smax = sh_misc[0], smin = sh_misc[1], gnull2 = sh_misc[2];
+
+  // ---- 2. lambda -------------------------------------------------------------
+  double lam = lambda_in;
+  if (!(lambda_in >= 0.0)) {
+    const double lo = (smin > 0.0) ? 1e-3 * smin : 1e-12 * smax;
+    const double llo = log(lo), lhi = log(smax);
+    const double step = (lhi - llo) / (NGRID - 1);
+    for (int i = tid; i < NGRID; i += NT) {
+      const double t = (i == NGRID - 1) ? lhi : llo + i * step;
+      grid[i] = exp(t);
+      vals[i] = gcv_eval(sig, g, k, gnull2, grid[i], variant);
+    }
+    __syncthreads();
+    if (tid == 0) {
+      int bi = 0;
+      for (int i = 1; i < NGRID; ++i)
+        if (vals[i] < vals[bi]) bi = i;
+      double a = log(grid[max(bi - 1, 0)]);
+      double b = log(grid[min(bi + 1, NGRID - 1)]);
+      const double invphi = (sqrt(5.0) - 1.0) / 2.0;
+      double c = b - invphi * (b - a), d = a + invphi * (b - a);
+      double fc = gcv_eval(sig, g, k, gnull2, exp(c), variant);
+      double fd = gcv_eval(sig, g, k, gnull2, exp(d), variant);
+      for (int it = 0; it < NGOLD; ++it) {
+        if (fc <= fd) {
+          b = d; d = c; fd = fc;
+          c = b - invphi * (b - a);
+          fc = gcv_eval(sig, g, k, gnull2, exp(c), variant);
+        } else {
+          a = c; c = d; fc = fd;
+          d = a + invphi * (b - a);
+          fd = gcv_eval(sig, g, k, gnull2, exp(d), variant);
+        }
+      }
+      const double t = (fc <= fd) ? c : d;
+      const double best = fmin(fc, fd);
+      if (vals[bi] < best) {
+        sh_misc[3] = grid[bi];
+        sh_misc[4] = vals[bi];
+      } else {
+        sh_misc[3] = exp(t);
+        sh_misc[4] = best;
+      }
+    }
+    __syncthreads();
+    lam = sh_misc[3];
+  } else if (tid == 0) {
+    sh_misc[4] = gcv_eval(sig, g, k, gnull2, lam, variant);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    *lambda_out = lam;
+    if (gcv_out) *gcv_out = sh_misc[4];
+  }
+
+  // ---- 3. (H^T H + lambda^2 I) y = beta H^T e_1, Cholesky --------------------
+  double* G = dsm;  // k x k row-major, overwrites the Jacobi copy
+  __syncthreads();
+  for (int idx = tid; idx < k * k; idx += NT) {
+    const int i = idx / k, jj = idx % k;
+    double s = 0.0;
+    for (int r = 0; r < rows; ++r) s += H[(size_t)r * ld + i] * H[(size_t)r * ld + jj];
+    if (i == jj) s += lam * lam;
+    G[idx] = s;
+  }
+  for (int i = tid; i < k; i += NT) g[i] = beta * H[i];  // rhs = beta * (row 1 of H)
+  __syncthreads();
+  for (int c = 0; c < k; ++c) {
+    if (tid == 0) G[c * k + c] = sqrt(G[c * k + c]);
+    __syncthreads();
+    const double d = G[c * k + c];
+    for (int r = c + 1 + tid; r < k; r += NT) G[r * k + c] /= d;
+    __syncthreads();
+    for (int idx = tid; idx < (k - c - 1) * (k - c - 1); idx += NT) {
+      const int r = c + 1 + idx / (k - c - 1), q = c + 1 + idx % (k - c - 1);
+      if (q <= r) G[r * k + q] -= G[r * k + c] * G[q * k + c];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    for (int r = 0; r < k; ++r) {  // L z = rhs
+      double s = g[r];
+      for (int q = 0; q < r; ++q) s -= G[r * k + q] * sig[q];
+      sig[r] = s / G[r * k + r];
+    }
+    for (int r = k - 1; r >= 0; --r) {  // L^T y = z
+      double s = sig[r];
+      for (int q = r + 1; q < k; ++q) s -= G[q * k + r] * g[q];
+      g[r] = s / G[r * k + r];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < kmax; i += NT) y[i] = (i < k) ? g[i] : 0.0;
+}
+
+__global__ void k_build_bidiag(const double* alpha, const double* beta, const int* kdev,
+                               int kmax, double* H) {
+  const int k = kdev ? min(*kdev, kmax) : kmax;
+  for (int idx = threadIdx.x; idx < (kmax + 1) * kmax; idx += blockDim.x) {
+    const int r = idx / kmax, c = idx % kmax;
+    double v = 0.0;
+    if (c < k) {
+      if (r == c) v = alpha[c];
+      else if (r == c + 1) v = beta[c + 1];
+    }
+    H[idx] = v;
+  }
+}
+
+}  // namespace
+
+int launch_tikhonov_gcv(const double* H, int ld, int kmax, const int* kdev,
+                        const double* beta, int variant, double lambda_in,
+                        double* lambda_out, double* y, double* gcv_out, const int* skip,
+                        cudaStream_t st) {
+  TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ);
+  const int kk = kmax + (kmax & 1);
+  size_t smem = sizeof(double) * (size_t)(kmax + 1) * kk;
+  const size_t gsz = sizeof(double) * (size_t)kmax * kmax;
+  if (gsz > smem) smem = gsz;
+  k_tikhonov_gcv<<<1, NT, smem, st>>>(H, ld, kmax, kdev, beta, variant, lambda_in, lambda_out,
+                                      y, gcv_out, skip);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_build_bidiag(const double* alpha, const double* beta, const int* kdev, int kmax,
+                        double* H, cudaStream_t st) {
+  k_build_bidiag<<<1, 256, 0, st>>>(alpha, beta, kdev, kmax, H);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// Called once per process (from plan creation) so that no attribute call
+// happens while a stream is being captured.
+int tc_kernels_init() {
+  TC_CUDA(cudaFuncSetAttribute(k_tikhonov_gcv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               200 * 1024));
+  return TC_OK;
+}

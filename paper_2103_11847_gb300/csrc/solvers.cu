@@ -1,0 +1,404 @@
+// Krylov drivers of §3 on the device: Golub-Kahan (Algorithm 4), DC-LSQR
+// (Algorithm 6) with the optional Tikhonov/GCV projection (Algorithm 5,
+// eqs. (normeq2), (xmlsqr)), restarted DC-GMRES(m) (Algorithms 2 and 3), and
+// the projected Tikhonov/GCV solve. The host only enqueues work: every scalar
+// (alpha, beta, rho, phi, h, lambda) lives in device memory and kernels read it
+// there, so a whole solve runs without a host round trip and can be replayed
+// as one CUDA graph. Early stops (convergence, breakdown) raise a device flag
+// that makes the remaining launches of the solve return at once.
+#include <cmath>
+#include <cstring>
+
+#include "tc_device.cuh"
+
+namespace {
+
+// Grow-only device buffer; *moved is set when the buffer was reallocated.
+template <class T>
+int grow(T** p, size_t* have, size_t need, bool* moved = nullptr) {
+  if (*p && *have >= need) return TC_OK;
+  if (moved) *moved = true;
+  if (*p) cudaFree(*p);
+  *p = nullptr;
+  *have = 0;
+  cudaError_t e = cudaMalloc((void**)p, (need ? need : 1) * sizeof(T));
+  if (e != cudaSuccess) {
+    tc_set_error("cudaMalloc", e);
+    *p = nullptr;
+    return TC_ENOMEM;
+  }
+  *have = need;
+  return TC_OK;
+}
+
+int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
+  bool moved = false;
+  if (!p->lsqr_U) {
+    moved = true;
+    if (cudaMalloc((void**)&p->lsqr_U, p->Ty * 4) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc((void**)&p->lsqr_V, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc((void**)&p->lsqr_W, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
+  }
+  if (!p->iflags && cudaMalloc((void**)&p->iflags, 16 * sizeof(int)) != cudaSuccess)
+    return TC_ENOMEM;
+  const size_t L = (size_t)itermax + 2;
+  const size_t kp = (size_t)(itermax < TC_MAX_PROJ ? itermax : TC_MAX_PROJ);
+  TC_TRY(grow(&p->dscal, &p->dscal_elems, 4 * L + (kp + 1) * kp + kp + 16, &moved));
+  if (keep_basis) TC_TRY(grow(&p->basis, &p->basis_elems, (size_t)itermax * p->Tx, &moved));
+  if (moved && p->lsqr_graph) {  // a captured solve holds the old addresses
+    cudaGraphExecDestroy(p->lsqr_graph);
+    p->lsqr_graph = nullptr;
+  }
+  return TC_OK;
+}
+
+// alpha_1 = ||A^T U_1|| and beta_1 = ||C|| are in place: set W_1 = V_1 and the
+// Givens state rhobar_1 = alpha_1, phibar_1 = beta_1 (Algorithm 6 step 2).
+__global__ void k_lsqr_init(const double* alpha, const double* beta, double* rhobar,
+                            double* phibar, int* flags) {
+  rhobar[0] = alpha[0];
+  phibar[0] = beta[0];
+  flags[1] = 0;
+  if (!isfinite(alpha[0]) || !isfinite(beta[0])) flags[2] = TC_ENONFINITE;
+  else if (alpha[0] == 0.0 || beta[0] == 0.0) flags[2] = TC_EBREAKDOWN;
+  if (flags[2] != 0) flags[0] = 1;
+}
+
+__global__ void k_lsqr_info(tc_solve_info* info, const int* flags, const double* phibar,
+                            const double* beta, const double* lam, const double* gcv) {
+  const int it = flags[1];
+  info->iters = it;
+  info->status = flags[2];
+  info->cycles = 0;
+  info->pad = 0;
+  info->resid = fabs(phibar[it]);
+  info->lambda = lam ? *lam : nan("");
+  info->gcv = gcv ? *gcv : nan("");
+  info->beta1 = beta[0];
+}
+
+// GMRES helpers. flags: [0] done, [1] total steps, [2] status, [3] steps in the
+// current cycle, [4] Arnoldi stopped in this cycle (done or h_{j+1,j} = 0).
+__global__ void k_gmres_check(const double* rnorm, double tol, int* flags, double* resid,
+                              int cycle) {
+  if (flags[0]) return;
+  *resid = *rnorm;
+  if (!isfinite(*rnorm)) {
+    flags[2] = TC_ENONFINITE;
+    flags[0] = 1;
+  } else if (*rnorm < tol || *rnorm == 0.0) {
+    flags[2] = 1;
+    flags[0] = 1;
+  }
+  flags[3] = 0;
+  flags[4] = flags[0];
+  flags[5] = cycle;
+}
+
+__global__ void k_gmres_step_done(const double* hnext, int j, int* flags) {
+  if (flags[4]) return;
+  flags[3] = j + 1;
+  flags[1] += 1;
+  if (!(*hnext > 0.0)) flags[4] = 1;  // h_{j+1,j} = 0 (or NaN): stop this cycle
+}
+
+__global__ void k_gmres_cycle_done(int* flags) {
+  if (!flags[0]) flags[5] += 1;
+}
+
+__global__ void k_gmres_info(tc_solve_info* info, const int* flags, const double* resid,
+                             const double* lam, const double* gcv, const double* beta1) {
+  info->iters = flags[1];
+  info->status = flags[2];
+  info->cycles = flags[5];
+  info->pad = 0;
+  info->resid = *resid;
+  info->lambda = *lam;
+  info->gcv = *gcv;
+  info->beta1 = *beta1;
+}
+
+// ----------------------------------------------------------------- LSQR ----
+struct LsqrArgs {
+  const float* C;
+  float* X;
+  float* X_reg;
+  int itermax;
+  double tol, lambda;
+  double* hist;
+  tc_solve_info* info;
+};
+
+int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
+  const size_t L = (size_t)a.itermax + 2;
+  const int kp = a.itermax < TC_MAX_PROJ ? a.itermax : TC_MAX_PROJ;
+  double* alpha = p->dscal;
+  double* beta = alpha + L;
+  double* rhobar = beta + L;
+  double* phibar = rhobar + L;
+  double* Hm = phibar + L;
+  double* y = Hm + (size_t)(kp + 1) * kp;
+  double* lam = y + kp;
+  double* gcv = lam + 1;
+  int* flags = p->iflags;
+  float *U = p->lsqr_U, *V = p->lsqr_V, *W = p->lsqr_W;
+  const bool keep = a.X_reg != nullptr;
+
+  TC_CUDA(cudaMemsetAsync(flags, 0, 16 * sizeof(int), st));
+  // beta_1 = ||C||_F
+  TC_TRY(launch_reduce(a.C, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
+  // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
+  {
+    Epi ep;
+    ep.coef.rule = COEF_INV;
+    ep.coef.s0 = beta;
+    ep.red = make_red(p, alpha, 1, nullptr, flags + 2);
+    TC_TRY(adjoint_epi(p, a.C, V, ep, st));
+  }
+  // W_1 = V_1 = V~_1 / alpha_1; X_0 = 0
+  {
+    Coef c;
+    c.rule = COEF_INV;
+    c.s0 = alpha;
+    TC_TRY(launch_scale(V, W, p->Tx, c, nullptr, nullptr, st));
+    if (keep) TC_TRY(launch_scale(V, p->basis, p->Tx, c, nullptr, nullptr, st));
+  }
+  TC_CUDA(cudaMemsetAsync(a.X, 0, p->Tx * sizeof(float), st));
+  k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags);
+  TC_CUDA(cudaGetLastError());
+
+  for (int j = 0; j < a.itermax; ++j) {
+    // (a) U~_{j+1} = A V_j - alpha_j U_j = (1/alpha_j) A V~_j - (alpha_j/beta_j) U~_j
+    {
+      Epi ep;
+      ep.coef.rule = COEF_GK;
+      ep.coef.s0 = alpha + j;
+      ep.coef.s1 = beta + j;
+      ep.prev = (j == 0) ? a.C : U;
+      ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
+      ep.skip = flags;
+      TC_TRY(cprod_epi(p, V, U, ep, st));
+    }
+    // (b) V~_{j+1} = (1/beta_{j+1}) A^T U~_{j+1} - (beta_{j+1}/alpha_j) V~_j
+    {
+      Epi ep;
+      ep.coef.rule = COEF_GK;
+      ep.coef.s0 = beta + j + 1;
+      ep.coef.s1 = alpha + j;
+      ep.prev = V;
+      ep.red = make_red(p, alpha + j + 1, 1, nullptr, flags + 2);
+      ep.skip = flags;
+      TC_TRY(adjoint_epi(p, U, V, ep, st));
+    }
+    // (c)-(g) Givens recurrences and the X, W updates
+    float* slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
+    TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist, j,
+                              a.tol, flags, st));
+  }
+  if (keep) {
+    TC_TRY(launch_build_bidiag(alpha, beta, flags + 1, kp, Hm, st));
+    TC_TRY(launch_tikhonov_gcv(Hm, kp, kp, flags + 1, beta, p->opts.gcv_variant, a.lambda,
+                               lam, y, gcv, nullptr, st));
+    TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
+                          st));
+  }
+  k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, keep ? lam : nullptr,
+                               keep ? gcv : nullptr);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+}  // namespace
+
+extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int itermax,
+                         double tol, double lambda, double* phibar_hist, tc_solve_info* info,
+                         tc_stream_t stream) {
+  if (!p || !C || !X || !info) return TC_EINVAL;
+  if (itermax < 1 || itermax > 4096 || !(tol >= 0.0)) return TC_EINVAL;
+  if (X_reg && itermax > TC_MAX_PROJ) return TC_EINVAL;
+  if ((const void*)C == (const void*)X || (X_reg && (X_reg == X))) return TC_EINVAL;
+  TC_TRY(ensure_lsqr(p, itermax, X_reg != nullptr));
+  cudaStream_t st = (cudaStream_t)stream;
+  LsqrArgs a{C, X, X_reg, itermax, tol, lambda, phibar_hist, info};
+  if (!p->opts.use_graphs) return lsqr_enqueue(p, a, st);
+
+  uint64_t tb, lb;
+  std::memcpy(&tb, &tol, 8);
+  std::memcpy(&lb, &lambda, 8);
+  const uintptr_t key[8] = {(uintptr_t)C, (uintptr_t)X, (uintptr_t)X_reg, (uintptr_t)itermax,
+                            (uintptr_t)tb, (uintptr_t)lb, (uintptr_t)phibar_hist,
+                            (uintptr_t)info};
+  if (!p->lsqr_graph || std::memcmp(key, p->lsqr_key, sizeof(key)) != 0) {
+    if (p->lsqr_graph) {
+      cudaGraphExecDestroy(p->lsqr_graph);
+      p->lsqr_graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    TC_CUDA(cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal));
+    const int r = lsqr_enqueue(p, a, p->cap_stream);
+    const cudaError_t e = cudaStreamEndCapture(p->cap_stream, &g);
+    if (r != TC_OK) {
+      if (g) cudaGraphDestroy(g);
+      return r;
+    }
+    if (e != cudaSuccess) {
+      tc_set_error("cudaStreamEndCapture", e);
+      return TC_ECUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&p->lsqr_graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      p->lsqr_graph = nullptr;
+      tc_set_error("cudaGraphInstantiate", e2);
+      return TC_ECUDA;
+    }
+    std::memcpy(p->lsqr_key, key, sizeof(key));
+  }
+  TC_CUDA(cudaGraphLaunch(p->lsqr_graph, st));
+  return TC_OK;
+}
+
+// ------------------------------------------------------------ Golub-Kahan ----
+extern "C" int tc_gkb_init(tc_plan* p, const float* C, float* U, float* V, double* alpha,
+                           double* beta, int mmax, tc_stream_t stream) {
+  if (!p || !C || !U || !V || !alpha || !beta || mmax < 1) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  TC_TRY(launch_reduce(C, nullptr, p->Ty, make_red(p, beta, 1, nullptr, nullptr), nullptr, st));
+  Coef c;
+  c.rule = COEF_INV;
+  c.s0 = beta;
+  TC_TRY(launch_scale(C, U, p->Ty, c, nullptr, nullptr, st));
+  Epi ep;
+  ep.red = make_red(p, alpha, 1, nullptr, nullptr);
+  TC_TRY(adjoint_epi(p, U, V, ep, st));
+  c.s0 = alpha;
+  return launch_scale(V, V, p->Tx, c, nullptr, nullptr, st);
+}
+
+extern "C" int tc_gkb_step(tc_plan* p, int j, float* U, float* V, double* alpha, double* beta,
+                           int mmax, tc_stream_t stream) {
+  if (!p || !U || !V || !alpha || !beta || j < 1 || j > mmax) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* Uj = U + (size_t)(j - 1) * p->Ty;
+  float* Uj1 = U + (size_t)j * p->Ty;
+  const float* Vj = V + (size_t)(j - 1) * p->Tx;
+  float* Vj1 = V + (size_t)j * p->Tx;
+  Coef inv;
+  inv.rule = COEF_INV;
+  {  // U~ = A V_j - alpha_j U_j, beta_{j+1} = ||U~||, U_{j+1} = U~ / beta_{j+1}
+    Epi ep;
+    ep.coef.rule = COEF_AXPY;
+    ep.coef.s0 = alpha + (j - 1);
+    ep.prev = Uj;
+    ep.red = make_red(p, beta + j, 1, nullptr, nullptr);
+    TC_TRY(cprod_epi(p, Vj, Uj1, ep, st));
+    inv.s0 = beta + j;
+    TC_TRY(launch_scale(Uj1, Uj1, p->Ty, inv, nullptr, nullptr, st));
+  }
+  {  // V~ = A^T U_{j+1} - beta_{j+1} V_j, alpha_{j+1} = ||V~||, V_{j+1} = V~ / alpha_{j+1}
+    Epi ep;
+    ep.coef.rule = COEF_AXPY;
+    ep.coef.s0 = beta + j;
+    ep.prev = Vj;
+    ep.red = make_red(p, alpha + j, 1, nullptr, nullptr);
+    TC_TRY(adjoint_epi(p, Uj1, Vj1, ep, st));
+    inv.s0 = alpha + j;
+    TC_TRY(launch_scale(Vj1, Vj1, p->Tx, inv, nullptr, nullptr, st));
+  }
+  return TC_OK;
+}
+
+// ------------------------------------------------------------------ GMRES ----
+extern "C" int tc_gmres_c(tc_plan* p, const float* C, const float* X0, float* X, int m,
+                          int itermax, double tol, double lambda, tc_solve_info* info,
+                          tc_stream_t stream) {
+  if (!p || !C || !X || !info) return TC_EINVAL;
+  if (p->n1 != p->n2 || m < 1 || m > TC_MAX_PROJ || itermax < 1 || !(tol >= 0.0))
+    return TC_EINVAL;
+  if ((const void*)C == (const void*)X) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t T = p->Tx;  // == Ty for a square operator
+  TC_TRY(grow(&p->gm_basis, &p->gm_basis_elems, (size_t)(m + 1) * T));
+  TC_TRY(grow(&p->gm_dscal, &p->gm_dscal_elems, (size_t)(m + 1) * m + m + 16));
+  if (!p->gm_flags && cudaMalloc((void**)&p->gm_flags, 16 * sizeof(int)) != cudaSuccess)
+    return TC_ENOMEM;
+  double* H = p->gm_dscal;
+  double* y = H + (size_t)(m + 1) * m;
+  double* rnorm = y + m;
+  double* lam = rnorm + 1;
+  double* gcv = lam + 1;
+  double* resid = gcv + 1;
+  double* beta1 = resid + 1;
+  int* flags = p->gm_flags;
+  float* Vb = p->gm_basis;
+
+  TC_CUDA(cudaMemsetAsync(flags, 0, 16 * sizeof(int), st));
+  TC_CUDA(cudaMemsetAsync(lam, 0xff, 2 * sizeof(double), st));  // NaN until a cycle runs
+  TC_TRY(launch_reduce(C, nullptr, T, make_red(p, beta1, 1, nullptr, nullptr), nullptr, st));
+  if (X0) {
+    TC_CUDA(cudaMemcpyAsync(X, X0, T * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  } else {
+    TC_CUDA(cudaMemsetAsync(X, 0, T * sizeof(float), st));
+  }
+  int done = 0, cycle = 0;
+  while (true) {
+    // R_0 = C - A X (Algorithm 3 step 3; recomputed on every restart)
+    Epi er;
+    er.coef.rule = COEF_RESID;
+    er.prev = C;
+    er.red = make_red(p, rnorm, 1, nullptr, flags + 2);
+    er.skip = flags;
+    TC_TRY(cprod_epi(p, X, Vb, er, st));
+    k_gmres_check<<<1, 1, 0, st>>>(rnorm, tol, flags, resid, cycle);
+    TC_CUDA(cudaGetLastError());
+    if (done >= itermax) break;
+    const int mj = (m < itermax - done) ? m : (itermax - done);
+    TC_CUDA(cudaMemsetAsync(H, 0, (size_t)(m + 1) * m * sizeof(double), st));
+    // Algorithm 2: V_1 = R_0 / beta
+    Coef inv;
+    inv.rule = COEF_INV;
+    inv.s0 = rnorm;
+    TC_TRY(launch_scale(Vb, Vb, T, inv, nullptr, flags + 4, st));
+    for (int j = 0; j < mj; ++j) {
+      float* Vj = Vb + (size_t)j * T;
+      float* Wn = Vb + (size_t)(j + 1) * T;
+      double* hcol = H + j;  // H(i, j) at H[i*m + j]
+      Epi ea;  // W = A V_j, fused with h_{1,j} = <V_1, W>
+      ea.red = make_red(p, hcol, 0, Vb, flags + 2);
+      ea.skip = flags + 4;
+      TC_TRY(cprod_epi(p, Vj, Wn, ea, st));
+      for (int i = 0; i <= j; ++i) {  // MGS: W -= h_ij V_i, then the next product
+        const bool last = (i == j);
+        Red r = make_red(p, H + (size_t)(i + 1) * m + j, last ? 1 : 0,
+                         last ? nullptr : Vb + (size_t)(i + 1) * T, flags + 2);
+        TC_TRY(launch_mgs_pass(Wn, Vb + (size_t)i * T, H + (size_t)i * m + j,
+                               last ? nullptr : Vb + (size_t)(i + 1) * T, T, r, flags + 4, st));
+      }
+      inv.s0 = H + (size_t)(j + 1) * m + j;  // V_{j+1} = W / h_{j+1,j}
+      TC_TRY(launch_scale(Wn, Wn, T, inv, nullptr, flags + 4, st));
+      k_gmres_step_done<<<1, 1, 0, st>>>(H + (size_t)(j + 1) * m + j, j, flags);
+      TC_CUDA(cudaGetLastError());
+    }
+    // Algorithm 3 steps 5-6: lambda by GCV on H~, y, X = X_0 + V (*) y
+    TC_TRY(launch_tikhonov_gcv(H, m, mj, flags + 3, rnorm, p->opts.gcv_variant, lambda, lam, y,
+                               gcv, flags, st));
+    TC_TRY(launch_combine(X, X, Vb, T, mj, flags + 3, y, T, flags, st));
+    k_gmres_cycle_done<<<1, 1, 0, st>>>(flags);
+    TC_CUDA(cudaGetLastError());
+    done += mj;
+    ++cycle;
+  }
+  k_gmres_info<<<1, 1, 0, st>>>(info, flags, resid, lam, gcv, beta1);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// --------------------------------------------------------- Tikhonov / GCV ----
+extern "C" int tc_tikhonov_gcv(const double* H, int k, const double* beta, int variant,
+                               double lambda_in, double* lambda_out, double* y, double* gcv_out,
+                               tc_stream_t stream) {
+  if (!H || !beta || !lambda_out || !y || k < 1 || k > TC_MAX_PROJ) return TC_EINVAL;
+  if (variant != TC_GCV_PAPER && variant != TC_GCV_FULL) return TC_EINVAL;
+  return launch_tikhonov_gcv(H, k, k, nullptr, beta, variant, lambda_in, lambda_out, y, gcv_out,
+                             nullptr, (cudaStream_t)stream);
+}

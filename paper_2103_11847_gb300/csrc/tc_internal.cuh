@@ -1,0 +1,148 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "tcprod.h"
+
+// Slices handled by one CTA when the mode-3 transform is fused into the slice
+// GEMM (prologue on the operand, epilogue back to the spatial domain). Larger
+// n3 takes the unfused route: a transform pass, per-slice GEMMs, a transform
+// pass with the Krylov epilogue.
+#define TC_MAX_FUSED 4
+#define TC_MAX_N3 128
+#define TC_MAX_PROJ 128  // largest projected problem (k) on the device
+
+// ---------------------------------------------------------------- epilogue --
+// Every product and transform pass ends in
+//     out = ca * value + cp * prev
+// where (ca, cp) follow `rule` from device scalars s0, s1 (one thread reads
+// them and shares through shared memory), optionally followed by a reduction
+// of out (sum of squares, or dot with `other`) into a deterministic two-level
+// tree: one FP64 partial per CTA, summed in CTA order by the last CTA.
+enum CoefRule : int {
+  COEF_ONE = 0,    // ca = 1,       cp = 0
+  COEF_RESID = 1,  // ca = -1,      cp = 1       (R = C - M(X))
+  COEF_GK = 2,     // ca = 1/s0,    cp = -s0/s1  (Golub-Kahan with deferred normalisation)
+  COEF_INV = 3,    // ca = 1/s0,    cp = 0
+  COEF_NEG = 4,    // ca = -1,      cp = 0
+  COEF_AXPY = 5    // ca = 1,       cp = -s0
+};
+
+struct Coef {
+  int rule = COEF_ONE;
+  const double* s0 = nullptr;
+  const double* s1 = nullptr;
+};
+
+struct Red {
+  double* out = nullptr;          // nullptr: no reduction
+  const float* other = nullptr;   // nullptr: sum of squares; else <out, other>
+  int sqrt_out = 0;               // write sqrt of the sum
+  double* partials = nullptr;     // >= gridDim.x*gridDim.y*gridDim.z doubles
+  unsigned* ticket = nullptr;     // zero before the launch; reset by the last CTA
+  int* status = nullptr;          // set to TC_ENONFINITE when the sum is not finite
+};
+
+struct Epi {
+  Coef coef;
+  const float* prev = nullptr;    // same layout as the output, may alias it
+  Red red;
+  const int* skip = nullptr;      // nonzero: the whole kernel returns at once
+};
+
+// --------------------------------------------------------------- workspaces --
+struct Scratch {
+  double* partials = nullptr;
+  unsigned* tickets = nullptr;    // a few independent tickets
+  size_t npartials = 0;
+};
+
+struct tc_plan {
+  int n1, n2, s, n3;
+  bool two_sided;
+  tc_opts opts;
+  int device;
+  size_t Tx, Ty;                  // elements of X (n2 s n3) and of Y (n1 s n3)
+  float *Ah = nullptr, *AhT = nullptr;     // A x_3 M and its slice transposes
+  float *Bh = nullptr, *BhT = nullptr;
+  float *dM = nullptr, *dMinv = nullptr, *dMinvT = nullptr, *dMT = nullptr;  // n3 x n3
+  float hM[TC_MAX_FUSED * TC_MAX_FUSED], hMinv[TC_MAX_FUSED * TC_MAX_FUSED];
+  float hMinvT[TC_MAX_FUSED * TC_MAX_FUSED], hMT[TC_MAX_FUSED * TC_MAX_FUSED];
+  float *tmp1 = nullptr, *tmp2 = nullptr;  // transform-domain intermediates
+  size_t tmp_elems = 0;
+  Scratch scratch;
+  // solver workspaces (grow-only)
+  float* lsqr_U = nullptr; float* lsqr_V = nullptr; float* lsqr_W = nullptr;
+  float* basis = nullptr; size_t basis_elems = 0;
+  double* dscal = nullptr; size_t dscal_elems = 0;
+  int* iflags = nullptr;
+  float* gm_basis = nullptr; size_t gm_basis_elems = 0;    // GMRES basis V_1..V_{m+1}
+  double* gm_dscal = nullptr; size_t gm_dscal_elems = 0;
+  int* gm_flags = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  // graph cache for tc_lsqr_c
+  cudaGraphExec_t lsqr_graph = nullptr;
+  uintptr_t lsqr_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+// ----------------------------------------------------------- error helpers --
+void tc_set_error(const char* what, cudaError_t e);
+#define TC_CUDA(call)                                   \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) {                            \
+      tc_set_error(#call, e_);                          \
+      return TC_ECUDA;                                  \
+    }                                                   \
+  } while (0)
+#define TC_CHECK(cond)                                  \
+  do {                                                  \
+    if (!(cond)) return TC_EINVAL;                      \
+  } while (0)
+#define TC_TRY(call)                                    \
+  do {                                                  \
+    int r_ = (call);                                    \
+    if (r_ != TC_OK) return r_;                         \
+  } while (0)
+
+// ---------------------------------------------------------- kernel drivers --
+// gemm.cu: C_k = A_k * (pro-transformed B)_k for nslices slices, epilogue.
+// A: M x K per slice (row-major), B: K x N, C/prev: M x N; slice strides are
+// the dense sizes. pro/epi: n3 x n3 row-major (host arrays, by value), used
+// only when the CTA owns all n3 <= TC_MAX_FUSED slices.
+int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, int K,
+                      int nslices, const float* pro, const float* epi, const Epi& ep,
+                      cudaStream_t st);
+// transform.cu: out[k][p] = ca * sum_l T[k][l] in[l][p] + cp * prev[k][p] over P pixels.
+int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
+                 const Epi& ep, cudaStream_t st);
+// vec.cu
+int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
+                  const int* skip, cudaStream_t st);
+int launch_scale(const float* in, float* out, size_t n, const Coef& c, const float* prev,
+                 const int* skip, cudaStream_t st);
+int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
+                       double* alpha, double* beta, double* rhobar, double* phibar,
+                       double* phibar_hist, int j, double tol, int* flags,
+                       cudaStream_t st);
+int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
+                   const int* kdev, const double* y, size_t n, const int* skip,
+                   cudaStream_t st);
+int launch_mgs_pass(float* W, const float* Vi, const double* h, const float* Vnext,
+                    size_t n, const Red& red, const int* skip, cudaStream_t st);
+// small.cu (FP64, one CTA)
+int launch_tikhonov_gcv(const double* H, int ld, int kmax, const int* kdev,
+                        const double* beta, int variant, double lambda_in,
+                        double* lambda_out, double* y, double* gcv_out, const int* skip,
+                        cudaStream_t st);
+int launch_build_bidiag(const double* alpha, const double* beta, const int* kdev, int kmax,
+                        double* H, cudaStream_t st);
+
+// plan.cu helpers used by solvers
+int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st);
+int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st);
+Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
+int tc_kernels_init();

@@ -1,0 +1,99 @@
+// Mode-3 transform pass for n3 > TC_MAX_FUSED (Remark 2.1: X~ = X x_3 T with
+// T one of M, M^{-1}, M^{-T}, M^T): out[k][p] = ca * sum_l T[k][l] in[l][p]
+// + cp * prev[k][p], with the fused reduction of the epilogue. Each CTA owns
+// 128 consecutive pixels p of every slice: warp w computes the outputs
+// k = w, w+8, w+16, ... and lane q the pixels 4q..4q+3. Inputs stream through
+// shared memory 32 slices at a time; HBM traffic is one read of `in` (and
+// `prev`) and one write of `out`.
+#include "tc_device.cuh"
+
+namespace {
+
+constexpr int PB = 128;  // pixels per CTA
+constexpr int LC = 32;   // input slices per shared-memory stage
+
+template <int KPW>
+__global__ void __launch_bounds__(256)
+k_mode3(const float* __restrict__ in, float* out, const float* __restrict__ T, int n3,
+        size_t P, Epi ep) {
+  if (ep.skip && *ep.skip) return;
+  __shared__ __align__(16) float xs[LC][PB];
+  __shared__ float ts[LC][8 * KPW];
+  __shared__ float sh_coef[2];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const size_t p0 = (size_t)blockIdx.x * PB;
+  float acc[KPW][4];
+#pragma unroll
+  for (int q = 0; q < KPW; ++q)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
+
+  for (int l0 = 0; l0 < n3; l0 += LC) {
+    const int lc_n = min(LC, n3 - l0);
+    for (int idx = tid; idx < LC * PB; idx += 256) {
+      const int lc = idx / PB, px = idx % PB;
+      const size_t p = p0 + px;
+      xs[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
+    }
+    for (int idx = tid; idx < LC * 8 * KPW; idx += 256) {
+      const int lc = idx / (8 * KPW), k = idx % (8 * KPW);
+      ts[lc][k] = (lc < lc_n && k < n3) ? __ldg(T + (size_t)k * n3 + l0 + lc) : 0.f;
+    }
+    __syncthreads();
+    for (int lc = 0; lc < lc_n; ++lc) {
+      const float4 x = *reinterpret_cast<const float4*>(&xs[lc][lane * 4]);
+#pragma unroll
+      for (int q = 0; q < KPW; ++q) {
+        const float t = ts[lc][w + 8 * q];
+        acc[q][0] = fmaf(t, x.x, acc[q][0]);
+        acc[q][1] = fmaf(t, x.y, acc[q][1]);
+        acc[q][2] = fmaf(t, x.z, acc[q][2]);
+        acc[q][3] = fmaf(t, x.w, acc[q][3]);
+      }
+    }
+    __syncthreads();
+  }
+
+  coef_compute(ep.coef, sh_coef);
+  __syncthreads();
+  const float ca = sh_coef[0], cp = sh_coef[1];
+  float local = 0.f;
+#pragma unroll
+  for (int q = 0; q < KPW; ++q) {
+    const int k = w + 8 * q;
+    if (k >= n3) continue;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const size_t p = p0 + lane * 4 + e;
+      if (p < P) {
+        const size_t idx = (size_t)k * P + p;
+        float o = ca * acc[q][e];
+        if (ep.prev) o = fmaf(cp, ep.prev[idx], o);
+        out[idx] = o;
+        if (ep.red.out) local = fmaf(o, ep.red.other ? ep.red.other[idx] : o, local);
+      }
+    }
+  }
+  if (ep.red.out) reduce_finish((double)local, ep.red);
+}
+
+template <int KPW>
+int run(const float* in, float* out, const float* T, int n3, size_t P, const Epi& ep,
+        cudaStream_t st) {
+  const size_t blocks = (P + PB - 1) / PB;
+  k_mode3<KPW><<<(unsigned)blocks, 256, 0, st>>>(in, out, T, n3, P, ep);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+}  // namespace
+
+int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
+                 const Epi& ep, cudaStream_t st) {
+  TC_CHECK(n3 >= 1 && n3 <= TC_MAX_N3);
+  if (n3 <= 8) return run<1>(in, out, T_dev, n3, P, ep, st);
+  if (n3 <= 16) return run<2>(in, out, T_dev, n3, P, ep, st);
+  if (n3 <= 32) return run<4>(in, out, T_dev, n3, P, ep, st);
+  if (n3 <= 64) return run<8>(in, out, T_dev, n3, P, ep, st);
+  return run<16>(in, out, T_dev, n3, P, ep, st);
+}

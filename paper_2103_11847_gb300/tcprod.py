@@ -1,0 +1,231 @@
+"""ctypes binding of libtcprod (include/tcprod.h): argument marshalling only.
+
+Each ``tc_*`` function here calls the C function of the same name with the
+device pointers of CUDA torch tensors and the current torch stream. Nothing
+is computed in Python; if the library is missing the first call raises.
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+
+TC_OK, TC_EINVAL, TC_ECUDA, TC_EBREAKDOWN, TC_ENONFINITE, TC_ETIMEOUT, TC_ENOMEM, \
+    TC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+TC_FP32, TC_TF32, TC_BF16 = 0, 1, 2
+TC_GCV_PAPER, TC_GCV_FULL = 0, 1
+STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
+                TC_ENONFINITE: "nonfinite"}
+
+
+class tc_opts(ctypes.Structure):
+    _fields_ = [("precision", c_int), ("gcv_variant", c_int), ("use_graphs", c_int),
+                ("reserved", c_int * 5)]
+
+
+class tc_solve_info(ctypes.Structure):
+    _fields_ = [("iters", c_int), ("status", c_int), ("cycles", c_int), ("pad", c_int),
+                ("resid", c_double), ("lambda_", c_double), ("gcv", c_double),
+                ("beta1", c_double)]
+
+
+_SIGS = {
+    "tc_version": ([], ctypes.c_char_p),
+    "tc_last_error": ([], ctypes.c_char_p),
+    "tc_plan_create": ([ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_void_p, c_void_p,
+                        ctypes.POINTER(tc_opts), c_void_p], c_int),
+    "tc_plan_destroy": ([c_void_p], c_int),
+    "tc_cprod": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_cprod_adjoint": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_gkb_init": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int,
+                     c_void_p], c_int),
+    "tc_gkb_step": ([c_void_p, c_int, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+                    c_int),
+    "tc_lsqr_c": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_void_p,
+                   c_void_p, c_void_p], c_int),
+    "tc_gmres_c": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, c_double,
+                    c_void_p, c_void_p], c_int),
+    "tc_tikhonov_gcv": ([c_void_p, c_int, c_void_p, c_int, c_double, c_void_p, c_void_p,
+                         c_void_p, c_void_p], c_int),
+}
+
+_LIB = None
+
+
+def lib():
+    """Load libtcprod.so (built by build.build()); raise if it is missing."""
+    global _LIB
+    if _LIB is None:
+        path = _build.lib_path()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libtcprod.so is not built ({path}); run "
+                               "paper_2103_11847_gb300.build.build() first")
+        L = ctypes.CDLL(path)
+        for name, (args, res) in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = L
+    return _LIB
+
+
+class TcError(RuntimeError):
+    def __init__(self, fn, code):
+        msg = f"{fn} returned {code}"
+        if code == TC_ECUDA:
+            msg += ": " + lib().tc_last_error().decode()
+        super().__init__(msg)
+        self.code = code
+
+
+def _check(fn, code):
+    if code != TC_OK:
+        raise TcError(fn, code)
+
+
+def _ptr(t, dtype=torch.float32, shape=None, name="tensor"):
+    if t is None:
+        return None
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise ValueError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def tc_version():
+    return lib().tc_version().decode()
+
+
+def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
+                   use_graphs=True, stream=None):
+    """A: (n3, n1, n2); B: (n3, s, s) or None (then s must be given)."""
+    n3, n1, n2 = A.shape
+    if B is not None:
+        s = B.shape[1]
+        _ptr(B, shape=(n3, s, s), name="B")
+    if s is None:
+        raise ValueError("s (columns of X) is required for a one-sided plan")
+    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)))
+    h = c_void_p()
+    _check("tc_plan_create", lib().tc_plan_create(ctypes.byref(h), n1, n2, s, n3, _ptr(A, name="A"),
+                                                  _ptr(B, name="B"), ctypes.byref(o),
+                                                  _stream(stream)))
+    return h
+
+
+def tc_plan_destroy(h):
+    _check("tc_plan_destroy", lib().tc_plan_destroy(h))
+
+
+def tc_cprod(h, X, Y, stream=None):
+    _check("tc_cprod", lib().tc_cprod(h, _ptr(X, name="X"), _ptr(Y, name="Y"), _stream(stream)))
+
+
+def tc_cprod_adjoint(h, Y, X, stream=None):
+    _check("tc_cprod_adjoint", lib().tc_cprod_adjoint(h, _ptr(Y, name="Y"), _ptr(X, name="X"),
+                                                      _stream(stream)))
+
+
+def tc_gkb_init(h, C, U, V, alpha, beta, mmax, stream=None):
+    _check("tc_gkb_init", lib().tc_gkb_init(h, _ptr(C), _ptr(U), _ptr(V),
+                                            _ptr(alpha, torch.float64), _ptr(beta, torch.float64),
+                                            mmax, _stream(stream)))
+
+
+def tc_gkb_step(h, j, U, V, alpha, beta, mmax, stream=None):
+    _check("tc_gkb_step", lib().tc_gkb_step(h, j, _ptr(U), _ptr(V), _ptr(alpha, torch.float64),
+                                            _ptr(beta, torch.float64), mmax, _stream(stream)))
+
+
+def new_info():
+    """Device buffer for one tc_solve_info."""
+    return torch.zeros(ctypes.sizeof(tc_solve_info), dtype=torch.uint8, device="cuda")
+
+
+def read_info(buf):
+    raw = bytes(buf.cpu().numpy().tobytes())
+    info = tc_solve_info.from_buffer_copy(raw)
+    return dict(iters=info.iters, status=STATUS_NAMES.get(info.status, info.status),
+                cycles=info.cycles, resid=info.resid, lam=info.lambda_, gcv=info.gcv,
+                beta1=info.beta1)
+
+
+def tc_lsqr_c(h, C, X, X_reg, itermax, tol, lam, phibar_hist, info, stream=None):
+    _check("tc_lsqr_c", lib().tc_lsqr_c(h, _ptr(C), _ptr(X), _ptr(X_reg), itermax, tol,
+                                        -1.0 if lam is None else float(lam),
+                                        _ptr(phibar_hist, torch.float64),
+                                        _ptr(info, torch.uint8), _stream(stream)))
+
+
+def tc_gmres_c(h, C, X0, X, m, itermax, tol, lam, info, stream=None):
+    _check("tc_gmres_c", lib().tc_gmres_c(h, _ptr(C), _ptr(X0), _ptr(X), m, itermax, tol,
+                                          -1.0 if lam is None else float(lam),
+                                          _ptr(info, torch.uint8), _stream(stream)))
+
+
+def tc_tikhonov_gcv(H, k, beta, variant, lam, lambda_out, y, gcv_out, stream=None):
+    _check("tc_tikhonov_gcv", lib().tc_tikhonov_gcv(
+        _ptr(H, torch.float64), k, _ptr(beta, torch.float64), variant,
+        -1.0 if lam is None else float(lam), _ptr(lambda_out, torch.float64),
+        _ptr(y, torch.float64), _ptr(gcv_out, torch.float64), _stream(stream)))
+
+
+class Plan:
+    """Owns a tc_plan for A (and B); methods allocate outputs as torch tensors."""
+
+    def __init__(self, A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
+                 use_graphs=True):
+        self.n3, self.n1, self.n2 = A.shape
+        self.s = B.shape[1] if B is not None else s
+        self.two_sided = B is not None
+        self.handle = tc_plan_create(A, B, s, precision, gcv_variant, use_graphs)
+
+    def close(self):
+        if self.handle is not None:
+            tc_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def xshape(self):
+        return (self.n3, self.n2, self.s)
+
+    def yshape(self):
+        return (self.n3, self.n1, self.s)
+
+    def cprod(self, X, out=None):
+        Y = out if out is not None else torch.empty(self.yshape(), device="cuda")
+        tc_cprod(self.handle, X, Y)
+        return Y
+
+    def adjoint(self, Y, out=None):
+        X = out if out is not None else torch.empty(self.xshape(), device="cuda")
+        tc_cprod_adjoint(self.handle, Y, X)
+        return X
+
+    def lsqr(self, C, itermax, tol=0.0, regularize=False, lam=None, history=False):
+        X = torch.empty(self.xshape(), device="cuda")
+        Xr = torch.empty(self.xshape(), device="cuda") if regularize else None
+        hist = torch.zeros(itermax, dtype=torch.float64, device="cuda") if history else None
+        info = new_info()
+        tc_lsqr_c(self.handle, C, X, Xr, itermax, tol, lam, hist, info)
+        return X, Xr, hist, info
+
+    def gmres(self, C, m, itermax, tol=0.0, lam=None, X0=None):
+        X = torch.empty(self.xshape(), device="cuda")
+        info = new_info()
+        tc_gmres_c(self.handle, C, X0, X, m, itermax, tol, lam, info)
+        return X, info
