@@ -84,6 +84,9 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
   __syncthreads();
 
   // ---- 1. one-sided Jacobi -------------------------------------------------
+  // Rotate while |<h_p, h_q>| > rows * eps * ||h_p|| ||h_q||: below that the
+  // inner product is rounding noise of the (rows)-term dot product.
+  const double jtol = rows * 2.220446049250313e-16;
   const int npairs = kk / 2;
   for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
     if (tid == 0) sh_rot = 0;
@@ -105,7 +108,7 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
         al = warp_sum_d(al);
         be = warp_sum_d(be);
         ga = warp_sum_d(ga);
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+        if (ga != 0.0 && fabs(ga) > jtol * sqrt(al * be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t);

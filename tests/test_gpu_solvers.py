@@ -54,27 +54,54 @@ def oracle_ops(A, B):
     return (lambda X: cp.cprod(A, X, B)), (lambda Y: cp.cprod_adjoint(A, Y, B))
 
 
+# FP32 envelope. The paper's Golub-Kahan process has no reorthogonalisation.
+# On the 64x64x3 colour deblur, any FP32 execution of Algorithm 6 leaves the
+# FP64 trajectory once Ritz values converge. A CPU emulation of the same
+# recurrence in FP32 matches FP64 to 2.6e-7 at 15 iterations, but differs by
+# 3.6e-3 at 20 and by 0.106 at 30. This holds with FP32 products and FP64
+# vectors, and with FP64 products and FP32 vectors. Parity to 1e-3 is
+# therefore checked at 15 iterations. At the full 30 the check is the
+# envelope plus LSQR's own residual identity.
 @pytest.mark.parametrize("use_graphs", [True, False])
 def test_lsqr_gcv_colour_64(tc, use_graphs):
-    # 64x64x3 colour deblur, 30 iterations of c-LSQR then Tikhonov/GCV.
+    # 64x64x3 colour deblur: 15 iterations of c-LSQR, then Tikhonov/GCV.
     w = inputs.colour_deblur(n=64, seed=0)
     A, B, C = observe(w)
-    ref = kr.lsqr_gcv(*oracle_ops(A, B), C, itermax=30)
+    ref = kr.lsqr_gcv(*oracle_ops(A, B), C, itermax=15)
     plan = tc.Plan(dev(A), s=64, use_graphs=use_graphs)
     for _ in range(2):  # the second call replays the captured graph
-        X, Xr, hist, info = plan.lsqr(dev(C), 30, regularize=True, history=True)
+        X, Xr, hist, info = plan.lsqr(dev(C), 15, regularize=True, history=True)
         torch.cuda.synchronize()
         inf = tc.read_info(info)
-        assert inf["iters"] == 30 and inf["status"] == "maxiter"
+        assert inf["iters"] == 15 and inf["status"] == "maxiter"
         assert rel(X.cpu().numpy(), ref["X"]) < 1e-3
-        assert np.allclose(hist.cpu().numpy(), ref["phibar"], rtol=1e-3)
-        assert abs(inf["resid"] - ref["phibar"][-1]) < 1e-3 * ref["phibar"][-1]
+        assert np.allclose(hist.cpu().numpy(), ref["phibar"], rtol=1e-4)
+        assert abs(inf["resid"] - ref["phibar"][-1]) < 1e-4 * ref["phibar"][-1]
         assert abs(inf["lam"] - ref["lam"]) < 1e-3 * ref["lam"]
         e_gpu = mt.relative_error(w["X_true"], Xr.cpu().numpy())
         e_ref = mt.relative_error(w["X_true"], ref["X_reg"])
         assert abs(e_gpu - e_ref) < 0.01 * e_ref
         assert rel(Xr.cpu().numpy(), ref["X_reg"]) < 1e-3
     plan.close()
+
+
+def test_lsqr_colour_64_full_length_envelope(tc):
+    # 30 iterations: the FP32 envelope above (0.106 for a CPU FP32 run); the
+    # GPU's residual |phibar| must equal ||C - A X|| recomputed by the oracle.
+    w = inputs.colour_deblur(n=64, seed=0)
+    A, B, C = observe(w)
+    ref = kr.lsqr(*oracle_ops(A, B), C, itermax=30)
+    plan = tc.Plan(dev(A), s=64)
+    X, Xr, hist, info = plan.lsqr(dev(C), 30, regularize=True, history=True)
+    torch.cuda.synchronize()
+    inf = tc.read_info(info)
+    Xg = X.cpu().numpy().astype(np.float64)
+    assert inf["iters"] == 30
+    assert rel(Xg, ref["X"]) < 0.2
+    r_true = np.linalg.norm(C - cp.cprod(A, Xg, B))
+    assert abs(inf["resid"] - r_true) < 2e-2 * r_true
+    h = hist.cpu().numpy()
+    assert np.all(np.diff(h) <= 1e-6 * h[0])  # |phibar| never increases
 
 
 def test_lsqr_two_sided_256(tc):
@@ -109,20 +136,25 @@ def test_lsqr_ragged_and_unfused(tc, n1, n2, s, n3):
 
 
 def test_lsqr_tolerance_stop(tc):
+    # Well-conditioned problem. tol is the geometric mean of two consecutive
+    # oracle residuals with a wide gap, so FP32 and FP64 stop at the same step.
     rng = np.random.default_rng(4)
     n, n3, s = 24, 3, 8
-    A = rng.standard_normal((n3, n, n)) * 0.1
+    A = rng.standard_normal((n3, n, n)) * 0.01
     A[0] += np.eye(n) * 2.0
     A = f32(A).astype(np.float64)
     C = f32(rng.standard_normal((n3, n, s))).astype(np.float64)
-    tol = 1e-3 * np.linalg.norm(C)
+    full = kr.lsqr(*oracle_ops(A, None), C, itermax=40)
+    ph = full["phibar"]
+    k = int(np.argmax(ph < 1e-4 * ph[0]))
+    tol = float(np.sqrt(ph[k] * ph[k - 1]))
     ref = kr.lsqr(*oracle_ops(A, None), C, itermax=40, tol=tol)
     plan = tc.Plan(dev(A), s=s)
     X, _, _, info = plan.lsqr(dev(C), 40, tol=tol)
     torch.cuda.synchronize()
     inf = tc.read_info(info)
     assert inf["status"] == "converged" and ref["status"] == "converged"
-    assert inf["iters"] == ref["iters"]
+    assert inf["iters"] == ref["iters"] == k + 1
     assert rel(X.cpu().numpy(), ref["X"]) < 1e-4
 
 
@@ -217,11 +249,18 @@ def test_tikhonov_gcv_kernel(tc, variant, k):
     y = torch.zeros(k, dtype=torch.float64, device="cuda")
     tc.tc_tikhonov_gcv(dH, k, db, variant, None, lo, y, go)
     torch.cuda.synchronize()
-    assert abs(lo.item() - lam_ref) <= 1e-6 * lam_ref
     assert abs(go.item() - g_ref) <= 1e-8 * abs(g_ref)
-    assert np.allclose(y.cpu().numpy(), y_ref, rtol=1e-6, atol=1e-9 * np.abs(y_ref).max())
+    if k == 1 and variant == 0:
+        # eq. (gcv2) with one singular value is g~_1^2 for every lambda: any
+        # lambda is a minimiser, so only the value is compared.
+        sig, g = rg.svd_projected(H, b)
+        assert abs(go.item() - g[0] ** 2) <= 1e-10 * g[0] ** 2
+    else:
+        assert abs(lo.item() - lam_ref) <= 1e-6 * lam_ref
+        assert np.allclose(y.cpu().numpy(), y_ref, rtol=1e-6, atol=1e-9 * np.abs(y_ref).max())
     tc.tc_tikhonov_gcv(dH, k, db, variant, 0.3, lo, y, go)
     torch.cuda.synchronize()
     _, y_fix, g_fix = rg.tikhonov_gcv(H, b, name, lam=0.3)
     assert lo.item() == 0.3
     assert np.allclose(y.cpu().numpy(), y_fix, rtol=1e-9, atol=1e-12)
+    assert abs(go.item() - g_fix) <= 1e-9 * abs(g_fix)
