@@ -66,7 +66,7 @@ def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True):
     per_product = (2 if two_sided else 1) if fused else (4 if two_sided else 3)
     init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
     per_iter = 2 * per_product + 2
-    tail = (3 if keep_basis else 0) + 1
+    tail = (5 if keep_basis else 0) + 1  # 3 GCV grid levels, final, combine; info
     return init + iters * per_iter + tail
 
 

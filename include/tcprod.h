@@ -33,6 +33,8 @@
 #ifndef TCPROD_H
 #define TCPROD_H
 
+#include <stddef.h>
+
 #ifdef __cplusplus
 extern "C" {
 #endif
@@ -86,7 +88,8 @@ typedef struct {
   double beta1;  /* ||C||_F */
 } tc_solve_info;
 
-/* Library version string and the message of the last TC_ECUDA on this thread. */
+/* Library version string, and the message of the last TC_ECUDA (or of a
+ * TC_EINVAL whose reason is not obvious) on this thread. */
 const char* tc_version(void);
 const char* tc_last_error(void);
 
@@ -95,7 +98,7 @@ const char* tc_last_error(void);
  * device memory it allocates (freed by tc_plan_destroy).
  *   A: device, n1 x n2 x n3.   B: device s x s x n3, or NULL for A *c X.
  *   opts: may be NULL (FP32, paper GCV, graphs on).
- * Sizes must be >= 1; n3 <= 256. Synchronises `stream` before returning.
+ * Sizes must be >= 1; n3 <= 128. Synchronises `stream` before returning.
  * Source: Remark 2.1 and eqs. (dft9), (dft8), §2.2. */
 int tc_plan_create(tc_plan** plan, int n1, int n2, int s, int n3,
                    const float* A, const float* B, const tc_opts* opts,
@@ -127,7 +130,8 @@ int tc_gkb_step(tc_plan* plan, int j, float* U, float* V, double* alpha,
 /* DC-LSQR, Algorithm 6 (§3.3), from X_0 = 0, then optionally Tikhonov/GCV on
  * the projected bidiagonal C~_k (§3.2, eqs. (normeq2), (gcv2), (xmlsqr)).
  *   C: device n1 x s x n3.   X: device n2 x s x n3, the LSQR iterate X_k.
- *   X_reg: device n2 x s x n3 or NULL. If given, the basis V_1..V_k is kept and
+ *   X_reg: device n2 x s x n3 or NULL. If given (then itermax <= 128), the
+ *     basis V_1..V_k is kept in plan workspace and
  *     X_reg = V_k (*) y_lambda with lambda = `lambda` if it is >= 0, else the
  *     GCV minimiser (opts.gcv_variant).
  *   itermax: 1 .. 4096.  tol: stop when |phibar_{j+1}| < tol (0: never).
@@ -140,17 +144,27 @@ int tc_lsqr_c(tc_plan* plan, const float* C, float* X, float* X_reg,
 /* Restarted DC-GMRES(m) with Tikhonov/GCV, Algorithms 2 and 3 (§3.1).
  * Needs a square operator: n1 == n2 (the input and output shapes agree).
  *   C: device n1 x s x n3.  X0: device or NULL (zero).  X: device, the result.
- *   m: restart length 1 .. 256.  itermax: total Arnoldi steps.
+ *   m: restart length 1 .. 128.  itermax: total Arnoldi steps.
  *   lambda >= 0 fixes lambda; < 0 chooses it by GCV each cycle.
  *   info: device tc_solve_info (required). */
 int tc_gmres_c(tc_plan* plan, const float* C, const float* X0, float* X,
                int m, int itermax, double tol, double lambda,
                tc_solve_info* info, tc_stream_t stream);
 
+/* Step 2 of Algorithm 1 alone: the n3 frontal-slice products in the transform
+ * domain, Y~_k = A~_k X~_k (adjoint = 0) or Y~_k = A~_k^T X~_k (adjoint = 1),
+ * with A~ = A x_3 M held by the plan (eqs. (dft9), (dft8)). One-sided plans only.
+ *   Xh: device, n3 slices of K x s (K = n2, or n1 for the adjoint), in the
+ *       plan's GEMM input type: FP32 for TC_FP32 plans, BF16 for TC_BF16, FP32
+ *       already rounded to TF32 for TC_TF32.
+ *   Yh: device FP32, n3 slices of M x s (M = n1, or n2 for the adjoint).
+ * On the tensor-core forms this is one tcgen05 GEMM launch. */
+int tc_slice_gemm(tc_plan* plan, const void* Xh, float* Yh, int adjoint, tc_stream_t stream);
+
 /* Tikhonov solution of a projected problem with GCV (§3.1, eqs. (leastsq),
  * (tikho2), (gcv2)): y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
  *   H: device double, (k+1) x k row-major (Hessenberg or lower bidiagonal).
- *   k: 1 .. 256.   beta: device double scalar.
+ *   k: 1 .. 128.   beta: device double scalar.
  *   lambda_in >= 0 fixes lambda; < 0 minimises GCV (variant tc_gcv_variant).
  *   lambda_out: device double.  y: device double[k].  gcv_out: device or NULL. */
 int tc_tikhonov_gcv(const double* H, int k, const double* beta, int variant,

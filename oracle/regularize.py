@@ -18,18 +18,20 @@ Readings:
     GCV of the rectangular (m+1) x m problem ("full") is
       (sum_i (lambda^2 g~_i / (s_i^2 + lambda^2))^2 + g~_{m+1}^2)
       / (1 + sum_i lambda^2 / (s_i^2 + lambda^2))^2.
-  * The paper does not say how GCV is minimised. Here: 200 log-spaced points
-    on [lo, s_max] with lo = 1e-3 s_min (or 1e-12 s_max when s_min is 0), the
-    smallest value taken (first index on ties), then 40 golden-section steps
-    in log(lambda) on the bracket formed by the two grid neighbours.
+  * The paper does not say how GCV is minimised. Here: three nested log grids
+    of 200 points. Level 0 spans [1e-10 s, s] with s = ||H||_F (an upper
+    bound of sigma_max that needs no SVD). Each later level spans the two
+    grid neighbours of the previous level's minimum (first index on ties).
+    The answer is the last level's minimum; its spacing is 1.2e-5 in
+    log(lambda).
   * The Tikhonov weight is lambda^2 (eqs. (leastsq), (tikho2)), not the lambda of
     eq. (tr2); the reported parameter is lambda.
 """
 import numpy as np
 
 GRID_POINTS = 200
-GOLDEN_STEPS = 40
-LO_FACTOR = 1e-3
+GRID_LEVELS = 3
+GRID_DECADES = 10.0
 
 
 def svd_projected(H, beta):
@@ -58,38 +60,18 @@ def gcv_value(sig, g, lam, variant="paper"):
 
 
 def gcv_minimize(H, beta, variant="paper"):
-    """lambda minimising GCV for the projected matrix H (m+1 x m) and beta.
-
-    Log grid, then golden-section refinement in log(lambda) (reading above)."""
+    """lambda minimising GCV for the projected matrix H (m+1 x m) and beta,
+    by the nested log grids described above."""
     sig, g = svd_projected(H, beta)
-    smax = float(sig[0])
-    smin = float(sig[-1])
-    lo = LO_FACTOR * smin if smin > 0.0 else 1e-12 * smax
-    grid = np.exp(np.linspace(np.log(lo), np.log(smax), GRID_POINTS))
-    vals = np.array([gcv_value(sig, g, t, variant) for t in grid])
-    i = int(np.argmin(vals))
-    a = np.log(grid[max(i - 1, 0)])
-    b = np.log(grid[min(i + 1, GRID_POINTS - 1)])
-    invphi = (np.sqrt(5.0) - 1.0) / 2.0
-    c = b - invphi * (b - a)
-    d = a + invphi * (b - a)
-    fc = gcv_value(sig, g, np.exp(c), variant)
-    fd = gcv_value(sig, g, np.exp(d), variant)
-    for _ in range(GOLDEN_STEPS):
-        if fc <= fd:
-            b, d, fd = d, c, fc
-            c = b - invphi * (b - a)
-            fc = gcv_value(sig, g, np.exp(c), variant)
-        else:
-            a, c, fc = c, d, fd
-            d = a + invphi * (b - a)
-            fd = gcv_value(sig, g, np.exp(d), variant)
-    t = c if fc <= fd else d
-    best = min(fc, fd)
-    # keep the grid point if the refinement did not improve on it
-    if vals[i] < best:
-        return float(grid[i]), float(vals[i])
-    return float(np.exp(t)), float(best)
+    s = float(np.linalg.norm(np.asarray(H, np.float64)))
+    lo, hi = np.log(s) - GRID_DECADES * np.log(10.0), np.log(s)
+    for _ in range(GRID_LEVELS):
+        lams = np.exp(np.linspace(lo, hi, GRID_POINTS))
+        vals = np.array([gcv_value(sig, g, t, variant) for t in lams])
+        b = int(np.argmin(vals))
+        lo = np.log(lams[max(b - 1, 0)])
+        hi = np.log(lams[min(b + 1, GRID_POINTS - 1)])
+    return float(lams[b]), float(vals[b])
 
 
 def tikhonov_solve(H, beta, lam):

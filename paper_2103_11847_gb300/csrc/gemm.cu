@@ -1,12 +1,23 @@
 // Frontal-slice GEMMs of the c-product (Algorithm 1, step 2; eqs. (dft9),
-// (dft8)), FP32 on the FFMA pipe, with the mode-3 transform of Remark 2.1
-// fused in when n3 <= TC_MAX_FUSED:
+// (dft8)), FP32 on the FFMA pipe.
+//
+// Fused form (n3 <= TC_MAX_FUSED): one output tile (i, j) for all n3 slices
+// per CTA, with the mode-3 transform of Remark 2.1 fused in:
 //   prologue  B~_k = sum_l pro[k][l] B_l        (the operand's transform)
 //   epilogue  Y_l  = sum_k epi[l][k] (A_k B~_k)  (back to the spatial domain)
-// followed by out = ca * Y + cp * prev and an optional fused reduction.
-// One CTA owns an (i, j) output tile for NS slices; with the transforms fused
-// it owns all n3 slices, so the epilogue transform needs no other CTA.
+// then out = ca * Y + cp * prev and an optional fused reduction. Small slices
+// (a 256 x 256 image has only 64 tiles of 32 x 32) are split along K over a
+// thread-block cluster of KS CTAs: each CTA accumulates its K range, the
+// partial tiles are summed through distributed shared memory in rank order,
+// and each rank finishes BM/KS rows of the tile.
+//
+// Per-slice form (no transforms): one tile of one slice per CTA, used when
+// n3 > TC_MAX_FUSED between separate transform passes.
+#include <cooperative_groups.h>
+
 #include "tc_device.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace {
 
@@ -15,24 +26,37 @@ struct Fused {
   float epi[TC_MAX_FUSED * TC_MAX_FUSED];
 };
 
-template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI>
+template <int NS, int BM, int BN, int BK, bool SPLIT>
+struct Smem {
+  static constexpr int kMain = NS * BK * (BM + BN);
+  static constexpr int kPart = SPLIT ? NS * BM * BN : 0;
+  static constexpr int kFloats = kMain > kPart ? kMain : kPart;
+};
+
+// SPLIT: K is split over the cluster and the epilogue runs from the summed
+// partial tiles; otherwise (cluster of one) it runs from the registers.
+template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI, bool SPLIT>
 __global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_slice_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
-             int M, int N, int K, Fused f, Epi ep) {
+k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C, int M, int N,
+             int K, int kchunk, Fused f, Epi ep) {
   constexpr int TX = BN / TN;
   constexpr int NT = (BM / TM) * (BN / TN);
   if (ep.skip && *ep.skip) return;
-  __shared__ float As[NS][BK][BM];
-  __shared__ __align__(16) float Bs[NS][BK][BN];
+  __shared__ __align__(16) float sm[Smem<NS, BM, BN, BK, SPLIT>::kFloats];
   __shared__ float sh_coef[2];
+  float(*As)[BK][BM] = reinterpret_cast<float(*)[BK][BM]>(sm);
+  float(*Bs)[BK][BN] = reinterpret_cast<float(*)[BK][BN]>(sm + NS * BK * BM);
+  float* P = sm;  // partial tile [NS][BM][BN] after the main loop
 
+  cg::cluster_group cluster = cg::this_cluster();
+  const int KS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
   const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const int z0 = blockIdx.z * NS;
   const size_t sA = (size_t)M * K, sB = (size_t)K * N, sC = (size_t)M * N;
-  const float* Ab = A + z0 * sA;
-  const float* Bb = B + z0 * sB;
+  const int kbeg = rank * kchunk;
+  const int kend = min(K, kbeg + kchunk);
 
   float acc[NS][TM][TN];
 #pragma unroll
@@ -42,22 +66,21 @@ k_slice_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[k][i][j] = 0.f;
 
-  for (int k0 = 0; k0 < K; k0 += BK) {
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
     for (int idx = tid; idx < BM * BK; idx += NT) {
       const int r = idx / BK, c = idx % BK;
       const int gi = i0 + r, gk = k0 + c;
-      const bool ok = gi < M && gk < K;
+      const bool ok = gi < M && gk < kend;
 #pragma unroll
-      for (int k = 0; k < NS; ++k)
-        As[k][c][r] = ok ? __ldg(Ab + k * sA + (size_t)gi * K + gk) : 0.f;
+      for (int k = 0; k < NS; ++k) As[k][c][r] = ok ? __ldg(A + k * sA + (size_t)gi * K + gk) : 0.f;
     }
     for (int idx = tid; idx < BK * BN; idx += NT) {
       const int r = idx / BN, c = idx % BN;
       const int gk = k0 + r, gj = j0 + c;
-      const bool ok = gk < K && gj < N;
+      const bool ok = gk < kend && gj < N;
       float b[NS];
 #pragma unroll
-      for (int l = 0; l < NS; ++l) b[l] = ok ? __ldg(Bb + l * sB + (size_t)gk * N + gj) : 0.f;
+      for (int l = 0; l < NS; ++l) b[l] = ok ? __ldg(B + l * sB + (size_t)gk * N + gj) : 0.f;
       if (PRO) {
 #pragma unroll
         for (int k = 0; k < NS; ++k) {
@@ -90,65 +113,185 @@ k_slice_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
     __syncthreads();
   }
 
+  if (!SPLIT) {
+    coef_compute(ep.coef, sh_coef);
+    __syncthreads();
+    const float ca = sh_coef[0], cp = sh_coef[1];
+    float local = 0.f;
+#pragma unroll
+    for (int i = 0; i < TM; ++i) {
+      const int row = i0 + ty * TM + i;
+#pragma unroll
+      for (int j = 0; j < TN; ++j) {
+        const int col = j0 + tx * TN + j;
+        if (row < M && col < N) {
+#pragma unroll
+          for (int l = 0; l < NS; ++l) {
+            float y;
+            if (EPI) {
+              y = 0.f;
+#pragma unroll
+              for (int k = 0; k < NS; ++k) y = fmaf(f.epi[l * NS + k], acc[k][i][j], y);
+            } else {
+              y = acc[l][i][j];
+            }
+            const size_t o = (size_t)l * sC + (size_t)row * N + col;
+            float out = ca * y;
+            if (ep.prev) out = fmaf(cp, ep.prev[o], out);
+            C[o] = out;
+            if (ep.red.out) local = fmaf(out, ep.red.other ? ep.red.other[o] : out, local);
+          }
+        }
+      }
+    }
+    if (ep.red.out) reduce_finish((double)local, ep.red);
+    return;
+  }
+  // partial tile to shared memory, then sum over the cluster's K ranges
+#pragma unroll
+  for (int k = 0; k < NS; ++k)
+#pragma unroll
+    for (int i = 0; i < TM; ++i)
+#pragma unroll
+      for (int j = 0; j < TN; ++j) P[(k * BM + ty * TM + i) * BN + tx * TN + j] = acc[k][i][j];
   coef_compute(ep.coef, sh_coef);
-  __syncthreads();
+  cluster.sync();
   const float ca = sh_coef[0], cp = sh_coef[1];
+  const int rows = BM / KS;  // this rank finishes rows [rank*rows, (rank+1)*rows)
   float local = 0.f;
+  for (int idx = tid; idx < rows * BN; idx += NT) {
+    const int lr = rank * rows + idx / BN, lc = idx % BN;
+    const int row = i0 + lr, col = j0 + lc;
+    float v[NS];
+#pragma unroll
+    for (int k = 0; k < NS; ++k) v[k] = 0.f;
+    for (int q = 0; q < KS; ++q) {
+      const float* Pq = cluster.map_shared_rank(P, q);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) v[k] += Pq[(k * BM + lr) * BN + lc];
+    }
+    if (row < M && col < N) {
+#pragma unroll
+      for (int l = 0; l < NS; ++l) {
+        float y;
+        if (EPI) {
+          y = 0.f;
+#pragma unroll
+          for (int k = 0; k < NS; ++k) y = fmaf(f.epi[l * NS + k], v[k], y);
+        } else {
+          y = v[l];
+        }
+        const size_t o = (size_t)l * sC + (size_t)row * N + col;
+        float out = ca * y;
+        if (ep.prev) out = fmaf(cp, ep.prev[o], out);
+        C[o] = out;
+        if (ep.red.out) local = fmaf(out, ep.red.other ? ep.red.other[o] : out, local);
+      }
+    }
+  }
+  cluster.sync();  // peers may still read this CTA's partial tile until here
+  if (ep.red.out) reduce_finish((double)local, ep.red);
+}
+
+// Per-slice GEMM without transforms: C_z = A_z B_z for slice z = blockIdx.z.
+template <int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_slice_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C, int M, int N,
+             int K, const int* skip) {
+  constexpr int TX = BN / TN;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  if (skip && *skip) return;
+  __shared__ float As[BK][BM];
+  __shared__ __align__(16) float Bs[BK][BN];
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const float* Ab = A + (size_t)blockIdx.z * M * K;
+  const float* Bb = B + (size_t)blockIdx.z * K * N;
+  float acc[TM][TN];
+#pragma unroll
+  for (int i = 0; i < TM; ++i)
+#pragma unroll
+    for (int j = 0; j < TN; ++j) acc[i][j] = 0.f;
+  for (int k0 = 0; k0 < K; k0 += BK) {
+    for (int idx = tid; idx < BM * BK; idx += NT) {
+      const int r = idx / BK, c = idx % BK;
+      const int gi = i0 + r, gk = k0 + c;
+      As[c][r] = (gi < M && gk < K) ? __ldg(Ab + (size_t)gi * K + gk) : 0.f;
+    }
+    for (int idx = tid; idx < BK * BN; idx += NT) {
+      const int r = idx / BN, c = idx % BN;
+      const int gk = k0 + r, gj = j0 + c;
+      Bs[r][c] = (gk < K && gj < N) ? __ldg(Bb + (size_t)gk * N + gj) : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < BK; ++kk) {
+      float a[TM], b[TN];
+#pragma unroll
+      for (int i = 0; i < TM; ++i) a[i] = As[kk][ty * TM + i];
+#pragma unroll
+      for (int j = 0; j < TN; ++j) b[j] = Bs[kk][tx * TN + j];
+#pragma unroll
+      for (int i = 0; i < TM; ++i)
+#pragma unroll
+        for (int j = 0; j < TN; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+  float* Cb = C + (size_t)blockIdx.z * M * N;
 #pragma unroll
   for (int i = 0; i < TM; ++i) {
     const int row = i0 + ty * TM + i;
 #pragma unroll
     for (int j = 0; j < TN; ++j) {
       const int col = j0 + tx * TN + j;
-      if (row < M && col < N) {
-#pragma unroll
-        for (int l = 0; l < NS; ++l) {
-          float v;
-          if (EPI) {
-            v = 0.f;
-#pragma unroll
-            for (int k = 0; k < NS; ++k) v = fmaf(f.epi[l * NS + k], acc[k][i][j], v);
-          } else {
-            v = acc[l][i][j];
-          }
-          const size_t idx = (size_t)(z0 + l) * sC + (size_t)row * N + col;
-          float o = ca * v;
-          if (ep.prev) o = fmaf(cp, ep.prev[idx], o);
-          C[idx] = o;
-          if (ep.red.out) local = fmaf(o, ep.red.other ? ep.red.other[idx] : o, local);
-        }
-      }
+      if (row < M && col < N) Cb[(size_t)row * N + col] = acc[i][j];
     }
   }
-  if (ep.red.out) reduce_finish((double)local, ep.red);
 }
 
-template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI>
-int run(const float* A, const float* B, float* C, int M, int N, int K, int nslices,
-        const Fused& f, const Epi& ep, cudaStream_t st) {
-  dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, nslices / NS);
-  dim3 block((BM / TM) * (BN / TN));
-  k_slice_gemm<NS, BM, BN, BK, TM, TN, PRO, EPI><<<grid, block, 0, st>>>(A, B, C, M, N, K, f, ep);
-  TC_CUDA(cudaGetLastError());
+template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI, bool SPLIT>
+int run_fused(const float* A, const float* B, float* C, int M, int N, int K, const Fused& f,
+              const Epi& ep, cudaStream_t st) {
+  const long tiles = (long)((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+  // split K over a cluster until the grid covers every SM, keeping >= 2 K tiles per CTA
+  int KS = 1;
+  while (SPLIT && KS < 8 && tiles * KS < 152 && K >= 2 * BK * (KS * 2)) KS *= 2;
+  const int kchunk = (((K + KS - 1) / KS) + BK - 1) / BK * BK;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((N + BN - 1) / BN, (M + BM - 1) / BM, KS);
+  cfg.blockDim = dim3((BM / TM) * (BN / TN));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 1;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = KS;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TC_CUDA(cudaLaunchKernelEx(&cfg, k_fused_gemm<NS, BM, BN, BK, TM, TN, PRO, EPI, SPLIT>, A, B, C,
+                             M, N, K, kchunk, f, ep));
   return TC_OK;
 }
 
 template <int NS, bool PRO, bool EPI>
-int pick_tile(const float* A, const float* B, float* C, int M, int N, int K, int nslices,
-              const Fused& f, const Epi& ep, cudaStream_t st) {
-  const long big = (long)((M + 63) / 64) * ((N + 63) / 64) * (nslices / NS);
-  if (big >= 2 * 152)
-    return run<NS, 64, 64, 16, 4, 4, PRO, EPI>(A, B, C, M, N, K, nslices, f, ep, st);
-  return run<NS, 32, 32, 16, 2, 2, PRO, EPI>(A, B, C, M, N, K, nslices, f, ep, st);
+int pick_tile(const float* A, const float* B, float* C, int M, int N, int K, const Fused& f,
+              const Epi& ep, cudaStream_t st) {
+  const long big = (long)((M + 63) / 64) * ((N + 63) / 64);
+  if (big >= 152)
+    return run_fused<NS, 64, 64, 16, 4, 4, PRO, EPI, false>(A, B, C, M, N, K, f, ep, st);
+  return run_fused<NS, 32, 32, 16, 4, 2, PRO, EPI, true>(A, B, C, M, N, K, f, ep, st);
 }
 
 template <int NS>
 int pick_flags(bool pro, bool epi, const float* A, const float* B, float* C, int M, int N,
-               int K, int nslices, const Fused& f, const Epi& ep, cudaStream_t st) {
-  if (pro && epi) return pick_tile<NS, true, true>(A, B, C, M, N, K, nslices, f, ep, st);
-  if (pro) return pick_tile<NS, true, false>(A, B, C, M, N, K, nslices, f, ep, st);
-  if (epi) return pick_tile<NS, false, true>(A, B, C, M, N, K, nslices, f, ep, st);
-  return pick_tile<NS, false, false>(A, B, C, M, N, K, nslices, f, ep, st);
+               int K, const Fused& f, const Epi& ep, cudaStream_t st) {
+  if (pro && epi) return pick_tile<NS, true, true>(A, B, C, M, N, K, f, ep, st);
+  if (pro) return pick_tile<NS, true, false>(A, B, C, M, N, K, f, ep, st);
+  if (epi) return pick_tile<NS, false, true>(A, B, C, M, N, K, f, ep, st);
+  return pick_tile<NS, false, false>(A, B, C, M, N, K, f, ep, st);
 }
 
 }  // namespace
@@ -156,21 +299,31 @@ int pick_flags(bool pro, bool epi, const float* A, const float* B, float* C, int
 int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, int K,
                       int nslices, const float* pro, const float* epi, const Epi& ep,
                       cudaStream_t st) {
-  Fused f{};
-  const bool fused = (pro || epi);
-  if (fused) {
+  if (pro || epi) {
     TC_CHECK(nslices <= TC_MAX_FUSED);
+    Fused f{};
     for (int i = 0; i < nslices * nslices; ++i) {
       f.pro[i] = pro ? pro[i] : 0.f;
       f.epi[i] = epi ? epi[i] : 0.f;
     }
     switch (nslices) {
-      case 1: return pick_flags<1>(pro, epi, A, B, C, M, N, K, 1, f, ep, st);
-      case 2: return pick_flags<2>(pro, epi, A, B, C, M, N, K, 2, f, ep, st);
-      case 3: return pick_flags<3>(pro, epi, A, B, C, M, N, K, 3, f, ep, st);
-      case 4: return pick_flags<4>(pro, epi, A, B, C, M, N, K, 4, f, ep, st);
+      case 1: return pick_flags<1>(pro, epi, A, B, C, M, N, K, f, ep, st);
+      case 2: return pick_flags<2>(pro, epi, A, B, C, M, N, K, f, ep, st);
+      case 3: return pick_flags<3>(pro, epi, A, B, C, M, N, K, f, ep, st);
+      case 4: return pick_flags<4>(pro, epi, A, B, C, M, N, K, f, ep, st);
       default: return TC_EINVAL;
     }
   }
-  return pick_tile<1, false, false>(A, B, C, M, N, K, nslices, f, ep, st);
+  // per-slice GEMM between transform passes: no epilogue beyond the store
+  TC_CHECK(ep.prev == nullptr && ep.red.out == nullptr && ep.coef.rule == COEF_ONE);
+  const long big = (long)((M + 63) / 64) * ((N + 63) / 64) * nslices;
+  if (big >= 2 * 152) {
+    dim3 grid((N + 63) / 64, (M + 63) / 64, nslices);
+    k_slice_gemm<64, 64, 16, 4, 4><<<grid, 256, 0, st>>>(A, B, C, M, N, K, ep.skip);
+  } else {
+    dim3 grid((N + 31) / 32, (M + 31) / 32, nslices);
+    k_slice_gemm<32, 32, 16, 4, 2><<<grid, 128, 0, st>>>(A, B, C, M, N, K, ep.skip);
+  }
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
 }

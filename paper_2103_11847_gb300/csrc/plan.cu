@@ -7,6 +7,7 @@
 #include <vector>
 
 #include "tc_device.cuh"
+#include "umma.cuh"
 
 namespace {
 thread_local char g_err[512] = "";
@@ -81,7 +82,8 @@ void dfree(void* p) {
   if (p) cudaFree(p);
 }
 
-bool fused(const tc_plan* p) { return p->n3 <= TC_MAX_FUSED; }
+bool fused(const tc_plan* p) { return p->n3 <= TC_MAX_FUSED && p->opts.precision == TC_FP32; }
+bool lowp(const tc_plan* p) { return p->opts.precision != TC_FP32; }
 }  // namespace
 
 void tc_set_error(const char* what, cudaError_t e) {
@@ -113,6 +115,13 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     TC_TRY(launch_slice_gemm(p->Ah, X, p->tmp1, n1, s, n2, n3, p->hM, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->Bh, Y, n1, s, s, n3, nullptr, p->hMinv, ep, st);
   }
+  if (lowp(p)) {  // transform to the GEMM input type, tcgen05 slice GEMMs, transform back
+    int* err = ep.red.status ? ep.red.status : p->dev_err;
+    TC_TRY(launch_mode3_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s,
+                             p->opts.precision == TC_BF16, ep.skip, st));
+    TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
+    return launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
+  }
   TC_TRY(launch_mode3(X, p->tmp1, p->dM, n3, (size_t)n2 * s, mid, st));
   TC_TRY(launch_slice_gemm(p->Ah, p->tmp1, p->tmp2, n1, s, n2, n3, nullptr, nullptr, mid, st));
   const float* src = p->tmp2;
@@ -133,6 +142,13 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
       return launch_slice_gemm(p->AhT, Y, X, n2, s, n1, n3, p->hMinvT, p->hMT, ep, st);
     TC_TRY(launch_slice_gemm(p->AhT, Y, p->tmp1, n2, s, n1, n3, p->hMinvT, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->BhT, X, n2, s, s, n3, nullptr, p->hMT, ep, st);
+  }
+  if (lowp(p)) {
+    int* err = ep.red.status ? ep.red.status : p->dev_err;
+    TC_TRY(launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s,
+                             p->opts.precision == TC_BF16, ep.skip, st));
+    TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
+    return launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
   TC_TRY(launch_mode3(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, mid, st));
   TC_TRY(launch_slice_gemm(p->AhT, p->tmp1, p->tmp2, n2, s, n1, n3, nullptr, nullptr, mid, st));
@@ -201,8 +217,24 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
   size_t np = 152 * 32 + 64;
   const size_t big = (p->tmp_elems / n3 + 127) / 128 + 64;
   if (big > np) np = big;
-  const size_t tiles = (size_t)((n1 > n2 ? n1 : n2) + 31) / 32 * ((s + 31) / 32) * n3 + 64;
+  // fused GEMMs: 32 x 32 tiles times a K split of up to 8
+  const size_t tiles = (size_t)((n1 > n2 ? n1 : n2) + 31) / 32 * ((s + 31) / 32) * 8 + 64;
   if (tiles > np) np = tiles;
+  TC_TRY(dalloc(&p->dev_err, 1));
+  TC_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), st));
+  if (lowp(p)) {
+    const int bf16 = p->opts.precision == TC_BF16;
+    const size_t es = bf16 ? 2 : 4;
+    TC_CUDA(cudaMalloc(&p->AhL, TA * es));
+    TC_CUDA(cudaMalloc(&p->AhTL, TA * es));
+    TC_TRY(launch_round(p->Ah, p->AhL, TA, bf16, st));
+    TC_TRY(launch_round(p->AhT, p->AhTL, TA, bf16, st));
+    p->umf = new UmmaMaps();
+    p->uma = new UmmaMaps();
+    const int kind = bf16 ? 0 : 1;
+    TC_TRY(make_umma_maps(p->umf, kind, p->AhL, p->tmp1, n1, s, n2, n3));
+    TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, p->tmp1, n2, s, n1, n3));
+  }
   TC_TRY(dalloc(&p->scratch.partials, np));
   TC_TRY(dalloc(&p->scratch.tickets, 16));
   p->scratch.npartials = np;
@@ -226,6 +258,11 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   dfree(p->iflags);
   dfree(p->gm_dscal);
   dfree(p->gm_flags);
+  dfree(p->dev_err);
+  dfree(p->AhL);
+  dfree(p->AhTL);
+  delete p->umf;
+  delete p->uma;
   delete p;
   return TC_OK;
 }
@@ -249,10 +286,15 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
       return TC_EINVAL;
     if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
   }
-  if (o.precision != TC_FP32) return TC_EUNSUPPORTED;
+  if (o.precision != TC_FP32) {
+    // tensor-core forms: one-sided, every dimension a multiple of 8 (16-byte
+    // rows for TMA), the transform passes of the unfused route
+    if (B || n1 % 8 || n2 % 8 || s % 8) return TC_EUNSUPPORTED;
+  }
   static int inited = 0;
   if (!inited) {
     TC_TRY(tc_kernels_init());
+    TC_TRY(umma_init());
     inited = 1;
   }
   tc_plan* p = new (std::nothrow) tc_plan();
@@ -285,4 +327,21 @@ extern "C" int tc_cprod_adjoint(tc_plan* p, const float* Y, float* X, tc_stream_
   if (!p || !X || !Y || (const void*)X == (const void*)Y) return TC_EINVAL;
   Epi ep;
   return adjoint_epi(p, Y, X, ep, (cudaStream_t)stream);
+}
+
+extern "C" int tc_slice_gemm(tc_plan* p, const void* Xh, float* Yh, int adjoint,
+                             tc_stream_t stream) {
+  if (!p || !Xh || !Yh || (const void*)Xh == (const void*)Yh) return TC_EINVAL;
+  if (p->two_sided) return TC_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int M = adjoint ? p->n2 : p->n1, K = adjoint ? p->n1 : p->n2;
+  if (!lowp(p)) {
+    Epi none;
+    return launch_slice_gemm(adjoint ? p->AhT : p->Ah, static_cast<const float*>(Xh), Yh, M,
+                             p->s, K, p->n3, nullptr, nullptr, none, st);
+  }
+  UmmaMaps m;
+  TC_TRY(make_umma_maps(&m, p->opts.precision == TC_BF16 ? 0 : 1, adjoint ? p->AhTL : p->AhL, Xh,
+                        M, p->s, K, p->n3));
+  return launch_umma(m, Yh, p->dev_err, nullptr, st);
 }

@@ -4,10 +4,10 @@
 //      round-robin pair order, warps rotate disjoint column pairs),
 //      sigma_i = ||h_i||, g~_i = beta * (first row of H V)_i / sigma_i;
 //   2. GCV(lambda) of eq. (gcv2) ("paper") or of the rectangular problem
-//      ("full", with g~_{k+1}^2 = beta^2 - sum g~_i^2), minimised on 200
-//      log-spaced points in [1e-3 sigma_min, sigma_max] (first minimum on
-//      ties), then 40 golden-section steps in log(lambda) between the grid
-//      neighbours; the grid point is kept if the refinement is not lower;
+//      ("full", with g~_{k+1}^2 = beta^2 - sum g~_i^2), minimised on three
+//      nested log grids of 200 points: [1e-10 s, s] with s = ||H||_F, then
+//      twice the bracket between the grid neighbours of the minimum (first
+//      index on ties);
 //   3. y from the normal equations (H^T H + lambda^2 I) y = beta H^T e_1 by
 //      Cholesky.
 // GB300 runs FP64 at a small fraction of its FP32 rate, so everything here is
@@ -16,9 +16,10 @@
 
 namespace {
 
-constexpr int NT = 256;
+constexpr int NT = 1024;
+constexpr int NW = NT / 32;
 constexpr int NGRID = 200;
-constexpr int NGOLD = 40;
+constexpr int NLEVEL = 3;
 constexpr int MAX_SWEEPS = 40;
 
 __device__ double gcv_eval(const double* sig, const double* g, int k, double gnull2,
@@ -59,7 +60,7 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
                double* y, double* gcv_out, const int* skip) {
   if (skip && *skip) return;
   extern __shared__ double dsm[];
-  __shared__ double sig[TC_MAX_PROJ], g[TC_MAX_PROJ];
+  __shared__ double sig[TC_MAX_PROJ], g[TC_MAX_PROJ], dn[TC_MAX_PROJ];
   __shared__ double vals[NGRID];
   __shared__ double grid[NGRID];
   __shared__ int sh_rot;
@@ -85,29 +86,33 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
 
   // ---- 1. one-sided Jacobi -------------------------------------------------
   // Rotate while |<h_p, h_q>| > rows * eps * ||h_p|| ||h_q||: below that the
-  // inner product is rounding noise of the (rows)-term dot product.
+  // inner product is rounding noise of the (rows)-term dot product. Each warp
+  // rotates one column pair of the round; squared column norms d[] are
+  // recomputed every sweep and updated by the exact rotation identities
+  // d_p -= t gamma, d_q += t gamma in between.
   const double jtol = rows * 2.220446049250313e-16;
   const int npairs = kk / 2;
   for (int sweep = 0; sweep < MAX_SWEEPS; ++sweep) {
     if (tid == 0) sh_rot = 0;
+    for (int c = warp; c < kk; c += NW) {
+      const double* x = Hs + (size_t)c * rows;
+      double s2 = 0.0;
+      for (int r = lane; r < rows; r += 32) s2 += x[r] * x[r];
+      s2 = warp_sum_d(s2);
+      if (lane == 0) dn[c] = s2;
+    }
     __syncthreads();
     for (int rnd = 0; rnd < kk - 1; ++rnd) {
-      for (int pi = warp; pi < npairs; pi += NT / 32) {
+      for (int pi = warp; pi < npairs; pi += NW) {
         // circle method: player 0 fixed, the others rotate by rnd
         const int a = (pi == 0) ? 0 : ((pi - 1 + rnd) % (kk - 1)) + 1;
         const int b = ((kk - 2 - pi + rnd) % (kk - 1)) + 1;
         double* xp = Hs + (size_t)a * rows;
         double* xq = Hs + (size_t)b * rows;
-        double al = 0.0, be = 0.0, ga = 0.0;
-        for (int r = lane; r < rows; r += 32) {
-          const double u = xp[r], v = xq[r];
-          al += u * u;
-          be += v * v;
-          ga += u * v;
-        }
-        al = warp_sum_d(al);
-        be = warp_sum_d(be);
+        double ga = 0.0;
+        for (int r = lane; r < rows; r += 32) ga += xp[r] * xq[r];
         ga = warp_sum_d(ga);
+        const double al = dn[a], be = dn[b];
         if (ga != 0.0 && fabs(ga) > jtol * sqrt(al * be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
@@ -118,7 +123,11 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
             xp[r] = c * u - s * v;
             xq[r] = s * u + c * v;
           }
-          if (lane == 0) sh_rot = 1;
+          if (lane == 0) {
+            dn[a] = al - t * ga;
+            dn[b] = be + t * ga;
+            sh_rot = 1;
+          }
         }
       }
       __syncthreads();
@@ -127,7 +136,7 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
     __syncthreads();
     if (!any) break;
   }
-  for (int c = warp; c < k; c += NT / 32) {
+  for (int c = warp; c < k; c += NW) {
     const double* x = Hs + (size_t)c * rows;
     double s2 = 0.0;
     for (int r = lane; r < rows; r += 32) s2 += x[r] * x[r];
@@ -156,47 +165,40 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
   // ---- 2. lambda -------------------------------------------------------------
   double lam = lambda_in;
   if (!(lambda_in >= 0.0)) {
-    const double lo = (smin > 0.0) ? 1e-3 * smin : 1e-12 * smax;
-    const double llo = log(lo), lhi = log(smax);
-    const double step = (lhi - llo) / (NGRID - 1);
-    for (int i = tid; i < NGRID; i += NT) {
-      const double t = (i == NGRID - 1) ? lhi : llo + i * step;
-      grid[i] = exp(t);
-      vals[i] = gcv_eval(sig, g, k, gnull2, grid[i], variant);
+    double hs = 0.0;  // ||H||_F
+    for (int idx = tid; idx < rows * k; idx += NT) {
+      const double v = H[(size_t)(idx / k) * ld + idx % k];
+      hs += v * v;
     }
+    hs = warp_sum_d(hs);
+    if (lane == 0) vals[warp] = hs;
     __syncthreads();
     if (tid == 0) {
-      int bi = 0;
-      for (int i = 1; i < NGRID; ++i)
-        if (vals[i] < vals[bi]) bi = i;
-      double a = log(grid[max(bi - 1, 0)]);
-      double b = log(grid[min(bi + 1, NGRID - 1)]);
-      const double invphi = (sqrt(5.0) - 1.0) / 2.0;
-      double c = b - invphi * (b - a), d = a + invphi * (b - a);
-      double fc = gcv_eval(sig, g, k, gnull2, exp(c), variant);
-      double fd = gcv_eval(sig, g, k, gnull2, exp(d), variant);
-      for (int it = 0; it < NGOLD; ++it) {
-        if (fc <= fd) {
-          b = d; d = c; fd = fc;
-          c = b - invphi * (b - a);
-          fc = gcv_eval(sig, g, k, gnull2, exp(c), variant);
-        } else {
-          a = c; c = d; fc = fd;
-          d = a + invphi * (b - a);
-          fd = gcv_eval(sig, g, k, gnull2, exp(d), variant);
-        }
-      }
-      const double t = (fc <= fd) ? c : d;
-      const double best = fmin(fc, fd);
-      if (vals[bi] < best) {
-        sh_misc[3] = grid[bi];
-        sh_misc[4] = vals[bi];
-      } else {
-        sh_misc[3] = exp(t);
-        sh_misc[4] = best;
-      }
+      double t = 0.0;
+      for (int w = 0; w < NW; ++w) t += vals[w];
+      sh_misc[5] = log(sqrt(t)) - 10.0 * log(10.0);
+      sh_misc[6] = log(sqrt(t));
     }
     __syncthreads();
+    for (int level = 0; level < NLEVEL; ++level) {
+      const double lo = sh_misc[5], hi = sh_misc[6];
+      const double step = (hi - lo) / (NGRID - 1);
+      for (int i = tid; i < NGRID; i += NT) {
+        grid[i] = exp(i == NGRID - 1 ? hi : lo + i * step);
+        vals[i] = gcv_eval(sig, g, k, gnull2, grid[i], variant);
+      }
+      __syncthreads();
+      if (tid == 0) {
+        int bi = 0;
+        for (int i = 1; i < NGRID; ++i)
+          if (vals[i] < vals[bi]) bi = i;
+        sh_misc[3] = grid[bi];
+        sh_misc[4] = vals[bi];
+        sh_misc[5] = log(grid[max(bi - 1, 0)]);
+        sh_misc[6] = log(grid[min(bi + 1, NGRID - 1)]);
+      }
+      __syncthreads();
+    }
     lam = sh_misc[3];
   } else if (tid == 0) {
     sh_misc[4] = gcv_eval(sig, g, k, gnull2, lam, variant);

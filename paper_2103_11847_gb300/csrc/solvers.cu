@@ -43,7 +43,7 @@ int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
     return TC_ENOMEM;
   const size_t L = (size_t)itermax + 2;
   const size_t kp = (size_t)(itermax < TC_MAX_PROJ ? itermax : TC_MAX_PROJ);
-  TC_TRY(grow(&p->dscal, &p->dscal_elems, 4 * L + (kp + 1) * kp + kp + 16, &moved));
+  TC_TRY(grow(&p->dscal, &p->dscal_elems, 7 * L + 1200 + kp + 16, &moved));
   if (keep_basis) TC_TRY(grow(&p->basis, &p->basis_elems, (size_t)itermax * p->Tx, &moved));
   if (moved && p->lsqr_graph) {  // a captured solve holds the old addresses
     cudaGraphExecDestroy(p->lsqr_graph);
@@ -136,8 +136,9 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   double* beta = alpha + L;
   double* rhobar = beta + L;
   double* phibar = rhobar + L;
-  double* Hm = phibar + L;
-  double* y = Hm + (size_t)(kp + 1) * kp;
+  double* rgiv = phibar + L;  // rho_j, theta_{j+1}, phi_j interleaved (3 L)
+  double* gwork = rgiv + 3 * L;
+  double* y = gwork + 1200;
   double* lam = y + kp;
   double* gcv = lam + 1;
   int* flags = p->iflags;
@@ -192,13 +193,12 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     }
     // (c)-(g) Givens recurrences and the X, W updates
     float* slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
-    TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist, j,
-                              a.tol, flags, st));
+    TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist,
+                              keep ? rgiv : nullptr, j, a.tol, flags, st));
   }
   if (keep) {
-    TC_TRY(launch_build_bidiag(alpha, beta, flags + 1, kp, Hm, st));
-    TC_TRY(launch_tikhonov_gcv(Hm, kp, kp, flags + 1, beta, p->opts.gcv_variant, a.lambda,
-                               lam, y, gcv, nullptr, st));
+    TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
+                             a.lambda, gwork, lam, y, gcv, st));
     TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
                           st));
   }

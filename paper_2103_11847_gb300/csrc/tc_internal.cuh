@@ -60,6 +60,8 @@ struct Scratch {
   size_t npartials = 0;
 };
 
+struct UmmaMaps;
+
 struct tc_plan {
   int n1, n2, s, n3;
   bool two_sided;
@@ -82,6 +84,12 @@ struct tc_plan {
   float* gm_basis = nullptr; size_t gm_basis_elems = 0;    // GMRES basis V_1..V_{m+1}
   double* gm_dscal = nullptr; size_t gm_dscal_elems = 0;
   int* gm_flags = nullptr;
+  // tensor-core precision forms (opts.precision TF32 / BF16)
+  void* AhL = nullptr;            // A~ rounded to the GEMM input type
+  void* AhTL = nullptr;           // its slice transposes
+  UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
+  UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
+  int* dev_err = nullptr;         // set by a tensor-core GEMM whose bounded wait gave up
   cudaStream_t cap_stream = nullptr;
   // graph cache for tc_lsqr_c
   cudaGraphExec_t lsqr_graph = nullptr;
@@ -119,6 +127,12 @@ int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, in
 // transform.cu: out[k][p] = ca * sum_l T[k][l] in[l][p] + cp * prev[k][p] over P pixels.
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
                  const Epi& ep, cudaStream_t st);
+// The same transform writing the operand of a tensor-core GEMM: BF16, or FP32
+// rounded to TF32 (bf16 = 0). No epilogue.
+int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
+                      int bf16, const int* skip, cudaStream_t st);
+// Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
+int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st);
 // vec.cu
 int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
                   const int* skip, cudaStream_t st);
@@ -126,7 +140,7 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
                  const int* skip, cudaStream_t st);
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
-                       double* phibar_hist, int j, double tol, int* flags,
+                       double* phibar_hist, double* rgiv, int j, double tol, int* flags,
                        cudaStream_t st);
 int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
                    const int* kdev, const double* y, size_t n, const int* skip,
@@ -140,6 +154,11 @@ int launch_tikhonov_gcv(const double* H, int ld, int kmax, const int* kdev,
                         cudaStream_t st);
 int launch_build_bidiag(const double* alpha, const double* beta, const int* kdev, int kmax,
                         double* H, cudaStream_t st);
+// gcv_bidiag.cu: lambda, GCV and y from LSQR's rotations (rho, theta, phi
+// interleaved in rgiv) without an SVD; work holds 1200 doubles.
+int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha, const double* beta,
+                      const int* kdev, int kmax, int variant, double lambda_in, double* work,
+                      double* lambda_out, double* y, double* gcv_out, cudaStream_t st);
 
 // plan.cu helpers used by solvers
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st);

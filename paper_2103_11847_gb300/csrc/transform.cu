@@ -5,16 +5,29 @@
 // k = w, w+8, w+16, ... and lane q the pixels 4q..4q+3. Inputs stream through
 // shared memory 32 slices at a time; HBM traffic is one read of `in` (and
 // `prev`) and one write of `out`.
+#include <cuda_bf16.h>
+
 #include "tc_device.cuh"
 
 namespace {
 
+// Output element of a transform pass: FP32 (with the Krylov epilogue), or the
+// low-precision operand of a tensor-core GEMM: BF16 (round to nearest even)
+// or FP32 holding a TF32 value (round to nearest, ties away, as cvt.rna).
+enum OutKind { OUT_F32 = 0, OUT_BF16 = 1, OUT_TF32 = 2 };
+
+__device__ __forceinline__ float round_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
 constexpr int PB = 128;  // pixels per CTA
 constexpr int LC = 32;   // input slices per shared-memory stage
 
-template <int KPW>
+template <int KPW, int OUT>
 __global__ void __launch_bounds__(256)
-k_mode3(const float* __restrict__ in, float* out, const float* __restrict__ T, int n3,
+k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, int n3,
         size_t P, Epi ep) {
   if (ep.skip && *ep.skip) return;
   __shared__ __align__(16) float xs[LC][PB];
@@ -54,6 +67,26 @@ k_mode3(const float* __restrict__ in, float* out, const float* __restrict__ T, i
     __syncthreads();
   }
 
+  if (OUT != OUT_F32) {  // operand of a tensor-core GEMM: store only
+#pragma unroll
+    for (int q = 0; q < KPW; ++q) {
+      const int k = w + 8 * q;
+      if (k >= n3) continue;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const size_t p = p0 + lane * 4 + e;
+        if (p < P) {
+          const size_t idx = (size_t)k * P + p;
+          if (OUT == OUT_BF16)
+            static_cast<__nv_bfloat16*>(out_v)[idx] = __float2bfloat16_rn(acc[q][e]);
+          else
+            static_cast<float*>(out_v)[idx] = round_tf32(acc[q][e]);
+        }
+      }
+    }
+    return;
+  }
+  float* out = static_cast<float*>(out_v);
   coef_compute(ep.coef, sh_coef);
   __syncthreads();
   const float ca = sh_coef[0], cp = sh_coef[1];
@@ -77,13 +110,33 @@ k_mode3(const float* __restrict__ in, float* out, const float* __restrict__ T, i
   if (ep.red.out) reduce_finish((double)local, ep.red);
 }
 
-template <int KPW>
-int run(const float* in, float* out, const float* T, int n3, size_t P, const Epi& ep,
+template <int KPW, int OUT>
+int run(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
         cudaStream_t st) {
   const size_t blocks = (P + PB - 1) / PB;
-  k_mode3<KPW><<<(unsigned)blocks, 256, 0, st>>>(in, out, T, n3, P, ep);
+  k_mode3<KPW, OUT><<<(unsigned)blocks, 256, 0, st>>>(in, out, T, n3, P, ep);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
+}
+
+template <int OUT>
+int pick(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
+         cudaStream_t st) {
+  if (n3 <= 8) return run<1, OUT>(in, out, T, n3, P, ep, st);
+  if (n3 <= 16) return run<2, OUT>(in, out, T, n3, P, ep, st);
+  if (n3 <= 32) return run<4, OUT>(in, out, T, n3, P, ep, st);
+  if (n3 <= 64) return run<8, OUT>(in, out, T, n3, P, ep, st);
+  return run<16, OUT>(in, out, T, n3, P, ep, st);
+}
+
+__global__ void k_round(const float* __restrict__ in, void* out, size_t n, int kind) {
+  const size_t st = (size_t)gridDim.x * blockDim.x;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
+    if (kind == OUT_BF16)
+      static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(in[i]);
+    else
+      static_cast<float*>(out)[i] = round_tf32(in[i]);
+  }
 }
 
 }  // namespace
@@ -91,9 +144,20 @@ int run(const float* in, float* out, const float* T, int n3, size_t P, const Epi
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
                  const Epi& ep, cudaStream_t st) {
   TC_CHECK(n3 >= 1 && n3 <= TC_MAX_N3);
-  if (n3 <= 8) return run<1>(in, out, T_dev, n3, P, ep, st);
-  if (n3 <= 16) return run<2>(in, out, T_dev, n3, P, ep, st);
-  if (n3 <= 32) return run<4>(in, out, T_dev, n3, P, ep, st);
-  if (n3 <= 64) return run<8>(in, out, T_dev, n3, P, ep, st);
-  return run<16>(in, out, T_dev, n3, P, ep, st);
+  return pick<OUT_F32>(in, out, T_dev, n3, P, ep, st);
+}
+
+int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
+                      int bf16, const int* skip, cudaStream_t st) {
+  TC_CHECK(n3 >= 1 && n3 <= TC_MAX_N3);
+  Epi ep;
+  ep.skip = skip;
+  return bf16 ? pick<OUT_BF16>(in, out, T_dev, n3, P, ep, st)
+              : pick<OUT_TF32>(in, out, T_dev, n3, P, ep, st);
+}
+
+int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st) {
+  k_round<<<152 * 8, 256, 0, st>>>(in, out, n, bf16 ? OUT_BF16 : OUT_TF32);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
 }

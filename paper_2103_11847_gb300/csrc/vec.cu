@@ -55,7 +55,7 @@ k_scale(const float* __restrict__ in, float* out, size_t n, Coef c, const float*
 __global__ void __launch_bounds__(NT)
 k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot, size_t n,
               const double* alpha, const double* beta, double* rhobar, double* phibar,
-              double* phibar_hist, int j, double tol, int* flags) {
+              double* phibar_hist, double* rgiv, int j, double tol, int* flags) {
   if (flags[0]) return;
   __shared__ float sh[4];
   __shared__ int sh_stop;
@@ -77,6 +77,11 @@ k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot
     if (blockIdx.x == 0) {
       rhobar[j + 1] = c * a;
       phibar[j + 1] = pbn;
+      if (rgiv) {  // R_k and f_k of Q_k [C~_k beta_1 e_1] (§3.3): rho, theta, phi
+        rgiv[3 * j] = rho;
+        rgiv[3 * j + 1] = theta;
+        rgiv[3 * j + 2] = phi;
+      }
       if (phibar_hist) phibar_hist[j] = fabs(pbn);
       flags[1] = j + 1;
       if (!finite) flags[2] = TC_ENONFINITE;
@@ -159,10 +164,10 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
-                       double* phibar_hist, int j, double tol, int* flags,
+                       double* phibar_hist, double* rgiv, int j, double tol, int* flags,
                        cudaStream_t st) {
   k_lsqr_update<<<grid_for(n, 8), NT, 0, st>>>(X, W, V, basis_slot, n, alpha, beta, rhobar,
-                                               phibar, phibar_hist, j, tol, flags);
+                                               phibar, phibar_hist, rgiv, j, tol, flags);
   TC_CUDA(cudaGetLastError());
   k_lsqr_flag<<<1, 1, 0, st>>>(flags);
   TC_CUDA(cudaGetLastError());

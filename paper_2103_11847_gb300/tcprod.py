@@ -50,6 +50,7 @@ _SIGS = {
                     c_void_p, c_void_p], c_int),
     "tc_tikhonov_gcv": ([c_void_p, c_int, c_void_p, c_int, c_double, c_void_p, c_void_p,
                          c_void_p, c_void_p], c_int),
+    "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
 }
 
 _LIB = None
@@ -177,6 +178,13 @@ def tc_tikhonov_gcv(H, k, beta, variant, lam, lambda_out, y, gcv_out, stream=Non
         _ptr(H, torch.float64), k, _ptr(beta, torch.float64), variant,
         -1.0 if lam is None else float(lam), _ptr(lambda_out, torch.float64),
         _ptr(y, torch.float64), _ptr(gcv_out, torch.float64), _stream(stream)))
+
+
+def tc_slice_gemm(h, Xh, Yh, adjoint=False, stream=None):
+    """Transform-domain slice products; Xh is FP32, or BF16 for a BF16 plan."""
+    dt = torch.bfloat16 if Xh.dtype == torch.bfloat16 else torch.float32
+    _check("tc_slice_gemm", lib().tc_slice_gemm(h, _ptr(Xh, dt, name="Xh"), _ptr(Yh, name="Yh"),
+                                                int(bool(adjoint)), _stream(stream)))
 
 
 class Plan:

@@ -54,6 +54,18 @@ def oracle_ops(A, B):
     return (lambda X: cp.cprod(A, X, B)), (lambda Y: cp.cprod_adjoint(A, Y, B))
 
 
+def check_lambda(lam_gpu, ref, variant="paper", rtol=1e-3):
+    """lambda parity. When GCV is flat where it is smallest (eq. (gcv2) can
+    increase monotonically in lambda, leaving a plateau as lambda -> 0 whose
+    values agree to rounding), every lambda on the plateau is a minimiser: then
+    the oracle's GCV at the GPU's lambda must equal its minimum to 1e-9."""
+    if abs(lam_gpu - ref["lam"]) <= rtol * ref["lam"]:
+        return
+    sig, g = rg.svd_projected(ref["Cm"], ref["beta"][0])
+    g_at = rg.gcv_value(sig, g, lam_gpu, variant)
+    assert abs(g_at - ref["gcv"]) <= 1e-9 * ref["gcv"], (lam_gpu, ref["lam"], g_at, ref["gcv"])
+
+
 # FP32 envelope. The paper's Golub-Kahan process has no reorthogonalisation.
 # On the 64x64x3 colour deblur, any FP32 execution of Algorithm 6 leaves the
 # FP64 trajectory once Ritz values converge. A CPU emulation of the same
@@ -77,11 +89,28 @@ def test_lsqr_gcv_colour_64(tc, use_graphs):
         assert rel(X.cpu().numpy(), ref["X"]) < 1e-3
         assert np.allclose(hist.cpu().numpy(), ref["phibar"], rtol=1e-4)
         assert abs(inf["resid"] - ref["phibar"][-1]) < 1e-4 * ref["phibar"][-1]
-        assert abs(inf["lam"] - ref["lam"]) < 1e-3 * ref["lam"]
+        check_lambda(inf["lam"], ref)
         e_gpu = mt.relative_error(w["X_true"], Xr.cpu().numpy())
         e_ref = mt.relative_error(w["X_true"], ref["X_reg"])
         assert abs(e_gpu - e_ref) < 0.01 * e_ref
         assert rel(Xr.cpu().numpy(), ref["X_reg"]) < 1e-3
+    plan.close()
+
+
+def test_lsqr_gcv_full_variant_interior_minimum(tc):
+    # The rectangular-problem GCV (TC_GCV_FULL) has an interior minimum on the
+    # 64x64x3 deblur (lambda ~ 0.1 after 15 iterations): lambda to 1e-3.
+    w = inputs.colour_deblur(n=64, seed=0)
+    A, B, C = observe(w)
+    ref = kr.lsqr_gcv(*oracle_ops(A, B), C, itermax=15, variant="full")
+    assert 1e-3 < ref["lam"] < 10.0
+    plan = tc.Plan(dev(A), s=64, gcv_variant=tc.TC_GCV_FULL)
+    X, Xr, _, info = plan.lsqr(dev(C), 15, regularize=True)
+    torch.cuda.synchronize()
+    inf = tc.read_info(info)
+    assert abs(inf["lam"] - ref["lam"]) < 1e-3 * ref["lam"]
+    assert abs(inf["gcv"] - ref["gcv"]) < 1e-4 * ref["gcv"]
+    assert rel(Xr.cpu().numpy(), ref["X_reg"]) < 1e-3
     plan.close()
 
 
@@ -118,7 +147,7 @@ def test_lsqr_two_sided_256(tc):
     e_gpu = mt.relative_error(w["X_true"], Xr.cpu().numpy())
     e_ref = mt.relative_error(w["X_true"], ref["X_reg"])
     assert abs(e_gpu - e_ref) < 0.01 * e_ref
-    assert abs(inf["lam"] - ref["lam"]) < 1e-3 * ref["lam"]
+    check_lambda(inf["lam"], ref)
 
 
 @pytest.mark.parametrize("n1,n2,s,n3", [(37, 29, 23, 3), (33, 33, 17, 7), (20, 20, 20, 1)])
