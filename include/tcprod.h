@@ -171,6 +171,26 @@ int tc_tikhonov_gcv(const double* H, int k, const double* beta, int variant,
                     double lambda_in, double* lambda_out, double* y,
                     double* gcv_out, tc_stream_t stream);
 
+/* Frobenius norm ||X||_F of n FP32 values, written to *out (device double),
+ * without allocating any device memory. The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as code
+ * whose device memory belongs to another allocator that has reserved the
+ * device, or code that cannot accept the device synchronisation that
+ * cudaMalloc and cudaFree may imply.
+ *   X: device, n floats (read).  out: device double (written).
+ *   n: 1 .. 79691776 (4864 CTAs x 256 threads x 64 values); larger n returns
+ *      TC_EINVAL and tc_last_error() says why.
+ * It computes the same reduction as the norm that tc_gkb_init writes to
+ * beta[0]: the same grid, per-thread FP32 sums, then an FP64 tree in a fixed
+ * order. Its scratch is a 39 KB array in the library's static device memory,
+ * held by every GPU that loads the library until the process exits.
+ * The first call on each device looks up that array's address with that
+ * device current; make this first call before any stream capture. All calls
+ * on a device share the array, so calls that overlap on the GPU (different
+ * streams, or other host threads) race and must be serialised by the caller.
+ * Each call clears the array's arrival counter on `stream` before its kernel. */
+int tc_fro_norm_noalloc(const float* X, size_t n, double* out, tc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

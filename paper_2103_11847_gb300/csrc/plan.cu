@@ -90,6 +90,8 @@ void tc_set_error(const char* what, cudaError_t e) {
   std::snprintf(g_err, sizeof(g_err), "%s: %s (%d)", what, cudaGetErrorString(e), (int)e);
 }
 
+void tc_set_message(const char* msg) { std::snprintf(g_err, sizeof(g_err), "%s", msg); }
+
 extern "C" const char* tc_last_error(void) { return g_err; }
 extern "C" const char* tc_version(void) { return "tcprod 0.1 (sm_103a)"; }
 

@@ -98,6 +98,7 @@ struct tc_plan {
 
 // ----------------------------------------------------------- error helpers --
 void tc_set_error(const char* what, cudaError_t e);
+void tc_set_message(const char* msg);
 #define TC_CUDA(call)                                   \
   do {                                                  \
     cudaError_t e_ = (call);                            \

@@ -50,6 +50,7 @@ _SIGS = {
                     c_void_p, c_void_p], c_int),
     "tc_tikhonov_gcv": ([c_void_p, c_int, c_void_p, c_int, c_double, c_void_p, c_void_p,
                          c_void_p, c_void_p], c_int),
+    "tc_fro_norm_noalloc": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p], c_int),
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
 }
 
@@ -185,6 +186,12 @@ def tc_slice_gemm(h, Xh, Yh, adjoint=False, stream=None):
     dt = torch.bfloat16 if Xh.dtype == torch.bfloat16 else torch.float32
     _check("tc_slice_gemm", lib().tc_slice_gemm(h, _ptr(Xh, dt, name="Xh"), _ptr(Yh, name="Yh"),
                                                 int(bool(adjoint)), _stream(stream)))
+
+
+def tc_fro_norm_noalloc(X, out, stream=None):
+    """||X||_F into the device double `out`, using no device allocation."""
+    _check("tc_fro_norm_noalloc", lib().tc_fro_norm_noalloc(
+        _ptr(X, name="X"), X.numel(), _ptr(out, torch.float64, name="out"), _stream(stream)))
 
 
 class Plan:
