@@ -61,9 +61,11 @@ def product_flops(n1, n2, s, n3, two_sided):
     return f
 
 
-def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True):
+def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32"):
     """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu)."""
     per_product = (2 if two_sided else 1) if fused else (4 if two_sided else 3)
+    if precision != "fp32":  # transform, [transpose for TF32], tcgen05 GEMM, transform back
+        per_product = 4 if precision == "tf32" else 3
     init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
     per_iter = 2 * per_product + 2
     tail = (5 if keep_basis else 0) + 1  # 3 GCV grid levels, final, combine; info
@@ -168,6 +170,152 @@ def cpu_baseline(workload, budget_s=12.0):
 
 # ---------------------------------------------------------------- GPU arm ----
 
+def precision_forms(dev, peaks, steps=3):
+    """The video workload (512 x 512 x 64, 50 c-LSQR iterations + Tikhonov/GCV)
+    in FP32, TF32 and BF16 slice GEMMs: LSQR iterations/s, the reconstruction
+    error of X_reg against the clean video (the matched-error check), and the
+    transform-domain slice GEMM timed alone (tc_slice_gemm) against the HBM
+    roofline: it reads A~ and X~ once and writes Y~ in FP32."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    wl = WORKLOADS["video_512"]
+    w = make_problem("video_512")
+    n3, n1, n2 = w["A"].shape
+    s = w["X_true"].shape[2]
+    iters = wl["iters"]
+    A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+    Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
+    G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
+    out = {"workload": f"video_512: c-LSQR {iters} it + Tikhonov/GCV, A {n1}x{n2}x{n3}, "
+                       f"X {n2}x{s}x{n3}", "l2": "inputs (64-256 MB per tensor) exceed L2"}
+    C = None
+    st = torch.cuda.current_stream()
+    for name, code in (("fp32", tcprod.TC_FP32), ("tf32", tcprod.TC_TF32), ("bf16", tcprod.TC_BF16)):
+        plan = tcprod.Plan(A, s=s, precision=code)
+        if C is None:
+            Cc = plan.cprod(Xt)
+            C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
+        X = torch.empty(plan.xshape(), device=dev)
+        Xr = torch.empty(plan.xshape(), device=dev)
+        info = tcprod.new_info()
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        inf = tcprod.read_info(info)
+        # slice GEMM alone on a transform-domain operand of the plan's input type
+        dt = torch.bfloat16 if name == "bf16" else torch.float32
+        Xh = torch.randn((n3, n2, s), device=dev).to(dt)
+        Yh = torch.empty((n3, n1, s), device=dev)
+        for _ in range(3):
+            tcprod.tc_slice_gemm(plan.handle, Xh, Yh)
+        reps = 20
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(st)
+        for _ in range(reps):
+            tcprod.tc_slice_gemm(plan.handle, Xh, Yh)
+        g1.record(st)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / reps
+        es = 2 if name == "bf16" else 4
+        gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
+        gflops = 2.0 * n1 * n2 * s * n3
+        gbs = gbytes / (gms * 1e-3) / 1e9
+        out[name] = {"iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+                     "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+                     "rel_err_lsqr": float((X - Xt).norm() / Xt.norm()), "lambda": inf["lam"],
+                     "status": inf["status"],
+                     "slice_gemm": {"kernel": "k_umma_gemm (tcgen05)" if name != "fp32"
+                                    else "k_slice_gemm (FFMA)", "ms": gms,
+                                    "GB_per_s": gbs, "TFLOP_per_s": gflops / (gms * 1e-3) / 1e12,
+                                    "hbm_frac": gbs / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
+                                    "algorithmic_bytes": gbytes}}
+        plan.close()
+    base = out["fp32"]["rel_err_reg"]
+    for name in ("tf32", "bf16"):
+        out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
+        out[name]["speedup_vs_fp32"] = out[name]["iters_per_s"] / out["fp32"]["iters_per_s"]
+    return out
+
+
+def batched_form(dev, iters=40, count=128, steps=2):
+    """128 independent colour deblurring problems of uneven sizes n in
+    {64, 96, ..., 512} (n x n x 3, sigma ~ U[1, 4], noise ~ U[1e-4, 1e-2]),
+    solved by c-LSQR (40 iterations) + Tikhonov/GCV in one graph launch, in FP32
+    and BF16 slice GEMMs: solves/s and the mean reconstruction error."""
+    import torch
+    from paper_2103_11847_gb300 import inputs, tcprod
+    sizes = inputs.batch_sizes(count)
+    As, Cs, Xt = [], [], []
+    for i, n in enumerate(sizes):
+        w = inputs.batch_problem(i, n)
+        A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+        As.append(A)
+        Xt.append(torch.from_numpy(w["X_true"].astype(np.float32)).to(dev))
+        Cs.append((w, A))
+    out = {"workload": f"{count} problems n x n x 3, n in {{64..512}} (sum n^2 = "
+                       f"{sum(n * n for n in sizes)}), c-LSQR {iters} it + Tikhonov/GCV",
+           "launch": "one CUDA graph of per-problem child graphs"}
+    C_dev = None
+    st = torch.cuda.current_stream()
+    for name, code in (("fp32", tcprod.TC_FP32), ("bf16", tcprod.TC_BF16)):
+        h = tcprod.tc_batch_create(As, sizes, precision=code)
+        if C_dev is None:  # observations C = A *c X + N, formed by the library
+            C_dev = []
+            for i, (w, A) in enumerate(Cs):
+                p = tcprod.Plan(A, s=sizes[i])
+                Cc = p.cprod(Xt[i])
+                G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
+                C_dev.append((Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous())
+                p.close()
+        Xs = [torch.empty_like(c) for c in C_dev]
+        Xr = [torch.empty_like(c) for c in C_dev]
+        infos = tcprod.new_infos(count)
+        tcprod.tc_lsqr_c_batched(h, C_dev, Xs, Xr, iters, 0.0, None, infos)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            tcprod.tc_lsqr_c_batched(h, C_dev, Xs, Xr, iters, 0.0, None, infos)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        errs = [float((Xr[i] - Xt[i]).norm() / Xt[i].norm()) for i in range(count)]
+        out[name] = {"solves_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
+                     "iters_per_s": count * iters / (ms * 1e-3),
+                     "mean_rel_err_reg": float(np.mean(errs))}
+        tcprod.tc_batch_destroy(h)
+    base = out["fp32"]["mean_rel_err_reg"]
+    out["bf16"]["matched_error"] = bool(abs(out["bf16"]["mean_rel_err_reg"] - base) <= 0.02 * base)
+    return out
+
+
+def learned_form(train_count=20000):
+    """Learned lambda / stop index: 20k c-LSQR solves of 128 x 128 x 3 problems
+    labelled by tc_lsqr_label, the network trained by tc_mlp_train, then the
+    learned solve against plain GCV-driven c-LSQR (40 steps) on held-out
+    512 x 512 x 3 images and a 512 x 512 x 32 video."""
+    import torch
+    from paper_2103_11847_gb300 import learn
+    t0 = time.perf_counter()
+    F, T = learn.training_data(train_count)
+    t1 = time.perf_counter()
+    mlp, hist = learn.train(F, T)
+    t2 = time.perf_counter()
+    out = {"train": {"solves": train_count, "size": "128x128x3", "label_s": t1 - t0,
+                     "train_s": t2 - t1, "loss_first": float(hist[0].item()),
+                     "loss_last50": float(hist[-50:].mean().item())},
+           "eval_512x512x3": learn.summarize(learn.compare(mlp, count=8)),
+           "eval_512x512x32": learn.summarize(learn.compare(mlp, count=2, frames=32))}
+    mlp.close()
+    return out
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -195,7 +343,8 @@ def run_gpu(args):
     B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
     Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
     G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
-    plan = tcprod.Plan(A, B, s=s)
+    prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16}[args.precision]
+    plan = tcprod.Plan(A, B, s=s, precision=prec)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
     Cc = plan.cprod(Xt)
     C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
@@ -280,12 +429,13 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
             "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else f"{args.precision} GEMM inputs, f32",
             "data": "synthetic (seeded image + Gaussian blur + 1e-3 noise)",
             "config": {"workload": f"{args.workload}: c-LSQR {iters} it + Tikhonov/GCV, "
                                    f"A {n1}x{n2}x{n3}" + (f", B {s}x{s}x{n3}" if two else "")
                                    + f", X {n2}x{s}x{n3}",
-                       "precision": "fp32", "l2": "flushed between timed steps (256 MB write)",
+                       "precision": args.precision,
+                       "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": {"kernel": "k_slice_gemm (all GEMM stages of one c-product)",
                          "bound": "alu", "achieved": achieved, "peak": fp32_peak,
@@ -296,13 +446,18 @@ def run_gpu(args):
             "e2e": {"value": iters / (e2e_ms / 1000.0) * world, "unit": "LSQR iterations/s",
                     "h2d_bytes_per_step": int(C.numel() * 4),
                     "d2h_bytes_per_step": int(Xr.numel() * 4 + info.numel())},
-            "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4),
+            "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4,
+                                                              precision=args.precision),
             "clocks": clk,
             "solve": {"iters": inf["iters"], "status": inf["status"], "lambda": inf["lam"],
                       "resid": inf["resid"],
                       "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
                       "rel_err_lsqr": float((X - Xt).norm() / Xt.norm())},
         }
+        if not args.no_precision_forms and world == 1:
+            line["precision_forms"] = precision_forms(dev, peaks)
+            line["batched_form"] = batched_form(dev)
+            line["learned_form"] = learned_form()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
@@ -350,6 +505,10 @@ def main():
     ap.add_argument("--impl", default="tcprod", choices=["tcprod", "reference"])
     ap.add_argument("--workload", default="two_sided_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-forms", action="store_true")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="slice-GEMM inputs of the main workload (tensor-core forms need "
+                         "one-sided plans: video_512 or colour_64)")
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()

@@ -43,6 +43,7 @@ extern "C" {
 typedef struct CUstream_st* tc_stream_t;
 
 typedef struct tc_plan tc_plan;
+typedef struct tc_mlp tc_mlp;
 
 typedef enum {
   TC_OK = 0,
@@ -80,7 +81,7 @@ typedef struct {
   int status;    /* 0 ran to itermax, 1 converged (residual < tol),
                     TC_EBREAKDOWN or TC_ENONFINITE */
   int cycles;    /* GMRES restart cycles */
-  int pad;
+  int fallback;  /* tc_lsqr_c_learned: 1 when GCV replaced the predicted lambda */
   double resid;  /* LSQR: |phibar_{k+1}| = ||C - M(X_k)||_F (§3.3);
                     GMRES: ||C - M(X)||_F at the last check */
   double lambda; /* Tikhonov parameter used (NaN if none) */
@@ -150,6 +151,83 @@ int tc_lsqr_c(tc_plan* plan, const float* C, float* X, float* X_reg,
 int tc_gmres_c(tc_plan* plan, const float* C, const float* X0, float* X,
                int m, int itermax, double tol, double lambda,
                tc_solve_info* info, tc_stream_t stream);
+
+/* Batched c-LSQR over independent problems of uneven sizes. This is the batched
+ * form of the solver of Algorithm 6 (§3.3) with the Tikhonov/GCV projection.
+ * tc_batch_create makes one plan per problem (one-sided, shared n3 and opts):
+ *   n1, n2, s: host arrays[count]; A: host array[count] of device pointers,
+ *   A[i] of size n1[i] x n2[i] x n3. Synchronises `stream`.
+ * tc_lsqr_c_batched solves problem i exactly as tc_lsqr_c would on plan i, with
+ * the same itermax, tol and lambda for all:
+ *   C, X: host arrays[count] of device pointers (C[i]: n1[i] x s[i] x n3,
+ *   X[i]: n2[i] x s[i] x n3). X_reg: host array of device pointers or NULL.
+ *   infos: device array of count tc_solve_info.
+ * Every problem's solve is captured as one child graph. The children go into a
+ * single parent graph with no dependencies between them, launched once on
+ * `stream`, so the problems run concurrently. The parent graph is cached while
+ * the pointers and parameters stay the same. */
+typedef struct tc_batch tc_batch;
+int tc_batch_create(tc_batch** batch, int count, const int* n1, const int* n2, const int* s,
+                    int n3, const float* const* A, const tc_opts* opts, tc_stream_t stream);
+int tc_batch_destroy(tc_batch* batch);
+int tc_lsqr_c_batched(tc_batch* batch, const float* const* C, float* const* X,
+                      float* const* X_reg, int itermax, double tol, double lambda,
+                      tc_solve_info* infos, tc_stream_t stream);
+
+/* ---- Learned lambda and stopping index --------------------------------------
+ * None of this has a counterpart in the paper. A small network stands in for the
+ * per-solve GCV search (§3.1, eq. (gcv2)) and for the choice of the stopping
+ * index (§3.3, k_opt); GCV stays as the fallback. The network is
+ *   36 -> 64 -> 64 -> 2, GELU, W row-major (in x out), parameters one FP32
+ *   vector [W1 | b1 | W2 | b2 | W3 | b3] of TC_MLP_NPARAMS values; the forward
+ *   pass uses BF16 copies of the weights with FP32 accumulation.
+ * Inputs (36, from the first 12 c-LSQR steps): log(alpha_i / beta_1),
+ *   log(beta_{i+1} / beta_1), log(|phibar_{i+1}| / beta_1), i = 1..12.
+ * Outputs: (log lambda, stopping index). The normalisation vector `norm`
+ *   (TC_MLP_NORM values: input means[36], input stds[36], output means[2],
+ *   output stds[2]) maps raw features and targets to network units; the
+ *   training calls take data already normalised. */
+#define TC_MLP_NPARAMS 6658
+#define TC_MLP_NORM 76
+int tc_mlp_create(tc_mlp** mlp, unsigned long long seed, tc_stream_t stream);
+int tc_mlp_destroy(tc_mlp* mlp);
+/* theta: device FP32[TC_MLP_NPARAMS] or NULL; norm: device FP32[TC_MLP_NORM] or NULL.
+ * Setting theta resets the Adam state. */
+int tc_mlp_set_params(tc_mlp* mlp, const float* theta, const float* norm, tc_stream_t stream);
+int tc_mlp_get_params(tc_mlp* mlp, float* theta, float* norm, tc_stream_t stream);
+/* Y (device B x 2) = network(X (device B x 36)), normalised units. */
+int tc_mlp_forward(tc_mlp* mlp, const float* X, int B, float* Y, tc_stream_t stream);
+/* loss = (1/2B) sum (Y - T)^2 and its gradient for one batch (B <= 1024):
+ * loss: device float or NULL, grad: device FP32[TC_MLP_NPARAMS]. */
+int tc_mlp_loss_grad(tc_mlp* mlp, const float* X, const float* T, int B, float* loss,
+                     float* grad, tc_stream_t stream);
+/* Set the network's normalisation from raw training data (N rows): column means
+ * and standard deviations of Xraw (N x 36) and Traw (N x 2); writes the
+ * normalised copies Xn, Tn (device, same shapes). */
+int tc_mlp_fit_norm(tc_mlp* mlp, const float* Xraw, const float* Traw, int N, float* Xn,
+                    float* Tn, tc_stream_t stream);
+/* `steps` Adam steps (beta 0.9, 0.999, eps 1e-8, rate lr) on consecutive
+ * batches of X (N x 36), T (N x 2), wrapping around; loss_hist: device
+ * float[steps] or NULL. */
+int tc_mlp_train(tc_mlp* mlp, const float* X, const float* T, int N, int batch, int steps,
+                 float lr, float* loss_hist, tc_stream_t stream);
+/* Training data from one solve: kmax (13 .. 128) steps of c-LSQR on C, then
+ * the features (device float[36]) and the target (device float[2]):
+ *   k_opt  = the smallest k in {4, 6, .., kmax} whose best error over lambda
+ *            is within 1% of the best over all k, and
+ *   lambda = the lambda that minimises the error at k_opt.
+ * The error is ||V_k y_k(lambda) - X_true||_F, taken exactly from the Gram
+ * matrix of the kept basis V, with lambda on 48 log-spaced values in
+ * [1e-6, 1] ||C~_kmax||_F. */
+int tc_lsqr_label(tc_plan* plan, const float* C, const float* X_true, int kmax, float* feat,
+                  float* target, tc_stream_t stream);
+/* c-LSQR with the learned stop index and lambda, all on the device. It runs
+ * 12 steps, predicts (lambda, k), continues to min(k, kmax) steps, then
+ * forms X_reg = V_k (*) y_lambda. If GCV(lambda) exceeds gcv_factor times the
+ * GCV minimum (opts.gcv_variant), the GCV lambda is used and info.fallback = 1.
+ *   kmax: 13 .. 128. X: the LSQR iterate. X_reg: required. info: device. */
+int tc_lsqr_c_learned(tc_plan* plan, const tc_mlp* mlp, const float* C, float* X, float* X_reg,
+                      int kmax, double gcv_factor, tc_solve_info* info, tc_stream_t stream);
 
 /* Step 2 of Algorithm 1 alone: the n3 frontal-slice products in the transform
  * domain, Y~_k = A~_k X~_k (adjoint = 0) or Y~_k = A~_k^T X~_k (adjoint = 1),

@@ -19,96 +19,60 @@
 // Search: the same three nested 200-point log grids as the general path
 // (first level [1e-10 s, s] with s = ||C~_k||_F). Each point of a level runs on
 // its own CTA, so the serial O(k) chains of the 200 points overlap across SMs.
-#include "tc_device.cuh"
+#include "gcv_eval.cuh"
 
 namespace {
 
 constexpr int NGRID = 200;
 constexpr int NLEVEL = 3;
 
-// GCV at lambda (and y_lambda into y if given) from R (rho, theta), f (phi),
-// interleaved as rg[3j] = rho_j, rg[3j+1] = theta_{j+1}, rg[3j+2] = phi_j,
-// and pbar2 = phibar_{k+1}^2.
-//
-// The residual sum is formed as l^4 ||z||^2 with z = (R R^T + l^2 I)^{-1} f,
-// never as f - R y: that difference cancels when l << sigma_min. R R^T is
-// handled through R' = P R^T P (P reverses the order), which is upper
-// bidiagonal: R R^T + l^2 I = P (R'^T R' + l^2 I) P = P Rh^T Rh P, where Rh
-// comes from the rotations above applied to [R'; l I]. The trace is the same
-// for R R^T and R^T R. y_l = R^T z.
-__device__ double gcv_bd_eval(const double* rg, int k, double pbar2, double lam, int variant,
-                              double* y) {
-  double d[TC_MAX_PROJ], e[TC_MAX_PROJ], u[TC_MAX_PROJ];
-  double mu = lam, T = 1.0, D = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const int jr = k - 1 - j;  // R'_{jj} = rho_{jr}, R'_{j,j+1} = theta of column jr-1
-    const double rj = rg[3 * jr];
-    const double r = hypot(rj, mu);
-    const double c = (r > 0.0) ? rj / r : 1.0, s = (r > 0.0) ? mu / r : 0.0;
-    d[j] = r;
-    D += T / (r * r);
-    e[j] = 0.0;
-    if (j + 1 < k) {
-      const double th = rg[3 * (jr - 1) + 1];
-      e[j] = c * th;
-      const double fill = -s * th;  // row k+j, column j+1
-      const double q = e[j] / r;
-      T = 1.0 + q * q * T;
-      mu = hypot(fill, lam);  // merge the fill into row k+j+1 (only l at column j+1)
-    }
+// First index of the smallest of v[0..n) over one warp (ties to the lower index).
+__device__ int warp_argmin(const double* v, int n) {
+  const int lane = threadIdx.x & 31;
+  double best = INFINITY;
+  int bi = n;
+  for (int t = lane; t < n; t += 32) {
+    const double x = v[t];
+    if (x < best) { best = x; bi = t; }
   }
-  // Rh^T w = P f, Rh u = w; z = P u
-  double wp = 0.0;
-  for (int j = 0; j < k; ++j) {
-    const double fj = rg[3 * (k - 1 - j) + 2];
-    wp = (fj - (j > 0 ? e[j - 1] * wp : 0.0)) / d[j];
-    u[j] = wp;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
   }
-  double uu = 0.0, un = 0.0;
-  for (int j = k - 1; j >= 0; --j) {
-    un = (u[j] - e[j] * un) / d[j];
-    u[j] = un;
-    uu += un * un;
-  }
-  if (y) {  // y_j = rho_j z_j + theta_j z_{j-1}, z_i = u_{k-1-i}
-    for (int j = 0; j < k; ++j)
-      y[j] = rg[3 * j] * u[k - 1 - j] + (j > 0 ? rg[3 * (j - 1) + 1] * u[k - j] : 0.0);
-  }
-  if (variant == TC_GCV_FULL) {
-    const double l2 = lam * lam;
-    const double den = 1.0 + l2 * D;
-    return (l2 * l2 * uu + pbar2) / (den * den);
-  }
-  return uu / (D * D);
+  return bi < n ? bi : 0;
 }
 
 // One level of the search: CTA i evaluates grid point i of this level.
 __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const double* alpha, const double* beta,
                                const int* kdev, int kmax, int variant, int level, double* lams,
                                double* vals) {
-  if (threadIdx.x != 0) return;
   const int k = kdev ? min(*kdev, kmax) : kmax;
   const int i = blockIdx.x;
   if (k <= 0) {
-    lams[level * NGRID + i] = nan("");
-    vals[level * NGRID + i] = nan("");
+    if (threadIdx.x == 0) {
+      lams[level * NGRID + i] = nan("");
+      vals[level * NGRID + i] = nan("");
+    }
     return;
   }
   double lo, hi;
   if (level == 0) {
-    double s2 = 0.0;  // ||C~_k||_F^2: diagonal alpha_1..alpha_k, subdiagonal beta_2..beta_{k+1}
-    for (int j = 0; j < k; ++j) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
+    // ||C~_k||_F^2: diagonal alpha_1..alpha_k, subdiagonal beta_2..beta_{k+1}
+    double s2 = 0.0;
+    for (int j = threadIdx.x; j < k; j += 32) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     hi = log(sqrt(s2));
     lo = hi - 10.0 * log(10.0);
   } else {
     const double* pl = lams + (level - 1) * NGRID;
-    const double* pv = vals + (level - 1) * NGRID;
-    int b = 0;
-    for (int t = 1; t < NGRID; ++t)
-      if (pv[t] < pv[b]) b = t;
+    const int b = warp_argmin(vals + (level - 1) * NGRID, NGRID);
     lo = log(pl[max(b - 1, 0)]);
     hi = log(pl[min(b + 1, NGRID - 1)]);
   }
+  if (threadIdx.x != 0) return;
   const double step = (hi - lo) / (NGRID - 1);
   const double lam = exp(i == NGRID - 1 ? hi : lo + i * step);
   const double pb = phibar[k];
@@ -117,27 +81,36 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
 }
 
 // lambda (the last level's minimum, or lambda_in >= 0), GCV there, and y.
-__global__ void k_gcv_bd_final(const double* rg, const double* phibar, const int* kdev, int kmax, int variant,
-                               double lambda_in, const double* lams, const double* vals,
-                               double* lambda_out, double* y, double* gcv_out) {
-  if (threadIdx.x != 0) return;
+// With lam_pred (a predicted lambda): keep it unless its GCV exceeds factor
+// times the last level's minimum, in which case the minimiser is used and
+// *fallback is set to 1.
+__global__ void k_gcv_bd_final(const double* rg, const double* phibar, const int* kdev, int kmax,
+                               int variant, double lambda_in, const double* lams,
+                               const double* vals, const double* lam_pred, double factor,
+                               int* fallback, double* lambda_out, double* y, double* gcv_out) {
   const int k = kdev ? min(*kdev, kmax) : kmax;
-  for (int j = (k > 0 ? k : 0); j < kmax; ++j) y[j] = 0.0;
+  for (int j = (k > 0 ? k : 0) + (int)threadIdx.x; j < kmax; j += 32) y[j] = 0.0;
+  double lam = lambda_in;
+  int b = 0;
+  if (k > 0 && !(lambda_in >= 0.0)) {
+    b = warp_argmin(vals + (NLEVEL - 1) * NGRID, NGRID);
+    lam = lams[(NLEVEL - 1) * NGRID + b];
+  }
+  if (threadIdx.x != 0) return;
   if (k <= 0) {
     *lambda_out = nan("");
     if (gcv_out) *gcv_out = nan("");
     return;
   }
-  double lam = lambda_in;
-  if (!(lambda_in >= 0.0)) {
-    const double* pl = lams + (NLEVEL - 1) * NGRID;
-    const double* pv = vals + (NLEVEL - 1) * NGRID;
-    int b = 0;
-    for (int t = 1; t < NGRID; ++t)
-      if (pv[t] < pv[b]) b = t;
-    lam = pl[b];
-  }
   const double pb = phibar[k];
+  if (lam_pred) {
+    const double lp = *lam_pred;
+    const double gp = gcv_bd_eval(rg, k, pb * pb, lp, variant, nullptr);
+    const double gmin = vals[(NLEVEL - 1) * NGRID + b];
+    const bool use_pred = isfinite(gp) && lp > 0.0 && gp <= factor * gmin;
+    if (fallback) *fallback = use_pred ? 0 : 1;
+    if (use_pred) lam = lp;
+  }
   const double gv = gcv_bd_eval(rg, k, pb * pb, lam, variant, y);
   *lambda_out = lam;
   if (gcv_out) *gcv_out = gv;
@@ -145,21 +118,23 @@ __global__ void k_gcv_bd_final(const double* rg, const double* phibar, const int
 
 }  // namespace
 
-int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha, const double* beta,
-                      const int* kdev, int kmax, int variant, double lambda_in, double* work,
-                      double* lambda_out, double* y, double* gcv_out, cudaStream_t st) {
+int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha,
+                      const double* beta, const int* kdev, int kmax, int variant,
+                      double lambda_in, double* work, double* lambda_out, double* y,
+                      double* gcv_out, cudaStream_t st, const double* lam_pred, double factor,
+                      int* fallback) {
   TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ);
   double* lams = work;
   double* vals = work + NLEVEL * NGRID;
   if (!(lambda_in >= 0.0)) {
     for (int level = 0; level < NLEVEL; ++level) {
-      k_gcv_bd_level<<<NGRID, 32, 0, st>>>(rg, phibar, alpha, beta, kdev, kmax,
-                                           variant, level, lams, vals);
+      k_gcv_bd_level<<<NGRID, 32, 0, st>>>(rg, phibar, alpha, beta, kdev, kmax, variant, level,
+                                           lams, vals);
       TC_CUDA(cudaGetLastError());
     }
   }
-  k_gcv_bd_final<<<1, 32, 0, st>>>(rg, phibar, kdev, kmax, variant, lambda_in, lams,
-                                   vals, lambda_out, y, gcv_out);
+  k_gcv_bd_final<<<1, 32, 0, st>>>(rg, phibar, kdev, kmax, variant, lambda_in, lams, vals,
+                                   lam_pred, factor, fallback, lambda_out, y, gcv_out);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

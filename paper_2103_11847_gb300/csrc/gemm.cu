@@ -66,42 +66,95 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[k][i][j] = 0.f;
 
-  for (int k0 = kbeg; k0 < kend; k0 += BK) {
-    for (int idx = tid; idx < BM * BK; idx += NT) {
-      const int r = idx / BK, c = idx % BK;
-      const int gi = i0 + r, gk = k0 + c;
-      const bool ok = gi < M && gk < kend;
+  // Register double buffering: the next K tile's global loads are issued
+  // before the current tile's FMAs. Fast path: one float4 per thread and
+  // slice for each of the A and B tiles (16-byte aligned rows).
+  static_assert(BM * BK == 4 * NT && BK * BN == 4 * NT, "one float4 per thread per tile");
+  const bool vec = ((K | N) % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) |
+                                           reinterpret_cast<uintptr_t>(B)) & 15) == 0;
+  const int ar = tid / (BK / 4), ac = (tid % (BK / 4)) * 4;  // A tile: row, first column
+  const int br = tid / (BN / 4), bc = (tid % (BN / 4)) * 4;  // B tile: row, first column
+  float4 ra[NS], rb[NS];
+  auto fetch = [&](int k0) {
 #pragma unroll
-      for (int k = 0; k < NS; ++k) As[k][c][r] = ok ? __ldg(A + k * sA + (size_t)gi * K + gk) : 0.f;
-    }
-    for (int idx = tid; idx < BK * BN; idx += NT) {
-      const int r = idx / BN, c = idx % BN;
-      const int gk = k0 + r, gj = j0 + c;
-      const bool ok = gk < kend && gj < N;
-      float b[NS];
-#pragma unroll
-      for (int l = 0; l < NS; ++l) b[l] = ok ? __ldg(B + l * sB + (size_t)gk * N + gj) : 0.f;
-      if (PRO) {
-#pragma unroll
-        for (int k = 0; k < NS; ++k) {
-          float t = 0.f;
-#pragma unroll
-          for (int l = 0; l < NS; ++l) t = fmaf(f.pro[k * NS + l], b[l], t);
-          Bs[k][r][c] = t;
+    for (int k = 0; k < NS; ++k) {
+      const int gi = i0 + ar, gk = k0 + ac;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (vec) {
+        if (gi < M && gk + 3 < kend) {
+          v = __ldg(reinterpret_cast<const float4*>(A + k * sA + (size_t)gi * K + gk));
+        } else if (gi < M) {
+          const float* src = A + k * sA + (size_t)gi * K;
+          v.x = gk < kend ? __ldg(src + gk) : 0.f;
+          v.y = gk + 1 < kend ? __ldg(src + gk + 1) : 0.f;
+          v.z = gk + 2 < kend ? __ldg(src + gk + 2) : 0.f;
+          v.w = gk + 3 < kend ? __ldg(src + gk + 3) : 0.f;
         }
-      } else {
-#pragma unroll
-        for (int l = 0; l < NS; ++l) Bs[l][r][c] = b[l];
+      } else if (gi < M) {
+        const float* src = A + k * sA + (size_t)gi * K;
+        v.x = gk < kend ? __ldg(src + gk) : 0.f;
+        v.y = gk + 1 < kend ? __ldg(src + gk + 1) : 0.f;
+        v.z = gk + 2 < kend ? __ldg(src + gk + 2) : 0.f;
+        v.w = gk + 3 < kend ? __ldg(src + gk + 3) : 0.f;
       }
+      ra[k] = v;
+      const int gk2 = k0 + br, gj = j0 + bc;
+      float4 u = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (gk2 < kend) {
+        const float* src = B + k * sB + (size_t)gk2 * N;
+        if (vec && gj + 3 < N) {
+          u = __ldg(reinterpret_cast<const float4*>(src + gj));
+        } else {
+          u.x = gj < N ? __ldg(src + gj) : 0.f;
+          u.y = gj + 1 < N ? __ldg(src + gj + 1) : 0.f;
+          u.z = gj + 2 < N ? __ldg(src + gj + 2) : 0.f;
+          u.w = gj + 3 < N ? __ldg(src + gj + 3) : 0.f;
+        }
+      }
+      rb[k] = u;
+    }
+  };
+  if (kbeg < kend) fetch(kbeg);
+  for (int k0 = kbeg; k0 < kend; k0 += BK) {
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      As[k][ac + 0][ar] = ra[k].x;
+      As[k][ac + 1][ar] = ra[k].y;
+      As[k][ac + 2][ar] = ra[k].z;
+      As[k][ac + 3][ar] = ra[k].w;
+    }
+    if (PRO) {
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < NS; ++l) {
+          const float m = f.pro[k * NS + l];
+          t.x = fmaf(m, rb[l].x, t.x);
+          t.y = fmaf(m, rb[l].y, t.y);
+          t.z = fmaf(m, rb[l].z, t.z);
+          t.w = fmaf(m, rb[l].w, t.w);
+        }
+        *reinterpret_cast<float4*>(&Bs[k][br][bc]) = t;
+      }
+    } else {
+#pragma unroll
+      for (int l = 0; l < NS; ++l) *reinterpret_cast<float4*>(&Bs[l][br][bc]) = rb[l];
     }
     __syncthreads();
+    if (k0 + BK < kend) fetch(k0 + BK);
 #pragma unroll
     for (int kk = 0; kk < BK; ++kk) {
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         float a[TM], b[TN];
+        if (TM == 4) {
+          const float4 av = *reinterpret_cast<const float4*>(&As[k][kk][ty * TM]);
+          a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+        } else {
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[k][kk][ty * TM + i];
+          for (int i = 0; i < TM; ++i) a[i] = As[k][kk][ty * TM + i];
+        }
 #pragma unroll
         for (int j = 0; j < TN; ++j) b[j] = Bs[k][kk][tx * TN + j];
 #pragma unroll

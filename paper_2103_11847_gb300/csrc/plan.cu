@@ -45,7 +45,9 @@ void transform_pair(int n, std::vector<double>& M, std::vector<double>& Mi) {
     }
 }
 
-__global__ void k_transpose_slices(const float* __restrict__ in, float* out, int R, int Cc) {
+__global__ void k_transpose_slices(const float* __restrict__ in, float* out, int R, int Cc,
+                                   const int* skip) {
+  if (skip && *skip) return;
   __shared__ float t[32][33];
   const size_t so = (size_t)blockIdx.z * R * Cc;
   const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
@@ -60,9 +62,10 @@ __global__ void k_transpose_slices(const float* __restrict__ in, float* out, int
   }
 }
 
-int transpose_slices(const float* in, float* out, int R, int Cc, int n3, cudaStream_t st) {
+int transpose_slices(const float* in, float* out, int R, int Cc, int n3, cudaStream_t st,
+                     const int* skip = nullptr) {
   dim3 grid((Cc + 31) / 32, (R + 31) / 32, n3);
-  k_transpose_slices<<<grid, dim3(32, 8), 0, st>>>(in, out, R, Cc);
+  k_transpose_slices<<<grid, dim3(32, 8), 0, st>>>(in, out, R, Cc, skip);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -121,6 +124,7 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     int* err = ep.red.status ? ep.red.status : p->dev_err;
     TC_TRY(launch_mode3_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s,
                              p->opts.precision == TC_BF16, ep.skip, st));
+    if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
     return launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
   }
@@ -149,6 +153,7 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     int* err = ep.red.status ? ep.red.status : p->dev_err;
     TC_TRY(launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s,
                              p->opts.precision == TC_BF16, ep.skip, st));
+    if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
     return launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
@@ -234,8 +239,11 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
     p->umf = new UmmaMaps();
     p->uma = new UmmaMaps();
     const int kind = bf16 ? 0 : 1;
-    TC_TRY(make_umma_maps(p->umf, kind, p->AhL, p->tmp1, n1, s, n2, n3));
-    TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, p->tmp1, n2, s, n1, n3));
+    // TF32 reads B K-major: the transformed operand is transposed per slice into tmp3
+    if (!bf16) TC_TRY(dalloc(&p->tmp3, p->tmp_elems));
+    const void* bop = bf16 ? (const void*)p->tmp1 : (const void*)p->tmp3;
+    TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3));
+    TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3));
   }
   TC_TRY(dalloc(&p->scratch.partials, np));
   TC_TRY(dalloc(&p->scratch.tickets, 16));
@@ -252,7 +260,8 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   if (p->lsqr_graph) cudaGraphExecDestroy(p->lsqr_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   float* fs[] = {p->Ah, p->AhT, p->Bh, p->BhT, p->dM, p->dMinv, p->dMinvT, p->dMT,
-                 p->tmp1, p->tmp2, p->lsqr_U, p->lsqr_V, p->lsqr_W, p->basis, p->gm_basis};
+                 p->tmp1, p->tmp2, p->tmp3, p->lsqr_U, p->lsqr_V, p->lsqr_W, p->basis,
+                 p->gm_basis};
   for (float* f : fs) dfree(f);
   dfree(p->scratch.partials);
   dfree(p->scratch.tickets);
@@ -261,6 +270,7 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   dfree(p->gm_dscal);
   dfree(p->gm_flags);
   dfree(p->dev_err);
+  dfree(p->aux);
   dfree(p->AhL);
   dfree(p->AhTL);
   delete p->umf;
@@ -342,8 +352,13 @@ extern "C" int tc_slice_gemm(tc_plan* p, const void* Xh, float* Yh, int adjoint,
     return launch_slice_gemm(adjoint ? p->AhT : p->Ah, static_cast<const float*>(Xh), Yh, M,
                              p->s, K, p->n3, nullptr, nullptr, none, st);
   }
+  const void* bop = Xh;
+  if (p->tmp3) {  // TF32: K-major copy of the operand
+    TC_TRY(transpose_slices(static_cast<const float*>(Xh), p->tmp3, K, p->s, p->n3, st));
+    bop = p->tmp3;
+  }
   UmmaMaps m;
-  TC_TRY(make_umma_maps(&m, p->opts.precision == TC_BF16 ? 0 : 1, adjoint ? p->AhTL : p->AhL, Xh,
+  TC_TRY(make_umma_maps(&m, p->opts.precision == TC_BF16 ? 0 : 1, adjoint ? p->AhTL : p->AhL, bop,
                         M, p->s, K, p->n3));
   return launch_umma(m, Yh, p->dev_err, nullptr, st);
 }

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstring>
 
+#include "mlp.cuh"
 #include "tc_device.cuh"
 
 namespace {
@@ -31,6 +32,8 @@ int grow(T** p, size_t* have, size_t need, bool* moved = nullptr) {
   return TC_OK;
 }
 
+}  // namespace
+
 int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
   bool moved = false;
   if (!p->lsqr_U) {
@@ -52,6 +55,8 @@ int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
   return TC_OK;
 }
 
+namespace {
+
 // alpha_1 = ||A^T U_1|| and beta_1 = ||C|| are in place: set W_1 = V_1 and the
 // Givens state rhobar_1 = alpha_1, phibar_1 = beta_1 (Algorithm 6 step 2).
 __global__ void k_lsqr_init(const double* alpha, const double* beta, double* rhobar,
@@ -70,7 +75,7 @@ __global__ void k_lsqr_info(tc_solve_info* info, const int* flags, const double*
   info->iters = it;
   info->status = flags[2];
   info->cycles = 0;
-  info->pad = 0;
+  info->fallback = flags[7];
   info->resid = fabs(phibar[it]);
   info->lambda = lam ? *lam : nan("");
   info->gcv = gcv ? *gcv : nan("");
@@ -111,24 +116,16 @@ __global__ void k_gmres_info(tc_solve_info* info, const int* flags, const double
   info->iters = flags[1];
   info->status = flags[2];
   info->cycles = flags[5];
-  info->pad = 0;
+  info->fallback = 0;
   info->resid = *resid;
   info->lambda = *lam;
   info->gcv = *gcv;
   info->beta1 = *beta1;
 }
 
-// ----------------------------------------------------------------- LSQR ----
-struct LsqrArgs {
-  const float* C;
-  float* X;
-  float* X_reg;
-  int itermax;
-  double tol, lambda;
-  double* hist;
-  tc_solve_info* info;
-};
+}  // namespace
 
+// ----------------------------------------------------------------- LSQR ----
 int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   const size_t L = (size_t)a.itermax + 2;
   const int kp = a.itermax < TC_MAX_PROJ ? a.itermax : TC_MAX_PROJ;
@@ -141,7 +138,8 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   double* y = gwork + 1200;
   double* lam = y + kp;
   double* gcv = lam + 1;
-  int* flags = p->iflags;
+  double* lam_pred = gcv + 1;
+  int* flags = p->iflags;  // [0] done [1] iterations [2] status [6] stop_at [7] fallback
   float *U = p->lsqr_U, *V = p->lsqr_V, *W = p->lsqr_W;
   const bool keep = a.X_reg != nullptr;
 
@@ -194,11 +192,15 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     // (c)-(g) Givens recurrences and the X, W updates
     float* slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
     TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist,
-                              keep ? rgiv : nullptr, j, a.tol, flags, st));
+                              keep ? rgiv : nullptr, j, a.tol, flags, st,
+                              a.mlp ? flags + 6 : nullptr));
+    if (a.mlp && j + 1 == MLP_FEAT_STEPS)
+      TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   }
   if (keep) {
     TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
-                             a.lambda, gwork, lam, y, gcv, st));
+                             a.mlp ? -1.0 : a.lambda, gwork, lam, y, gcv, st,
+                             a.mlp ? lam_pred : nullptr, a.factor, flags + 7));
     TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
                           st));
   }
@@ -207,8 +209,6 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
-
-}  // namespace
 
 extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int itermax,
                          double tol, double lambda, double* phibar_hist, tc_solve_info* info,

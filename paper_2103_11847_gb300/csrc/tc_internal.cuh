@@ -61,6 +61,7 @@ struct Scratch {
 };
 
 struct UmmaMaps;
+struct tc_mlp;
 
 struct tc_plan {
   int n1, n2, s, n3;
@@ -74,6 +75,7 @@ struct tc_plan {
   float hM[TC_MAX_FUSED * TC_MAX_FUSED], hMinv[TC_MAX_FUSED * TC_MAX_FUSED];
   float hMinvT[TC_MAX_FUSED * TC_MAX_FUSED], hMT[TC_MAX_FUSED * TC_MAX_FUSED];
   float *tmp1 = nullptr, *tmp2 = nullptr;  // transform-domain intermediates
+  float* tmp3 = nullptr;                   // TF32 plans: per-slice transposed GEMM operand
   size_t tmp_elems = 0;
   Scratch scratch;
   // solver workspaces (grow-only)
@@ -90,6 +92,8 @@ struct tc_plan {
   UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
   UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
   int* dev_err = nullptr;         // set by a tensor-core GEMM whose bounded wait gave up
+  void* aux = nullptr;            // tc_lsqr_label workspace (grow-only)
+  size_t aux_bytes = 0;
   cudaStream_t cap_stream = nullptr;
   // graph cache for tc_lsqr_c
   cudaGraphExec_t lsqr_graph = nullptr;
@@ -142,7 +146,7 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
                        double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       cudaStream_t st);
+                       cudaStream_t st, const int* stop_at = nullptr);
 int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
                    const int* kdev, const double* y, size_t n, const int* skip,
                    cudaStream_t st);
@@ -157,12 +161,35 @@ int launch_build_bidiag(const double* alpha, const double* beta, const int* kdev
                         double* H, cudaStream_t st);
 // gcv_bidiag.cu: lambda, GCV and y from LSQR's rotations (rho, theta, phi
 // interleaved in rgiv) without an SVD; work holds 1200 doubles.
-int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha, const double* beta,
-                      const int* kdev, int kmax, int variant, double lambda_in, double* work,
-                      double* lambda_out, double* y, double* gcv_out, cudaStream_t st);
+int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha,
+                      const double* beta, const int* kdev, int kmax, int variant,
+                      double lambda_in, double* work, double* lambda_out, double* y,
+                      double* gcv_out, cudaStream_t st, const double* lam_pred = nullptr,
+                      double factor = 0.0, int* fallback = nullptr);
 
 // plan.cu helpers used by solvers
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st);
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st);
 Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
 int tc_kernels_init();
+
+// solvers.cu: the c-LSQR solve as a sequence of launches on one stream
+// (capturable), and the workspaces it needs.
+struct LsqrArgs {
+  const float* C;
+  float* X;
+  float* X_reg;
+  int itermax;
+  double tol, lambda;
+  double* hist;
+  tc_solve_info* info;
+  const tc_mlp* mlp = nullptr;  // learned stop index and lambda (learned.cu)
+  double factor = 1.05;         // GCV fallback threshold for the learned lambda
+};
+// learned.cu: after MLP_FEAT_STEPS steps, features -> network -> lam_pred and
+// stop_at (the step count to stop after).
+int launch_learned_predict(const tc_mlp* m, const double* alpha, const double* beta,
+                           const double* phibar, int kmax, double* lam_pred, int* stop_at,
+                           cudaStream_t st);
+int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis);
+int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st);

@@ -1,10 +1,11 @@
 // Mode-3 transform pass for n3 > TC_MAX_FUSED (Remark 2.1: X~ = X x_3 T with
 // T one of M, M^{-1}, M^{-T}, M^T): out[k][p] = ca * sum_l T[k][l] in[l][p]
 // + cp * prev[k][p], with the fused reduction of the epilogue. Each CTA owns
-// 128 consecutive pixels p of every slice: warp w computes the outputs
-// k = w, w+8, w+16, ... and lane q the pixels 4q..4q+3. Inputs stream through
-// shared memory 32 slices at a time; HBM traffic is one read of `in` (and
-// `prev`) and one write of `out`.
+// 128 consecutive pixels p of every slice: warp w computes the KPW contiguous
+// outputs k = w*KPW .. w*KPW + KPW - 1 (coefficients read as float4
+// broadcasts) and lane q the pixels 4q..4q+3. Inputs stream through shared
+// memory 32 slices at a time; HBM traffic is one read of `in` (and `prev`)
+// and one write of `out`.
 #include <cuda_bf16.h>
 
 #include "tc_device.cuh"
@@ -31,10 +32,14 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
         size_t P, Epi ep) {
   if (ep.skip && *ep.skip) return;
   __shared__ __align__(16) float xs[LC][PB];
-  __shared__ float ts[LC][8 * KPW];
+  __shared__ __align__(16) float ts[LC][8 * KPW];
   __shared__ float sh_coef[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const size_t p0 = (size_t)blockIdx.x * PB;
+  // float4 path: whole groups of 4 pixels and 16-byte aligned tensors
+  auto al16 = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const bool vec = (P % 4 == 0) && al16(in) && al16(out_v) && (!ep.prev || al16(ep.prev)) &&
+                   (!ep.red.other || al16(ep.red.other));
   float acc[KPW][4];
 #pragma unroll
   for (int q = 0; q < KPW; ++q)
@@ -43,10 +48,20 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
 
   for (int l0 = 0; l0 < n3; l0 += LC) {
     const int lc_n = min(LC, n3 - l0);
-    for (int idx = tid; idx < LC * PB; idx += 256) {
-      const int lc = idx / PB, px = idx % PB;
-      const size_t p = p0 + px;
-      xs[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
+    if (vec) {
+      for (int idx = tid; idx < LC * PB / 4; idx += 256) {
+        const int lc = idx / (PB / 4), px = (idx % (PB / 4)) * 4;
+        const size_t p = p0 + px;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (lc < lc_n && p < P) v = __ldg(reinterpret_cast<const float4*>(in + (size_t)(l0 + lc) * P + p));
+        *reinterpret_cast<float4*>(&xs[lc][px]) = v;
+      }
+    } else {
+      for (int idx = tid; idx < LC * PB; idx += 256) {
+        const int lc = idx / PB, px = idx % PB;
+        const size_t p = p0 + px;
+        xs[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
+      }
     }
     for (int idx = tid; idx < LC * 8 * KPW; idx += 256) {
       const int lc = idx / (8 * KPW), k = idx % (8 * KPW);
@@ -55,13 +70,23 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
     __syncthreads();
     for (int lc = 0; lc < lc_n; ++lc) {
       const float4 x = *reinterpret_cast<const float4*>(&xs[lc][lane * 4]);
+      float t[KPW];  // warp w owns the contiguous outputs k = w*KPW .. w*KPW + KPW - 1
+      if (KPW % 4 == 0) {
+#pragma unroll
+        for (int q = 0; q < KPW; q += 4) {
+          const float4 tv = *reinterpret_cast<const float4*>(&ts[lc][w * KPW + q]);
+          t[q] = tv.x; t[q + 1] = tv.y; t[q + 2] = tv.z; t[q + 3] = tv.w;
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < KPW; ++q) t[q] = ts[lc][w * KPW + q];
+      }
 #pragma unroll
       for (int q = 0; q < KPW; ++q) {
-        const float t = ts[lc][w + 8 * q];
-        acc[q][0] = fmaf(t, x.x, acc[q][0]);
-        acc[q][1] = fmaf(t, x.y, acc[q][1]);
-        acc[q][2] = fmaf(t, x.z, acc[q][2]);
-        acc[q][3] = fmaf(t, x.w, acc[q][3]);
+        acc[q][0] = fmaf(t[q], x.x, acc[q][0]);
+        acc[q][1] = fmaf(t[q], x.y, acc[q][1]);
+        acc[q][2] = fmaf(t[q], x.z, acc[q][2]);
+        acc[q][3] = fmaf(t[q], x.w, acc[q][3]);
       }
     }
     __syncthreads();
@@ -70,7 +95,7 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
   if (OUT != OUT_F32) {  // operand of a tensor-core GEMM: store only
 #pragma unroll
     for (int q = 0; q < KPW; ++q) {
-      const int k = w + 8 * q;
+      const int k = w * KPW + q;
       if (k >= n3) continue;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -93,11 +118,31 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
   float local = 0.f;
 #pragma unroll
   for (int q = 0; q < KPW; ++q) {
-    const int k = w + 8 * q;
+    const int k = w * KPW + q;
     if (k >= n3) continue;
+    const size_t pb = p0 + lane * 4;
+    if (vec && pb + 4 <= P) {
+      const size_t idx = (size_t)k * P + pb;
+      float4 o = make_float4(ca * acc[q][0], ca * acc[q][1], ca * acc[q][2], ca * acc[q][3]);
+      if (ep.prev) {
+        const float4 pv = *reinterpret_cast<const float4*>(ep.prev + idx);
+        o.x = fmaf(cp, pv.x, o.x); o.y = fmaf(cp, pv.y, o.y);
+        o.z = fmaf(cp, pv.z, o.z); o.w = fmaf(cp, pv.w, o.w);
+      }
+      *reinterpret_cast<float4*>(out + idx) = o;
+      if (ep.red.out) {
+        if (ep.red.other) {
+          const float4 ov = *reinterpret_cast<const float4*>(ep.red.other + idx);
+          local = fmaf(o.x, ov.x, fmaf(o.y, ov.y, fmaf(o.z, ov.z, fmaf(o.w, ov.w, local))));
+        } else {
+          local = fmaf(o.x, o.x, fmaf(o.y, o.y, fmaf(o.z, o.z, fmaf(o.w, o.w, local))));
+        }
+      }
+      continue;
+    }
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
-      const size_t p = p0 + lane * 4 + e;
+      const size_t p = pb + e;
       if (p < P) {
         const size_t idx = (size_t)k * P + p;
         float o = ca * acc[q][e];

@@ -10,9 +10,10 @@
 //   warp 1, one lane : issues tcgen05.mma (kind::f16 with BF16 inputs, or
 //                      kind::tf32) and tcgen05.commit to release each stage;
 //   all four warps   : epilogue, tcgen05.ld of 32 lanes x 32 columns at a time.
-// A is read K-major and B MN-major straight from the row-major tensors, so
-// neither operand is transposed in memory. Each CTA fetches its own tiles (no
-// cluster multicast).
+// A is read K-major. B is read MN-major straight from the row-major K x N
+// operand for BF16. For TF32 it is read K-major from a per-slice transposed
+// copy (N x K): kind::tf32 with an MN-major B left the accumulator unchanged
+// on this part. Each CTA fetches its own tiles (no cluster multicast).
 //
 // Every mbarrier wait is bounded. A wait that gives up raises *err, and the
 // CTA skips the rest of its work, waits (bounded) for the copies it issued,
@@ -26,7 +27,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, STAGES = 4, NT = 128;
+constexpr int BM = 128, BN = 128, STAGES = 3, NT = 128;  // 97 KB smem: 2 CTAs per SM
 constexpr uint32_t A_BYTES = BM * 128;   // 128 rows of one 128-byte K slab
 constexpr uint32_t B_BYTES = 128 * BN;   // (128 / elem) K rows x BN columns
 constexpr int kSpin = 1 << 22;           // try_wait polls before giving up
@@ -124,8 +125,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 }
 
 // KIND 0: BF16 inputs (kind::f16), KIND 1: TF32 inputs (kind::tf32).
-template <int KIND>
-__global__ void __launch_bounds__(NT, 1)
+// BKMAJ: B given as N x K per slice (K contiguous) instead of K x N.
+template <int KIND, int BKMAJ>
+__global__ void __launch_bounds__(NT, 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             float* __restrict__ D, int M, int N, int K, int* err, const int* skip) {
   constexpr int ES = KIND == 0 ? 2 : 4;       // bytes per element
@@ -135,7 +137,8 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr int NBOX = BN / NATOM;            // B boxes per stage
   constexpr uint32_t B_COL = BKE * 128;       // bytes of one B atom column
   constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;  // BF16 : TF32
-  constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | (0u << 15) | (1u << 16) |
+  constexpr uint32_t BMAJ = BKMAJ ? 0u : 1u;  // 0: K-major, 1: MN-major
+  constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | (0u << 15) | (BMAJ << 16) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   if (skip && *skip) return;
   extern __shared__ uint8_t dsm_raw[];
@@ -185,9 +188,13 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       }
       mbar_expect_tx(full + s, A_BYTES + B_BYTES);
       tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, z, full + s);
+      if (BKMAJ) {
+        tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, z, full + s);
+      } else {
 #pragma unroll
-      for (int b = 0; b < NBOX; ++b)
-        tma_load_3d(sB + s * B_BYTES + b * B_COL, &tmB, n0 + b * NATOM, kb * BKE, z, full + s);
+        for (int b = 0; b < NBOX; ++b)
+          tma_load_3d(sB + s * B_BYTES + b * B_COL, &tmB, n0 + b * NATOM, kb * BKE, z, full + s);
+      }
       issued = kb + 1;
     }
   } else if (warp == 1 && lane == 0) {
@@ -202,8 +209,9 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
 #pragma unroll
       for (int kk = 0; kk < BKE / UK; ++kk) {
-        const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);   // K-major: advance in the row
-        const uint64_t bd = smem_desc(b0 + kk * UK * 128, B_COL, 1024);  // MN-major: advance UK rows
+        const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);  // K-major: advance in the row
+        const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
+                                  : smem_desc(b0 + kk * UK * 128, B_COL, 1024);  // MN: UK rows
         umma<KIND>(tmem, ad, bd, IDESC, (kb | kk) != 0);
       }
       umma_commit(empty + s);
@@ -252,9 +260,9 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }  // namespace
 
 int umma_init() {
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_bytes()));
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)smem_bytes()));
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
@@ -286,13 +294,17 @@ int make_tmap(CUtensorMap* map, const void* base, int bf16, int inner, int rows,
   return r == CUDA_SUCCESS ? TC_OK : TC_EINVAL;
 }
 
-// A operand: M x K per slice, K contiguous. B operand: K x N, N contiguous.
+// A operand: M x K per slice, K contiguous. B operand: K x N with N contiguous
+// (BF16), or its transpose N x K with K contiguous (TF32).
 int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, int N, int K,
                    int slices) {
   const int bf16 = kind == 0;
   const int bke = bf16 ? 64 : 32;
   TC_TRY(make_tmap(&m->a, A, bf16, K, M, slices, bke, BM));
-  TC_TRY(make_tmap(&m->b, B, bf16, N, K, slices, bke == 64 ? 64 : 32, bke));
+  if (bf16)
+    TC_TRY(make_tmap(&m->b, B, bf16, N, K, slices, 64, bke));
+  else
+    TC_TRY(make_tmap(&m->b, B, bf16, K, N, slices, bke, BN));
   m->M = M;
   m->N = N;
   m->K = K;
@@ -304,9 +316,9 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
   dim3 grid((m.N + BN - 1) / BN, (m.M + BM - 1) / BM, m.slices);
   if (m.kind == 0)
-    k_umma_gemm<0><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
+    k_umma_gemm<0, 0><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
   else
-    k_umma_gemm<1><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
+    k_umma_gemm<1, 1><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

@@ -7,7 +7,7 @@
 
 struct UmmaMaps {
   CUtensorMap a;  // M x K per slice, K contiguous (K-major operand)
-  CUtensorMap b;  // K x N per slice, N contiguous (MN-major operand)
+  CUtensorMap b;  // BF16: K x N per slice (MN-major); TF32: N x K per slice (K-major)
   int M = 0, N = 0, K = 0, slices = 0, kind = 0;  // kind 0: BF16, 1: TF32
 };
 

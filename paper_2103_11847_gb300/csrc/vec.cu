@@ -55,7 +55,8 @@ k_scale(const float* __restrict__ in, float* out, size_t n, Coef c, const float*
 __global__ void __launch_bounds__(NT)
 k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot, size_t n,
               const double* alpha, const double* beta, double* rhobar, double* phibar,
-              double* phibar_hist, double* rgiv, int j, double tol, int* flags) {
+              double* phibar_hist, double* rgiv, int j, double tol, int* flags,
+              const int* stop_at) {
   if (flags[0]) return;
   __shared__ float sh[4];
   __shared__ int sh_stop;
@@ -69,7 +70,8 @@ k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot
     const double pbn = -s * pb;
     const bool finite = isfinite(a) && isfinite(b) && isfinite(rho);
     const bool brk = (a == 0.0);
-    const bool conv = fabs(pbn) < tol;
+    // converged, or reached the step count a learned predictor chose
+    const bool conv = fabs(pbn) < tol || (stop_at && *stop_at > 0 && j + 1 >= *stop_at);
     sh[0] = (float)(phi / rho);
     sh[1] = brk ? 0.f : (float)(1.0 / a);
     sh[2] = (float)(theta / rho);
@@ -165,9 +167,9 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
                        double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       cudaStream_t st) {
+                       cudaStream_t st, const int* stop_at) {
   k_lsqr_update<<<grid_for(n, 8), NT, 0, st>>>(X, W, V, basis_slot, n, alpha, beta, rhobar,
-                                               phibar, phibar_hist, rgiv, j, tol, flags);
+                                               phibar, phibar_hist, rgiv, j, tol, flags, stop_at);
   TC_CUDA(cudaGetLastError());
   k_lsqr_flag<<<1, 1, 0, st>>>(flags);
   TC_CUDA(cudaGetLastError());

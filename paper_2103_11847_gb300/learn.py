@@ -1,0 +1,140 @@
+"""Learned lambda and stopping index for c-LSQR: training data from the solver,
+training with the library's own network kernels, and a comparison against
+plain GCV-driven c-LSQR. All arithmetic runs in libtcprod. This module only
+draws the synthetic problems and moves tensors around.
+
+Training problems: n x n x 3 colour images (default n = 128). Slice k of A
+is (1, 0.7, 0.4)[k] times a Gaussian blur, with sigma on a 32-level grid in
+[1, 5]. Noise is log-uniform in [1e-4, 1e-2]. The observation C = A *c X + N
+is formed by the library's product. Each problem is labelled by
+tc_lsqr_label: the error-optimal stop index and lambda of its c-LSQR
+trajectory.
+"""
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import inputs, tcprod
+
+SIGMA_LEVELS = np.linspace(1.0, 5.0, 32)
+
+
+class ProblemSource:
+    """Seeded stream of blur problems; plans are cached per sigma level."""
+
+    def __init__(self, n, seed, frames=3):
+        self.n, self.frames = n, frames
+        self.rng = inputs.rng_for(seed)
+        self.plans = {}
+
+    def plan(self, lvl):
+        if lvl not in self.plans:
+            s = float(SIGMA_LEVELS[lvl])
+            G = inputs.gaussian_blur(self.n, s, int(math.ceil(3 * s)))
+            w = (1.0, 0.7, 0.4) if self.frames == 3 else np.linspace(1.0, 0.4, self.frames)
+            A = torch.from_numpy(np.stack([wi * G for wi in w]).astype(np.float32)).cuda()
+            self.plans[lvl] = (tcprod.Plan(A, s=self.n), A)
+        return self.plans[lvl][0]
+
+    def draw(self):
+        lvl = int(self.rng.integers(len(SIGMA_LEVELS)))
+        nu = float(10.0 ** self.rng.uniform(-4.0, -2.0))
+        if self.frames == 3:
+            X = inputs.image(self.n, self.rng)
+        else:
+            X = inputs.video(self.n, self.frames, self.rng)
+        Gn = inputs.gaussian_noise(X.shape, self.rng)
+        plan = self.plan(lvl)
+        Xt = torch.from_numpy(X.astype(np.float32)).cuda()
+        Cc = plan.cprod(Xt)
+        Gt = torch.from_numpy(Gn.astype(np.float32)).cuda()
+        C = (Cc + (nu * Cc.norm() / Gt.norm()) * Gt).contiguous()
+        return plan, C, Xt, float(SIGMA_LEVELS[lvl]), nu
+
+    def close(self):
+        for p, _ in self.plans.values():
+            p.close()
+        self.plans = {}
+
+
+def training_data(count, n=128, kmax=32, seed=11):
+    """Features (count x 36) and targets (count x 2: log lambda, stop index)."""
+    src = ProblemSource(n, seed)
+    F = torch.empty((count, 36), device="cuda")
+    T = torch.empty((count, 2), device="cuda")
+    for i in range(count):
+        plan, C, Xt, _, _ = src.draw()
+        tcprod.tc_lsqr_label(plan.handle, C, Xt, kmax, F[i], T[i])
+    torch.cuda.synchronize()
+    src.close()
+    return F, T
+
+
+def train(F, T, steps=3000, batch=256, lr=2e-3, seed=5):
+    """Normalise (tc_mlp_fit_norm), shuffle once, Adam (tc_mlp_train)."""
+    mlp = tcprod.Mlp(seed=seed)
+    Xn, Tn = mlp.fit_norm(F.contiguous(), T.contiguous())
+    perm = torch.from_numpy(inputs.rng_for(seed).permutation(F.shape[0])).cuda()
+    hist = mlp.train(Xn[perm].contiguous(), Tn[perm].contiguous(), batch, steps, lr)
+    torch.cuda.synchronize()
+    return mlp, hist
+
+
+def compare(mlp, count=8, n=512, frames=3, kmax=40, factor=1.05, seed=23):
+    """Plain GCV-driven c-LSQR (kmax steps) against the learned solve on
+    held-out problems: relative errors of X_reg and solve times."""
+    src = ProblemSource(n, seed, frames=frames)
+    rows = []
+    st = torch.cuda.current_stream()
+    for _ in range(count):
+        plan, C, Xt, sigma, nu = src.draw()
+        X = torch.empty_like(Xt)
+        Xr_p = torch.empty_like(Xt)
+        Xr_l = torch.empty_like(Xt)
+        info_p, info_l = tcprod.new_info(), tcprod.new_info()
+        for _warm in range(2):
+            tcprod.tc_lsqr_c(plan.handle, C, X, Xr_p, kmax, 0.0, None, None, info_p)
+            tcprod.tc_lsqr_c_learned(plan.handle, mlp, C, X, Xr_l, kmax, factor, info_l)
+        torch.cuda.synchronize()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e[0].record(st)
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr_p, kmax, 0.0, None, None, info_p)
+        e[1].record(st)
+        e[2].record(st)
+        tcprod.tc_lsqr_c_learned(plan.handle, mlp, C, X, Xr_l, kmax, factor, info_l)
+        e[3].record(st)
+        torch.cuda.synchronize()
+        ip, il = tcprod.read_info(info_p), tcprod.read_info(info_l)
+        rows.append(dict(sigma=sigma, nu=nu,
+                         err_plain=float((Xr_p - Xt).norm() / Xt.norm()),
+                         err_learned=float((Xr_l - Xt).norm() / Xt.norm()),
+                         ms_plain=e[0].elapsed_time(e[1]), ms_learned=e[2].elapsed_time(e[3]),
+                         iters_learned=il["iters"], lam_plain=ip["lam"], lam_learned=il["lam"],
+                         fallback=il["fallback"]))
+    src.close()
+    return rows
+
+
+def summarize(rows):
+    ep = np.array([r["err_plain"] for r in rows])
+    el = np.array([r["err_learned"] for r in rows])
+    tp = np.array([r["ms_plain"] for r in rows])
+    tl = np.array([r["ms_learned"] for r in rows])
+    return dict(problems=len(rows), mean_err_plain=float(ep.mean()), mean_err_learned=float(el.mean()),
+                learned_better=int(np.sum(el < ep)), mean_ms_plain=float(tp.mean()),
+                mean_ms_learned=float(tl.mean()), speedup=float(tp.mean() / tl.mean()),
+                mean_iters_learned=float(np.mean([r["iters_learned"] for r in rows])),
+                fallbacks=int(sum(r["fallback"] for r in rows)))
+
+
+if __name__ == "__main__":
+    t0 = time.time()
+    F, T = training_data(20000)
+    t1 = time.time()
+    mlp, hist = train(F, T)
+    print(f"data {t1 - t0:.1f} s, train {time.time() - t1:.1f} s, loss {hist[0].item():.4f} -> "
+          f"{hist[-50:].mean().item():.4f}")
+    print("512x512x3:", summarize(compare(mlp)))
+    print("512x512x32:", summarize(compare(mlp, count=2, frames=32)))

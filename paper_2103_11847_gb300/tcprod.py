@@ -27,7 +27,7 @@ class tc_opts(ctypes.Structure):
 
 
 class tc_solve_info(ctypes.Structure):
-    _fields_ = [("iters", c_int), ("status", c_int), ("cycles", c_int), ("pad", c_int),
+    _fields_ = [("iters", c_int), ("status", c_int), ("cycles", c_int), ("fallback", c_int),
                 ("resid", c_double), ("lambda_", c_double), ("gcv", c_double),
                 ("beta1", c_double)]
 
@@ -52,6 +52,25 @@ _SIGS = {
                          c_void_p, c_void_p], c_int),
     "tc_fro_norm_noalloc": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p], c_int),
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
+    "tc_batch_create": ([ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int),
+                         ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
+                         ctypes.POINTER(c_void_p), ctypes.POINTER(tc_opts), c_void_p], c_int),
+    "tc_batch_destroy": ([c_void_p], c_int),
+    "tc_mlp_create": ([ctypes.POINTER(c_void_p), ctypes.c_ulonglong, c_void_p], c_int),
+    "tc_mlp_destroy": ([c_void_p], c_int),
+    "tc_mlp_set_params": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_mlp_get_params": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_mlp_forward": ([c_void_p, c_void_p, c_int, c_void_p, c_void_p], c_int),
+    "tc_mlp_loss_grad": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_mlp_fit_norm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_mlp_train": ([c_void_p, c_void_p, c_void_p, c_int, c_int, c_int, ctypes.c_float, c_void_p,
+                      c_void_p], c_int),
+    "tc_lsqr_label": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_lsqr_c_learned": ([c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double,
+                           c_void_p, c_void_p], c_int),
+    "tc_lsqr_c_batched": ([c_void_p, ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p),
+                           ctypes.POINTER(c_void_p), c_int, c_double, c_double, c_void_p,
+                           c_void_p], c_int),
 }
 
 _LIB = None
@@ -157,7 +176,7 @@ def read_info(buf):
     raw = bytes(buf.cpu().numpy().tobytes())
     info = tc_solve_info.from_buffer_copy(raw)
     return dict(iters=info.iters, status=STATUS_NAMES.get(info.status, info.status),
-                cycles=info.cycles, resid=info.resid, lam=info.lambda_, gcv=info.gcv,
+                cycles=info.cycles, fallback=info.fallback, resid=info.resid, lam=info.lambda_, gcv=info.gcv,
                 beta1=info.beta1)
 
 
@@ -192,6 +211,119 @@ def tc_fro_norm_noalloc(X, out, stream=None):
     """||X||_F into the device double `out`, using no device allocation."""
     _check("tc_fro_norm_noalloc", lib().tc_fro_norm_noalloc(
         _ptr(X, name="X"), X.numel(), _ptr(out, torch.float64, name="out"), _stream(stream)))
+
+
+def _ptr_array(ts, name):
+    arr = (c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t, name=f"{name}[{i}]")
+    return arr
+
+
+def tc_batch_create(As, ss, precision=TC_FP32, gcv_variant=TC_GCV_PAPER, stream=None):
+    """As: list of (n3, n1_i, n2_i) CUDA tensors; ss: list of column counts."""
+    n = len(As)
+    n3 = As[0].shape[0]
+    n1 = (c_int * n)(*[a.shape[1] for a in As])
+    n2 = (c_int * n)(*[a.shape[2] for a in As])
+    sv = (c_int * n)(*ss)
+    o = tc_opts(precision, gcv_variant, 1)
+    h = c_void_p()
+    _check("tc_batch_create", lib().tc_batch_create(ctypes.byref(h), n, n1, n2, sv, n3,
+                                                    _ptr_array(As, "A"), ctypes.byref(o),
+                                                    _stream(stream)))
+    return h
+
+
+def tc_batch_destroy(h):
+    _check("tc_batch_destroy", lib().tc_batch_destroy(h))
+
+
+def tc_lsqr_c_batched(h, Cs, Xs, Xregs, itermax, tol, lam, infos, stream=None):
+    """infos: device uint8 tensor of len(Cs) * sizeof(tc_solve_info) bytes."""
+    _check("tc_lsqr_c_batched", lib().tc_lsqr_c_batched(
+        h, _ptr_array(Cs, "C"), _ptr_array(Xs, "X"),
+        _ptr_array(Xregs, "X_reg") if Xregs is not None else None, itermax, tol,
+        -1.0 if lam is None else float(lam), _ptr(infos, torch.uint8), _stream(stream)))
+
+
+def new_infos(count):
+    return torch.zeros(count * ctypes.sizeof(tc_solve_info), dtype=torch.uint8, device="cuda")
+
+
+def read_infos(buf, count):
+    sz = ctypes.sizeof(tc_solve_info)
+    return [read_info(buf[i * sz:(i + 1) * sz]) for i in range(count)]
+
+
+MLP_NPARAMS, MLP_NORM = 6658, 76
+
+
+class Mlp:
+    """The learned-lambda network (tc_mlp_*): thin wrapper over the C calls."""
+
+    def __init__(self, seed=0):
+        self.handle = c_void_p()
+        _check("tc_mlp_create", lib().tc_mlp_create(ctypes.byref(self.handle), seed, _stream(None)))
+
+    def close(self):
+        if self.handle is not None:
+            lib().tc_mlp_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta=None, norm=None):
+        _check("tc_mlp_set_params", lib().tc_mlp_set_params(
+            self.handle, _ptr(theta, name="theta"), _ptr(norm, name="norm"), _stream(None)))
+
+    def get_params(self):
+        theta = torch.empty(MLP_NPARAMS, device="cuda")
+        norm = torch.empty(MLP_NORM, device="cuda")
+        _check("tc_mlp_get_params", lib().tc_mlp_get_params(self.handle, _ptr(theta), _ptr(norm),
+                                                            _stream(None)))
+        return theta, norm
+
+    def forward(self, X):
+        Y = torch.empty((X.shape[0], 2), device="cuda")
+        _check("tc_mlp_forward", lib().tc_mlp_forward(self.handle, _ptr(X), X.shape[0], _ptr(Y),
+                                                      _stream(None)))
+        return Y
+
+    def loss_grad(self, X, T):
+        loss = torch.empty(1, device="cuda")
+        grad = torch.empty(MLP_NPARAMS, device="cuda")
+        _check("tc_mlp_loss_grad", lib().tc_mlp_loss_grad(self.handle, _ptr(X), _ptr(T), X.shape[0],
+                                                          _ptr(loss), _ptr(grad), _stream(None)))
+        return loss, grad
+
+    def fit_norm(self, Xraw, Traw):
+        Xn, Tn = torch.empty_like(Xraw), torch.empty_like(Traw)
+        _check("tc_mlp_fit_norm", lib().tc_mlp_fit_norm(self.handle, _ptr(Xraw), _ptr(Traw),
+                                                        Xraw.shape[0], _ptr(Xn), _ptr(Tn),
+                                                        _stream(None)))
+        return Xn, Tn
+
+    def train(self, Xn, Tn, batch, steps, lr):
+        hist = torch.empty(steps, device="cuda")
+        _check("tc_mlp_train", lib().tc_mlp_train(self.handle, _ptr(Xn), _ptr(Tn), Xn.shape[0], batch,
+                                                  steps, lr, _ptr(hist), _stream(None)))
+        return hist
+
+
+def tc_lsqr_label(h, C, X_true, kmax, feat, target, stream=None):
+    _check("tc_lsqr_label", lib().tc_lsqr_label(h, _ptr(C), _ptr(X_true), kmax, _ptr(feat),
+                                                _ptr(target), _stream(stream)))
+
+
+def tc_lsqr_c_learned(h, mlp, C, X, X_reg, kmax, gcv_factor, info, stream=None):
+    _check("tc_lsqr_c_learned", lib().tc_lsqr_c_learned(h, mlp.handle, _ptr(C), _ptr(X), _ptr(X_reg),
+                                                        kmax, gcv_factor, _ptr(info, torch.uint8),
+                                                        _stream(stream)))
 
 
 class Plan:

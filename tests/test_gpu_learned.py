@@ -1,0 +1,171 @@
+"""The learned lambda / stop index: the network's forward pass, gradient and
+Adam step against the FP64 oracle (oracle/mlp.py), training, the labels, and
+the learned solve's mechanics (the stop index and the GCV fallback).
+
+Tolerances: the network runs in FP32 with BF16 weights. The oracle is given
+the same BF16-rounded weights, so forward and gradient agree to FP32
+accumulation error (1e-4 relative)."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cproduct as cp
+from oracle import krylov as kr
+from oracle import mlp as om
+from paper_2103_11847_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_11847_gb300 import tcprod
+    tcprod.lib()
+    return tcprod
+
+
+def bf16_round(a):
+    """Round float32 values to BF16 (nearest, ties to even), back in float32."""
+    u = np.asarray(a, np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32)
+
+
+def weights_as_used(theta):
+    """The weight matrices rounded to BF16, biases kept in FP32 (oracle layout)."""
+    th = np.asarray(theta, np.float32).copy()
+    o = 0
+    for a, b in zip(om.SIZES[:-1], om.SIZES[1:]):
+        th[o:o + a * b] = bf16_round(th[o:o + a * b])
+        o += a * b + b
+    return th.astype(np.float64)
+
+
+def test_forward_and_gradient_match_oracle(tc):
+    rng = np.random.default_rng(1)
+    theta = (rng.standard_normal(om.nparams()) * 0.15).astype(np.float32)
+    X = rng.standard_normal((37, 36)).astype(np.float32)
+    T = rng.standard_normal((37, 2)).astype(np.float32)
+    m = tc.Mlp(seed=3)
+    m.set_params(torch.from_numpy(theta).cuda())
+    Y = m.forward(torch.from_numpy(X).cuda()).cpu().numpy()
+    loss, grad = m.loss_grad(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda())
+    th = weights_as_used(theta)
+    Yr, _ = om.forward(th, X)
+    Lr, gr = om.loss_and_grad(th, X, T)
+    assert np.abs(Y - Yr).max() < 1e-4 * np.abs(Yr).max()
+    assert abs(loss.item() - Lr) < 1e-5 * Lr
+    g = grad.cpu().numpy()
+    assert np.linalg.norm(g - gr) < 1e-4 * np.linalg.norm(gr)
+
+
+def test_adam_step_matches_oracle(tc):
+    rng = np.random.default_rng(2)
+    theta = (rng.standard_normal(om.nparams()) * 0.1).astype(np.float32)
+    X = rng.standard_normal((64, 36)).astype(np.float32)
+    T = rng.standard_normal((64, 2)).astype(np.float32)
+    m = tc.Mlp(seed=4)
+    m.set_params(torch.from_numpy(theta).cuda())
+    m.train(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), 64, 1, 1e-2)
+    th_gpu, _ = m.get_params()
+    _, g = om.loss_and_grad(weights_as_used(theta), X, T)
+    th_ref, _, _ = om.adam_step(theta.astype(np.float64), g, np.zeros_like(g), np.zeros_like(g), 1,
+                                1e-2)
+    d = th_gpu.cpu().numpy() - th_ref
+    # each parameter moves by ~lr; agreement to a small fraction of the step
+    assert np.abs(d).max() < 1e-4
+
+
+def test_training_reduces_loss(tc):
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal((2048, 36)).astype(np.float32)
+    W = rng.standard_normal((36, 2)).astype(np.float32) * 0.3
+    T = np.tanh(X @ W).astype(np.float32)
+    m = tc.Mlp(seed=5)
+    hist = m.train(torch.from_numpy(X).cuda(), torch.from_numpy(T).cuda(), 256, 400, 3e-3)
+    h = hist.cpu().numpy()
+    assert h[-20:].mean() < 0.1 * h[:5].mean()
+
+
+def test_label_matches_oracle_on_well_conditioned_problem(tc):
+    # Mild blur (sigma 1) where FP32 tracks FP64 over 16 steps: the stop index
+    # and lambda found from the GPU basis agree with an FP64 oracle labelling.
+    n, kmax = 48, 16
+    G = inputs.gaussian_blur(n, 1.0, 3)
+    A = np.stack([w * G for w in (1.0, 0.7, 0.4)]).astype(np.float32).astype(np.float64)
+    rng = inputs.rng_for(9)
+    X = inputs.image(n, rng)
+    C = inputs.scale_noise(cp.cprod(A, X), rng.standard_normal(X.shape), 1e-2)
+    C = C.astype(np.float32).astype(np.float64)
+    plan = tc.Plan(torch.from_numpy(A.astype(np.float32)).cuda(), s=n)
+    feat = torch.empty(36, device="cuda")
+    targ = torch.empty(2, device="cuda")
+    tc.tc_lsqr_label(plan.handle, torch.from_numpy(C.astype(np.float32)).cuda(),
+                     torch.from_numpy(X.astype(np.float32)).cuda(), kmax, feat, targ)
+    torch.cuda.synchronize()
+    op = lambda Z: cp.cprod(A, Z)
+    adj = lambda Y: cp.cprod_adjoint(A, Y)
+    r = kr.lsqr(op, adj, C, itermax=kmax, keep_basis=True)
+    fo = om.features(r["alpha"], r["beta"], r["phibar"])
+    assert np.abs(feat.cpu().numpy() - fo).max() < 1e-3
+    # oracle labels on the same grid: k in {4, 6, .., 16}, 48 lambdas in [1e-6, 1] ||C~||
+    H = kr.bidiagonal(r["alpha"], r["beta"], kmax)
+    s = np.linalg.norm(H)
+    lams = np.exp(np.log(s) - 6 * np.log(10) + 6 * np.log(10) * np.arange(48) / 47)
+    err = {}
+    for k in range(4, kmax + 1, 2):
+        Hk = kr.bidiagonal(r["alpha"], r["beta"], k)
+        for li, lam in enumerate(lams):
+            from oracle import regularize as rg
+            y = rg.tikhonov_solve(Hk, r["beta"][0], lam)
+            Xk = cp.circledast(r["V"][:k], y)
+            err[(k, li)] = np.sum((Xk - X) ** 2)
+    best = min(err.values())
+    kopt = min(k for k in range(4, kmax + 1, 2)
+               if min(err[(k, li)] for li in range(48)) <= best * 1.0201)
+    lopt = min(range(48), key=lambda li: err[(kopt, li)])
+    t = targ.cpu().numpy()
+    assert int(t[1]) == kopt
+    assert abs(t[0] - np.log(lams[lopt])) <= 2 * 6 * np.log(10) / 47 + 1e-4  # within 2 grid steps
+
+
+def test_learned_solve_stop_index_and_fallback(tc):
+    # An untrained network with gcv_factor 1: its lambda fails the GCV check,
+    # so the solve falls back to GCV and must equal plain c-LSQR + GCV run for
+    # the predicted number of steps (same kernels, bit for bit).
+    from paper_2103_11847_gb300 import learn
+    src = learn.ProblemSource(64, seed=31)
+    plan, C, Xt, _, _ = src.draw()
+    m = tc.Mlp(seed=7)
+    X = torch.empty_like(Xt)
+    Xr = torch.empty_like(Xt)
+    info = tc.new_info()
+    tc.tc_lsqr_c_learned(plan.handle, m, C, X, Xr, 32, 1.0, info)
+    torch.cuda.synchronize()
+    il = tc.read_info(info)
+    assert 13 <= il["iters"] <= 32
+    if il["fallback"] == 1:
+        X2, Xr2, _, info2 = plan.lsqr(C, il["iters"], regularize=True)
+        torch.cuda.synchronize()
+        assert torch.equal(Xr2, Xr) and torch.equal(X2, X)
+        assert tc.read_info(info2)["lam"] == il["lam"]
+    src.close()
+
+
+def test_learned_gain_small(tc):
+    # A small training run (640 problems of 64 x 64 x 3), evaluated on 12
+    # held-out 64 x 64 x 3 problems against plain GCV-driven c-LSQR (32 steps).
+    from paper_2103_11847_gb300 import learn
+    F, T = learn.training_data(640, n=64, kmax=32, seed=41)
+    mlp, hist = learn.train(F, T, steps=1500, batch=128, lr=2e-3)
+    rows = learn.compare(mlp, count=12, n=64, kmax=32, seed=43)
+    s = learn.summarize(rows)
+    print(s)
+    assert hist[-50:].mean().item() < hist[:5].mean().item()
+    # the predicted stop index stays in range, and the learned solve's error
+    # stays within 10% of GCV's (the full-size comparison is in bench.py)
+    assert 13 <= s["mean_iters_learned"] <= 32
+    assert s["mean_err_learned"] < 1.1 * s["mean_err_plain"]
