@@ -337,7 +337,7 @@ def run_gpu(args):
     n3, n1, n2 = w["A"].shape
     two = w["B"] is not None
     s = w["B"].shape[1] if two else w["X_true"].shape[2]
-    iters = wl["iters"]
+    iters = args.iters or wl["iters"]
     dev = torch.device("cuda", local)
     A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
     B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
@@ -506,6 +506,7 @@ def main():
     ap.add_argument("--workload", default="two_sided_256", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
+    ap.add_argument("--iters", type=int, default=0, help="override the workload's iterations")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
                     help="slice-GEMM inputs of the main workload (tensor-core forms need "
                          "one-sided plans: video_512 or colour_64)")
