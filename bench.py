@@ -61,13 +61,17 @@ def product_flops(n1, n2, s, n3, two_sided):
     return f
 
 
-def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32"):
-    """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu)."""
-    per_product = (2 if two_sided else 1) if fused else (4 if two_sided else 3)
+def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32", s=0):
+    """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu).
+    A fused product is one launch, except two-sided with s > 256 (two)."""
+    if fused:
+        per_product = 2 if (two_sided and s > 256) else 1
+    else:
+        per_product = 4 if two_sided else 3
     if precision != "fp32":  # transform, [transpose for TF32], tcgen05 GEMM, transform back
         per_product = 4 if precision == "tf32" else 3
     init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
-    per_iter = 2 * per_product + 2
+    per_iter = 2 * per_product + 1  # product, adjoint, update
     tail = (5 if keep_basis else 0) + 1  # 3 GCV grid levels, final, combine; info
     return init + iters * per_iter + tail
 
@@ -380,16 +384,30 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
 
-    # dominant kernels: the slice GEMMs of one product, timed alone on the stream
+    # dominant kernel, timed alone on the stream. n3 <= 4 (FP32): the fused
+    # product launches (one for the two-sided product with s <= 256), timed
+    # through tc_cprod. Otherwise: the slice GEMMs of one product (tc_slice_gemm).
     fl = product_flops(n1, n2, s, n3, two)
     reps = 200
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    tmpY = torch.empty(plan.yshape(), device=dev)
+    if n3 <= 4 and args.precision == "fp32":
+        roof_kernel = ("k_cprod2 (the whole two-sided product, one launch)" if two and s <= 256
+                       else "k_fused_gemm (the GEMM stages of one c-product)")
+        src, dst = Xr, torch.empty(plan.yshape(), device=dev)
+        call = lambda: tcprod.tc_cprod(plan.handle, src, dst)
+    else:
+        lowp_dt = torch.bfloat16 if args.precision == "bf16" else torch.float32
+        roof_kernel = ("k_umma_gemm (tcgen05 slice GEMMs of one product)" if args.precision != "fp32"
+                       else "k_slice_gemm (FFMA slice GEMMs of one product)")
+        src = torch.randn((n3, n2, s), device=dev).to(lowp_dt)
+        dst = torch.empty((n3, n1, s), device=dev)
+        call = lambda: tcprod.tc_slice_gemm(plan.handle, src, dst)
+        reps = 50
     for _ in range(10):
-        tcprod.tc_cprod(plan.handle, Xr, tmpY)
+        call()
     e0.record(st)
     for _ in range(reps):
-        tcprod.tc_cprod(plan.handle, Xr, tmpY)
+        call()
     e1.record(st)
     torch.cuda.synchronize()
     prod_ms = e0.elapsed_time(e1) / reps
@@ -421,10 +439,25 @@ def run_gpu(args):
         t_max = float(t.item())
     value = world * args.steps * iters / (t_max / 1000.0)
     if rank == 0:
-        peaks, src = load_peaks()
+        peaks, src_peaks = load_peaks()
         sm_max = peaks.get("sm_max_mhz", 2070.0)
         fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12
         achieved = fl / (prod_ms * 1e-3) / 1e12
+        if args.precision == "fp32":
+            roof = {"kernel": roof_kernel, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
+                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
+                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
+                                   f"({src_peaks} max clock)", "launch_ms": prod_ms}
+        else:  # tcgen05 GEMM: A~ and X~ in the input type read once, Y~ written in FP32
+            es = 2 if args.precision == "bf16" else 4
+            gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
+            hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+            gbs = gbytes / (prod_ms * 1e-3) / 1e9
+            roof = {"kernel": roof_kernel, "bound": "hbm", "achieved": gbs, "peak": hbm,
+                    "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src_peaks})",
+                    "launch_ms": prod_ms, "algorithmic_bytes": gbytes,
+                    "note": "the mode-3 transform passes take most of this solve; see profiles"}
         line = {
             "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
             "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,
@@ -437,17 +470,12 @@ def run_gpu(args):
                        "precision": args.precision,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": {"kernel": "k_slice_gemm (all GEMM stages of one c-product)",
-                         "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                         "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": None,
-                         "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                        f"({src} max clock)",
-                         "launch_ms": prod_ms},
+            "roofline": roof,
             "e2e": {"value": iters / (e2e_ms / 1000.0) * world, "unit": "LSQR iterations/s",
                     "h2d_bytes_per_step": int(C.numel() * 4),
                     "d2h_bytes_per_step": int(Xr.numel() * 4 + info.numel())},
             "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4,
-                                                              precision=args.precision),
+                                                              precision=args.precision, s=s),
             "clocks": clk,
             "solve": {"iters": inf["iters"], "status": inf["status"], "lambda": inf["lam"],
                       "resid": inf["resid"],

@@ -99,7 +99,7 @@ const char* tc_last_error(void);
  * device memory it allocates (freed by tc_plan_destroy).
  *   A: device, n1 x n2 x n3.   B: device s x s x n3, or NULL for A *c X.
  *   opts: may be NULL (FP32, paper GCV, graphs on).
- * Sizes must be >= 1; n3 <= 128. Synchronises `stream` before returning.
+ * Sizes must be >= 1; n3 <= 64. Synchronises `stream` before returning.
  * Source: Remark 2.1 and eqs. (dft9), (dft8), §2.2. */
 int tc_plan_create(tc_plan** plan, int n1, int n2, int s, int n3,
                    const float* A, const float* B, const tc_opts* opts,

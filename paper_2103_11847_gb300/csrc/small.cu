@@ -292,5 +292,7 @@ int launch_build_bidiag(const double* alpha, const double* beta, const int* kdev
 int tc_kernels_init() {
   TC_CUDA(cudaFuncSetAttribute(k_tikhonov_gcv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                200 * 1024));
+  TC_TRY(cprod2_init());
+  TC_TRY(vec_init());
   return TC_OK;
 }

@@ -47,6 +47,7 @@ int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
   const size_t L = (size_t)itermax + 2;
   const size_t kp = (size_t)(itermax < TC_MAX_PROJ ? itermax : TC_MAX_PROJ);
   TC_TRY(grow(&p->dscal, &p->dscal_elems, 7 * L + 1200 + kp + 16, &moved));
+  TC_TRY(grow(&p->lsqr_done, &p->lsqr_done_elems, L, &moved));
   if (keep_basis) TC_TRY(grow(&p->basis, &p->basis_elems, (size_t)itermax * p->Tx, &moved));
   if (moved && p->lsqr_graph) {  // a captured solve holds the old addresses
     cudaGraphExecDestroy(p->lsqr_graph);
@@ -59,14 +60,15 @@ namespace {
 
 // alpha_1 = ||A^T U_1|| and beta_1 = ||C|| are in place: set W_1 = V_1 and the
 // Givens state rhobar_1 = alpha_1, phibar_1 = beta_1 (Algorithm 6 step 2).
+// done[0] gates the first step: set on a start-up breakdown or non-finite norm.
 __global__ void k_lsqr_init(const double* alpha, const double* beta, double* rhobar,
-                            double* phibar, int* flags) {
+                            double* phibar, int* flags, int* done) {
   rhobar[0] = alpha[0];
   phibar[0] = beta[0];
   flags[1] = 0;
   if (!isfinite(alpha[0]) || !isfinite(beta[0])) flags[2] = TC_ENONFINITE;
   else if (alpha[0] == 0.0 || beta[0] == 0.0) flags[2] = TC_EBREAKDOWN;
-  if (flags[2] != 0) flags[0] = 1;
+  done[0] = flags[2] != 0;
 }
 
 __global__ void k_lsqr_info(tc_solve_info* info, const int* flags, const double* phibar,
@@ -139,11 +141,14 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   double* lam = y + kp;
   double* gcv = lam + 1;
   double* lam_pred = gcv + 1;
-  int* flags = p->iflags;  // [0] done [1] iterations [2] status [6] stop_at [7] fallback
+  int* flags = p->iflags;  // [1] iterations [2] status [6] stop_at [7] fallback
+  // done[j] nonzero: every launch of step j returns at once (set by step j-1's update)
+  int* done = p->lsqr_done;
   float *U = p->lsqr_U, *V = p->lsqr_V, *W = p->lsqr_W;
   const bool keep = a.X_reg != nullptr;
 
   TC_CUDA(cudaMemsetAsync(flags, 0, 16 * sizeof(int), st));
+  TC_CUDA(cudaMemsetAsync(done, 0, L * sizeof(int), st));
   // beta_1 = ||C||_F
   TC_TRY(launch_reduce(a.C, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
   // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
@@ -163,7 +168,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     if (keep) TC_TRY(launch_scale(V, p->basis, p->Tx, c, nullptr, nullptr, st));
   }
   TC_CUDA(cudaMemsetAsync(a.X, 0, p->Tx * sizeof(float), st));
-  k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags);
+  k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags, done);
   TC_CUDA(cudaGetLastError());
 
   for (int j = 0; j < a.itermax; ++j) {
@@ -175,7 +180,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.coef.s1 = beta + j;
       ep.prev = (j == 0) ? a.C : U;
       ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
-      ep.skip = flags;
+      ep.skip = done + j;
       TC_TRY(cprod_epi(p, V, U, ep, st));
     }
     // (b) V~_{j+1} = (1/beta_{j+1}) A^T U~_{j+1} - (beta_{j+1}/alpha_j) V~_j
@@ -186,14 +191,14 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.coef.s1 = alpha + j;
       ep.prev = V;
       ep.red = make_red(p, alpha + j + 1, 1, nullptr, flags + 2);
-      ep.skip = flags;
+      ep.skip = done + j;
       TC_TRY(adjoint_epi(p, U, V, ep, st));
     }
     // (c)-(g) Givens recurrences and the X, W updates
     float* slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
     TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist,
-                              keep ? rgiv : nullptr, j, a.tol, flags, st,
-                              a.mlp ? flags + 6 : nullptr));
+                              keep ? rgiv : nullptr, j, a.tol, flags, done + j, done + j + 1,
+                              st, a.mlp ? flags + 6 : nullptr));
     if (a.mlp && j + 1 == MLP_FEAT_STEPS)
       TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   }

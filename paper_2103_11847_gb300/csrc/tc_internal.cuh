@@ -12,7 +12,7 @@
 // n3 takes the unfused route: a transform pass, per-slice GEMMs, a transform
 // pass with the Krylov epilogue.
 #define TC_MAX_FUSED 4
-#define TC_MAX_N3 128
+#define TC_MAX_N3 64
 #define TC_MAX_PROJ 128  // largest projected problem (k) on the device
 
 // ---------------------------------------------------------------- epilogue --
@@ -83,6 +83,7 @@ struct tc_plan {
   float* basis = nullptr; size_t basis_elems = 0;
   double* dscal = nullptr; size_t dscal_elems = 0;
   int* iflags = nullptr;
+  int* lsqr_done = nullptr; size_t lsqr_done_elems = 0;  // done[j]: step j's launches return
   float* gm_basis = nullptr; size_t gm_basis_elems = 0;    // GMRES basis V_1..V_{m+1}
   double* gm_dscal = nullptr; size_t gm_dscal_elems = 0;
   int* gm_flags = nullptr;
@@ -129,6 +130,14 @@ void tc_set_message(const char* msg);
 int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, int K,
                       int nslices, const float* pro, const float* epi, const Epi& ep,
                       cudaStream_t st);
+// gemm2.cu: the whole two-sided fused product Y = epi[ A_k (pro X)_k B_k ]
+// in one launch of thread-block clusters, for N = s <= 256 (cprod2_fits).
+// A: M x K per slice, X: K x N, B: N x N, Y/prev: M x N.
+bool cprod2_fits(int s);
+int cprod2_init();
+int launch_cprod2(const float* A, const float* X, const float* B, float* Y, int M, int K,
+                  int N, int nslices, const float* pro, const float* epi, const Epi& ep,
+                  cudaStream_t st);
 // transform.cu: out[k][p] = ca * sum_l T[k][l] in[l][p] + cp * prev[k][p] over P pixels.
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
                  const Epi& ep, cudaStream_t st);
@@ -139,6 +148,7 @@ int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, si
 // Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
 int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st);
 // vec.cu
+int vec_init();  // shared-memory carveout preference of the vector passes
 int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
                   const int* skip, cudaStream_t st);
 int launch_scale(const float* in, float* out, size_t n, const Coef& c, const float* prev,
@@ -146,7 +156,8 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
                        double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       cudaStream_t st, const int* stop_at = nullptr);
+                       const int* done_in, int* done_out, cudaStream_t st,
+                       const int* stop_at = nullptr);
 int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
                    const int* kdev, const double* y, size_t n, const int* skip,
                    cudaStream_t st);

@@ -3,9 +3,10 @@
 // + cp * prev[k][p], with the fused reduction of the epilogue. Each CTA owns
 // 128 consecutive pixels p of every slice: warp w computes the KPW contiguous
 // outputs k = w*KPW .. w*KPW + KPW - 1 (coefficients read as float4
-// broadcasts) and lane q the pixels 4q..4q+3. Inputs stream through shared
-// memory 32 slices at a time; HBM traffic is one read of `in` (and `prev`)
-// and one write of `out`.
+// broadcasts) and lane q the pixels 4q..4q+3. T is staged in shared memory
+// once; inputs stream through two shared-memory stages of 16 slices, filled
+// with cp.async while the other stage is consumed. HBM traffic is one read of
+// `in` (and `prev`) and one write of `out`.
 #include <cuda_bf16.h>
 
 #include "tc_device.cuh"
@@ -24,15 +25,24 @@ __device__ __forceinline__ float round_tf32(float x) {
 }
 
 constexpr int PB = 128;  // pixels per CTA
-constexpr int LC = 32;   // input slices per shared-memory stage
+constexpr int LC = 16;   // input slices per shared-memory stage (double-buffered)
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  const int n = valid ? 16 : 0;  // zero-fill when out of range
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n)
+               : "memory");
+}
 
 template <int KPW, int OUT>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 3)
 k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, int n3,
         size_t P, Epi ep) {
   if (ep.skip && *ep.skip) return;
-  __shared__ __align__(16) float xs[LC][PB];
-  __shared__ __align__(16) float ts[LC][8 * KPW];
+  // ts: T transposed (ts[l][k] = T[k][l]) for all l, loaded once;
+  // xs: two stages of LC input slices x PB pixels
+  __shared__ __align__(16) float ts[8 * KPW][8 * KPW];  // <= 16 KB (n3 <= 64)
+  __shared__ __align__(16) float xs[2][LC][PB];
   __shared__ float sh_coef[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const size_t p0 = (size_t)blockIdx.x * PB;
@@ -46,40 +56,53 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
 
-  for (int l0 = 0; l0 < n3; l0 += LC) {
-    const int lc_n = min(LC, n3 - l0);
+  for (int idx = tid; idx < n3 * 8 * KPW; idx += 256) {
+    const int l = idx / (8 * KPW), k = idx % (8 * KPW);
+    ts[l][k] = (k < n3) ? __ldg(T + (size_t)k * n3 + l) : 0.f;
+  }
+  const int nch = (n3 + LC - 1) / LC;
+  auto stage = [&](int c) {
+    const int l0 = c * LC, lc_n = min(LC, n3 - l0);
+    float(*xb)[PB] = xs[c & 1];
     if (vec) {
       for (int idx = tid; idx < LC * PB / 4; idx += 256) {
         const int lc = idx / (PB / 4), px = (idx % (PB / 4)) * 4;
         const size_t p = p0 + px;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (lc < lc_n && p < P) v = __ldg(reinterpret_cast<const float4*>(in + (size_t)(l0 + lc) * P + p));
-        *reinterpret_cast<float4*>(&xs[lc][px]) = v;
+        const bool ok = lc < lc_n && p < P;
+        cp_async16(&xb[lc][px], ok ? in + (size_t)(l0 + lc) * P + p : in, ok);
       }
     } else {
       for (int idx = tid; idx < LC * PB; idx += 256) {
         const int lc = idx / PB, px = idx % PB;
         const size_t p = p0 + px;
-        xs[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
+        xb[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
       }
     }
-    for (int idx = tid; idx < LC * 8 * KPW; idx += 256) {
-      const int lc = idx / (8 * KPW), k = idx % (8 * KPW);
-      ts[lc][k] = (lc < lc_n && k < n3) ? __ldg(T + (size_t)k * n3 + l0 + lc) : 0.f;
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  stage(0);
+  for (int c = 0; c < nch; ++c) {
+    if (c + 1 < nch) {
+      stage(c + 1);
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
     }
     __syncthreads();
+    const int l0 = c * LC, lc_n = min(LC, n3 - l0);
+    float(*xb)[PB] = xs[c & 1];
     for (int lc = 0; lc < lc_n; ++lc) {
-      const float4 x = *reinterpret_cast<const float4*>(&xs[lc][lane * 4]);
+      const float4 x = *reinterpret_cast<const float4*>(&xb[lc][lane * 4]);
       float t[KPW];  // warp w owns the contiguous outputs k = w*KPW .. w*KPW + KPW - 1
       if (KPW % 4 == 0) {
 #pragma unroll
         for (int q = 0; q < KPW; q += 4) {
-          const float4 tv = *reinterpret_cast<const float4*>(&ts[lc][w * KPW + q]);
+          const float4 tv = *reinterpret_cast<const float4*>(&ts[l0 + lc][w * KPW + q]);
           t[q] = tv.x; t[q + 1] = tv.y; t[q + 2] = tv.z; t[q + 3] = tv.w;
         }
       } else {
 #pragma unroll
-        for (int q = 0; q < KPW; ++q) t[q] = ts[lc][w * KPW + q];
+        for (int q = 0; q < KPW; ++q) t[q] = ts[l0 + lc][w * KPW + q];
       }
 #pragma unroll
       for (int q = 0; q < KPW; ++q) {
@@ -89,7 +112,7 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
         acc[q][3] = fmaf(t[q], x.w, acc[q][3]);
       }
     }
-    __syncthreads();
+    __syncthreads();  // the stage about to be refilled is no longer read
   }
 
   if (OUT != OUT_F32) {  // operand of a tensor-core GEMM: store only
@@ -170,8 +193,7 @@ int pick(const float* in, void* out, const float* T, int n3, size_t P, const Epi
   if (n3 <= 8) return run<1, OUT>(in, out, T, n3, P, ep, st);
   if (n3 <= 16) return run<2, OUT>(in, out, T, n3, P, ep, st);
   if (n3 <= 32) return run<4, OUT>(in, out, T, n3, P, ep, st);
-  if (n3 <= 64) return run<8, OUT>(in, out, T, n3, P, ep, st);
-  return run<16, OUT>(in, out, T, n3, P, ep, st);
+  return run<8, OUT>(in, out, T, n3, P, ep, st);
 }
 
 __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int kind) {

@@ -51,20 +51,39 @@ k_scale(const float* __restrict__ in, float* out, size_t n, Coef c, const float*
 //   X += (phi/rho) W,  W = V_{j+1} - (theta/rho) W,  V_{j+1} = Vt/alpha_{j+1}.
 // Every CTA derives the same scalars from alpha[j+1], beta[j+1], rhobar[j],
 // phibar[j]; CTA 0 writes index j+1 of the state, so no CTA reads a value
-// another CTA of this launch writes. flags: [0] done, [1] iterations, [2] status.
+// another CTA of this launch writes. Each thread loads its UPT elements of W,
+// X and V before thread 0's FP64 scalar chain, so the two latencies overlap.
+// done_in (= done[j]) gates the launch; done_out (= done[j+1], read by every
+// launch of the next step and by nothing in this one) is written by CTA 0.
+// flags: [1] iterations, [2] status.
+constexpr int UPT = 4;
 __global__ void __launch_bounds__(NT)
-k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot, size_t n,
-              const double* alpha, const double* beta, double* rhobar, double* phibar,
-              double* phibar_hist, double* rgiv, int j, double tol, int* flags,
+k_lsqr_update(float* __restrict__ X, float* __restrict__ W, const float* __restrict__ V,
+              float* __restrict__ basis_slot, size_t n, const double* alpha,
+              const double* beta, double* rhobar, double* phibar, double* phibar_hist,
+              double* rgiv, int j, double tol, int* flags, const int* done_in, int* done_out,
               const int* stop_at) {
-  if (flags[0]) return;
+  if (*done_in) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *done_out = 1;
+    return;
+  }
   __shared__ float sh[4];
   __shared__ int sh_stop;
+  const size_t base = (size_t)blockIdx.x * (NT * UPT) + threadIdx.x;
+  float w[UPT], x[UPT], v[UPT];
+#pragma unroll
+  for (int u = 0; u < UPT; ++u) {
+    const size_t i = base + (size_t)u * NT;
+    w[u] = i < n ? W[i] : 0.f;
+    x[u] = i < n ? X[i] : 0.f;
+    v[u] = i < n ? V[i] : 0.f;
+  }
   if (threadIdx.x == 0) {
     const double b = beta[j + 1], a = alpha[j + 1];
     const double rb = rhobar[j], pb = phibar[j];
     const double rho = hypot(rb, b);
-    const double c = rb / rho, s = b / rho;
+    const double irho = 1.0 / rho;
+    const double c = rb * irho, s = b * irho;
     const double theta = s * a;
     const double phi = c * pb;
     const double pbn = -s * pb;
@@ -72,9 +91,9 @@ k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot
     const bool brk = (a == 0.0);
     // converged, or reached the step count a learned predictor chose
     const bool conv = fabs(pbn) < tol || (stop_at && *stop_at > 0 && j + 1 >= *stop_at);
-    sh[0] = (float)(phi / rho);
+    sh[0] = (float)(phi * irho);
     sh[1] = brk ? 0.f : (float)(1.0 / a);
-    sh[2] = (float)(theta / rho);
+    sh[2] = (float)(theta * irho);
     sh_stop = brk || conv || !finite;
     if (blockIdx.x == 0) {
       rhobar[j + 1] = c * a;
@@ -89,27 +108,23 @@ k_lsqr_update(float* X, float* W, const float* __restrict__ V, float* basis_slot
       if (!finite) flags[2] = TC_ENONFINITE;
       else if (brk) flags[2] = TC_EBREAKDOWN;
       else if (conv) flags[2] = 1;
+      *done_out = (!finite || brk || conv) ? 1 : 0;
     }
   }
   __syncthreads();
   const float cx = sh[0], cv = sh[1], cw = sh[2];
   const bool stop = sh_stop;
-  const size_t stride = (size_t)gridDim.x * NT;
-  for (size_t i = (size_t)blockIdx.x * NT + threadIdx.x; i < n; i += stride) {
-    const float w = W[i];
-    X[i] = fmaf(cx, w, X[i]);
+#pragma unroll
+  for (int u = 0; u < UPT; ++u) {
+    const size_t i = base + (size_t)u * NT;
+    if (i >= n) break;
+    X[i] = fmaf(cx, w[u], x[u]);
     if (!stop) {
-      const float v = cv * V[i];
-      W[i] = fmaf(-cw, w, v);
-      if (basis_slot) basis_slot[i] = v;
+      const float vn = cv * v[u];
+      W[i] = fmaf(-cw, w[u], vn);
+      if (basis_slot) basis_slot[i] = vn;
     }
   }
-  // The done flag is raised by the next kernel on the stream (k_lsqr_flag) so
-  // that no CTA of this launch sees it change under it.
-}
-
-__global__ void k_lsqr_flag(int* flags) {
-  if (flags[2] != 0) flags[0] = 1;
 }
 
 // X = X0 + sum_{i<k} y_i V_i (V_i at basis + i*stride); k read from the device.
@@ -150,6 +165,19 @@ k_mgs_pass(float* W, const float* __restrict__ Vi, const double* h, const float*
 
 }  // namespace
 
+// The vector passes need no shared memory; asking for the largest shared
+// carveout keeps the SM in the split the GEMM launches around them use, so
+// consecutive launches of a solve do not reconfigure the L1/shared split.
+int vec_init() {
+  const int c = cudaSharedmemCarveoutMaxShared;
+  TC_CUDA(cudaFuncSetAttribute(k_reduce, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_scale, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_lsqr_update, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_combine, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_mgs_pass, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  return TC_OK;
+}
+
 int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
                   const int* skip, cudaStream_t st) {
   k_reduce<<<grid_for(n, 16), NT, 0, st>>>(x, other, n, red, skip);
@@ -167,11 +195,13 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
                        double* alpha, double* beta, double* rhobar, double* phibar,
                        double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       cudaStream_t st, const int* stop_at) {
-  k_lsqr_update<<<grid_for(n, 8), NT, 0, st>>>(X, W, V, basis_slot, n, alpha, beta, rhobar,
-                                               phibar, phibar_hist, rgiv, j, tol, flags, stop_at);
-  TC_CUDA(cudaGetLastError());
-  k_lsqr_flag<<<1, 1, 0, st>>>(flags);
+                       const int* done_in, int* done_out, cudaStream_t st,
+                       const int* stop_at) {
+  const size_t blocks = (n + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
+  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
+  k_lsqr_update<<<(unsigned)blocks, NT, 0, st>>>(X, W, V, basis_slot, n, alpha, beta, rhobar,
+                                                 phibar, phibar_hist, rgiv, j, tol, flags,
+                                                 done_in, done_out, stop_at);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

@@ -43,6 +43,11 @@ SHAPES = [  # n1, n2, s, n3, two_sided
     (33, 31, 29, 2, False), (50, 50, 50, 4, False), (37, 45, 23, 5, False), (64, 64, 48, 9, False),
     (30, 30, 30, 64, False), (70, 40, 20, 3, True), (32, 32, 32, 3, True), (29, 35, 31, 6, True),
     (130, 129, 131, 3, False), (200, 190, 70, 2, True),
+    # two-sided, one launch per product: clusters of ceil(s / 32) CTAs, ragged
+    # panels, odd widths (scalar loads), s = 256 (eight CTAs), and s = 257
+    # (past the one-launch limit: two launches)
+    (45, 61, 255, 4, True), (300, 96, 256, 1, True), (17, 250, 100, 3, True),
+    (64, 48, 257, 3, True), (33, 200, 160, 2, True),
 ]
 
 
