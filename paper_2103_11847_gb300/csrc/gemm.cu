@@ -197,7 +197,7 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
         }
       }
     }
-    if (ep.red.out) reduce_finish((double)local, ep.red);
+    if (ep.red.out) reduce_finish(local, ep.red);
     return;
   }
   // partial tile to shared memory, then sum over the cluster's K ranges
@@ -243,7 +243,7 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
     }
   }
   cluster.sync();  // peers may still read this CTA's partial tile until here
-  if (ep.red.out) reduce_finish((double)local, ep.red);
+  if (ep.red.out) reduce_finish(local, ep.red);
 }
 
 // Per-slice GEMM without transforms: C_z = A_z B_z for slice z = blockIdx.z.

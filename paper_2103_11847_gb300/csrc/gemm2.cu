@@ -15,13 +15,22 @@
 // Clusters of four fit the GPU in one wave at one CTA per SM (a 256 x 256
 // image is 32 clusters); clusters of eight would not.
 //
-// Inside a CTA the eight warps split every 64-deep K chunk (8 rows of K
+// Operands stream through a ring of S shared-memory slots filled with
+// cp.async, S - 1 chunks ahead of the FMAs. The left operand of stage 1 is
+// read K-major from the slice transposes of A~ that the plan keeps, so it
+// lands in the layout the FMAs read. Each thread applies the prologue
+// transform in place to the X positions it copied itself (all slices of
+// them), so a chunk needs one barrier.
+//
+// Inside a CTA the eight warps split every 32-deep K chunk (4 rows of K
 // each) and each owns the whole 8 x 64 x n3 block: every lane holds all 8
 // rows and two adjacent columns of every slice. The left operand is then the
 // same for the whole warp (one broadcast shared-memory read per 4 values) and
 // the right operand is one 64-bit read per lane: 4 shared-memory wavefronts
-// per 16 FMAs. The eight partial blocks are summed through shared memory at
-// the end of each stage. Operands stream through two register-staged buffers.
+// per 16 FMAs. The partial blocks are summed through shared memory at the
+// end of each stage. (Sixteen warps, a 6-slot ring or 64-deep chunks
+// measured no faster: at 8 rows per panel the per-SM fill rate of the ring
+// and the shared-memory operand reads bound the loop, not latency.)
 #include <cooperative_groups.h>
 
 #include "tc_device.cuh"
@@ -32,11 +41,13 @@ namespace {
 
 constexpr int BM = 8;    // rows of a cluster's panel
 constexpr int BN = 64;   // columns per CTA
-constexpr int BK = 64;   // K chunk
+constexpr int BK = 32;   // K chunk
 constexpr int NW = 8;    // warps per CTA
 constexpr int NT = 32 * NW;
+constexpr int S = 4;     // ring slots
 constexpr int CS_MAX = 4;
-constexpr int KW = BK / NW;  // K rows of a chunk per warp
+constexpr int KW = BK / NW;     // K rows of a chunk per warp
+constexpr int NPOS = BK * BN / 4 / NT;  // float4 positions of a B chunk per thread (2)
 
 struct Mix {
   float pro[TC_MAX_FUSED * TC_MAX_FUSED];
@@ -45,29 +56,52 @@ struct Mix {
 
 template <int NS>
 struct Lay {
-  static constexpr int kA = 2 * NS * BK * BM;     // As[2][NS][BK][BM] (K-major A chunk)
-  static constexpr int kB = 2 * NS * BK * BN;     // Bs[2][NS][BK][BN]
+  static constexpr int kA = NS * BK * BM;         // left operand of a chunk [NS][BK][BM]
+  static constexpr int kB = NS * BK * BN;         // right operand of a chunk [NS][BK][BN]
+  static constexpr int kSlot = kA + kB;
+  static constexpr int kRing = S * kSlot;
   static constexpr int kRed = NW * NS * BM * BN;  // per-warp partial blocks
-  static constexpr int kStage = (kA + kB) > kRed ? (kA + kB) : kRed;
+  static constexpr int kStage = kRing > kRed ? kRing : kRed;
   // followed by Tt[NS][K2p][BM]: the panel of T, K-major, K2p = CS * BN
   // rounded up to whole chunks (the rounding rows are zero)
   __host__ __device__ static constexpr int k2p(int cs) { return (cs * BN + BK - 1) / BK * BK; }
   static constexpr size_t bytes(int cs) { return (size_t)(kStage + NS * k2p(cs) * BM) * 4; }
 };
 
-// 4 consecutive floats of row r at column c of a rows x cols row-major
-// matrix, zero outside it.
-__device__ __forceinline__ float4 ld4(const float* base, int rows, int cols, int r, int c,
-                                      bool vec) {
-  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (r >= rows) return v;
-  const float* p = base + (size_t)r * cols;
-  if (vec && c + 3 < cols) return __ldg(reinterpret_cast<const float4*>(p + c));
-  if (c < cols) v.x = __ldg(p + c);
-  if (c + 1 < cols) v.y = __ldg(p + c + 1);
-  if (c + 2 < cols) v.z = __ldg(p + c + 2);
-  if (c + 3 < cols) v.w = __ldg(p + c + 3);
-  return v;
+__device__ __forceinline__ void cp16(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src),
+               "r"(valid ? 4 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Four consecutive floats of row r, columns c..c+3, of a rows x cols
+// row-major matrix into shared memory; zero outside the matrix. VEC: whole
+// 16-byte groups (cols % 4 == 0, 16-byte aligned base).
+template <bool VEC>
+__device__ __forceinline__ void cp_row4(float* dst, const float* base, int rows, int cols, int r,
+                                        int c) {
+  if (VEC) {
+    const bool ok = r < rows && c < cols;
+    cp16(dst, ok ? base + (size_t)r * cols + c : base, ok);
+  } else {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const bool ok = r < rows && c + e < cols;
+      cp4(dst + e, ok ? base + (size_t)r * cols + c + e : base, ok);
+    }
+  }
 }
 
 // acc[k][r][j] += a[k][kk][r] * b[k][kk][2 lane + j] over this warp's KW rows
@@ -106,17 +140,19 @@ __device__ __forceinline__ void acc_to_red(float* red, const float (&acc)[NS][BM
           make_float2(acc[k][r][0], acc[k][r][1]);
 }
 
-template <int NS>
+// At: the left factor K-major (NS x K x M, the slice transposes), X: NS x K x
+// N, B: NS x N x N, Y / prev / other: NS x M x N.
+template <int NS, bool VEC>
 __global__ void __launch_bounds__(NT, 1)
-k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
+k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
          const float* __restrict__ B, float* Y, int M, int K, int N, Mix f, Epi ep) {
   if (ep.skip && *ep.skip) return;  // uniform over the grid: no CTA reaches a barrier alone
   extern __shared__ __align__(16) float smem[];
   __shared__ float sh_coef[2];
-  float* As = smem;
-  float* Bs = smem + Lay<NS>::kA;
-  float* red = smem;
+  float* ring = smem;
+  float* red = smem;  // after a stage's main loop
   float* Tt = smem + Lay<NS>::kStage;
+  constexpr int kA = Lay<NS>::kA, kSlot = Lay<NS>::kSlot;
 
   cg::cluster_group cluster = cg::this_cluster();
   const int CS = (int)cluster.num_blocks();
@@ -124,12 +160,7 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
   const int K2 = CS * BN, K2p = Lay<NS>::k2p(CS);
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int r0 = blockIdx.y * BM, c0 = q * BN;
-  const size_t sA = (size_t)M * K, sX = (size_t)K * N, sB = (size_t)N * N, sY = (size_t)M * N;
-  const bool vec = (K % 4 == 0) && (N % 4 == 0) &&
-                   (((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(X) |
-                      reinterpret_cast<uintptr_t>(B) | reinterpret_cast<uintptr_t>(Y)) & 15) == 0) &&
-                   (!ep.prev || (reinterpret_cast<uintptr_t>(ep.prev) & 15) == 0) &&
-                   (!ep.red.other || (reinterpret_cast<uintptr_t>(ep.red.other) & 15) == 0);
+  const size_t sA = (size_t)K * M, sX = (size_t)K * N, sB = (size_t)N * N, sY = (size_t)M * N;
   coef_compute(ep.coef, sh_coef);  // read after the barriers below
   // Every CTA of the cluster must be running before a peer stores into its
   // shared memory: arrive now, wait just before the first remote store.
@@ -141,16 +172,63 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
     Tt[((size_t)k * K2p + K2) * BM + r] = 0.f;
   }
 
-  // Loader roles. A chunk (8 rows x 64 k per slice, 128 float4): thread t
-  // loads slices t/128, t/128 + 2 at row t%8, k 4((t%128)/8)..+3. X / B~
-  // chunk (64 k x 64 columns per slice): four float4 per thread and slice,
-  // k (t + 256 i)/16, columns 4(t%16)..+3.
-  constexpr int NA = (NS + 1) / 2;
-  const int la_s = tid >> 7, la_r = tid & 7, la_k = ((tid & 127) >> 3) * 4;
-  const int lb_k = tid >> 4, lb_c = (tid & 15) * 4;  // i adds 16 to the k row
+  // Copy roles of a chunk. Left operand (NS x BK k x 8 rows, 2 BK NS groups
+  // of 4 floats): group t is slice t/(2 BK), k (t%(2 BK))/2, rows
+  // 4(t%2)..+3. Right operand (BK k x 64 columns): thread t owns positions
+  // p = t + NT i (i < NPOS), k p/16, columns 4(p%16)..+3, for every slice.
+  auto issue1 = [&](int c) {
+    const int k0 = c * BK;
+    float* slot = ring + (c % S) * kSlot;
+    for (int t = tid; t < NS * BK * 2; t += NT) {
+      const int k = t / (2 * BK), kk = (t % (2 * BK)) >> 1, h = t & 1;
+      cp_row4<VEC>(slot + (k * BK + kk) * BM + 4 * h, At + k * sA, K, M, k0 + kk, r0 + 4 * h);
+    }
+    float* b = slot + kA;
+#pragma unroll
+    for (int i = 0; i < NPOS; ++i) {
+      const int p = tid + NT * i, kk = p >> 4, cq = (p & 15) * 4;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        cp_row4<VEC>(b + (k * BK + kk) * BN + cq, X + k * sX, K, N, k0 + kk, c0 + cq);
+    }
+  };
+  // X~_k = sum_l pro[k][l] X_l on this thread's own positions of a landed chunk
+  auto transform1 = [&](int c) {
+    float* b = ring + (c % S) * kSlot + kA;
+#pragma unroll
+    for (int i = 0; i < NPOS; ++i) {
+      const int p = tid + NT * i, kk = p >> 4, cq = (p & 15) * 4;
+      float4 x[NS];
+#pragma unroll
+      for (int l = 0; l < NS; ++l) x[l] = *reinterpret_cast<const float4*>(b + (l * BK + kk) * BN + cq);
+#pragma unroll
+      for (int k = 0; k < NS; ++k) {
+        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < NS; ++l) {
+          const float m = f.pro[k * NS + l];
+          t.x = fmaf(m, x[l].x, t.x);
+          t.y = fmaf(m, x[l].y, t.y);
+          t.z = fmaf(m, x[l].z, t.z);
+          t.w = fmaf(m, x[l].w, t.w);
+        }
+        *reinterpret_cast<float4*>(b + (k * BK + kk) * BN + cq) = t;
+      }
+    }
+  };
+  auto issue2 = [&](int c) {
+    const int k0 = c * BK;
+    float* b = ring + (c % S) * kSlot + kA;
+#pragma unroll
+    for (int i = 0; i < NPOS; ++i) {
+      const int p = tid + NT * i, kk = p >> 4, cq = (p & 15) * 4;
+#pragma unroll
+      for (int k = 0; k < NS; ++k)
+        cp_row4<VEC>(b + (k * BK + kk) * BN + cq, B + k * sB, N, N, k0 + kk, c0 + cq);
+    }
+  };
 
   float acc[NS][BM][2];
-  float4 ra[NA], rb[4][NS];
   auto zero_acc = [&]() {
 #pragma unroll
     for (int k = 0; k < NS; ++k)
@@ -159,61 +237,23 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
   };
 
   // ------------------------------------------------ stage 1: T = A~ (pro X)
-  auto fetch1 = [&](int k0) {
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const int k = la_s + 2 * j;
-      ra[j] = (k < NS && k0 + la_k < K) ? ld4(A + k * sA, M, K, r0 + la_r, k0 + la_k, vec)
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-#pragma unroll
-    for (int k = 0; k < NS; ++k)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        rb[i][k] = ld4(X + k * sX, K, N, k0 + lb_k + 16 * i, c0 + lb_c, vec);
-  };
-  auto store1 = [&](int buf) {
-    float* a = As + buf * NS * BK * BM;
-    float* b = Bs + buf * NS * BK * BN;
-#pragma unroll
-    for (int j = 0; j < NA; ++j) {
-      const int k = la_s + 2 * j;
-      if (k < NS) {
-        a[(k * BK + la_k + 0) * BM + la_r] = ra[j].x;
-        a[(k * BK + la_k + 1) * BM + la_r] = ra[j].y;
-        a[(k * BK + la_k + 2) * BM + la_r] = ra[j].z;
-        a[(k * BK + la_k + 3) * BM + la_r] = ra[j].w;
-      }
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < NS; ++k) {
-        float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int l = 0; l < NS; ++l) {
-          const float m = f.pro[k * NS + l];
-          t.x = fmaf(m, rb[i][l].x, t.x);
-          t.y = fmaf(m, rb[i][l].y, t.y);
-          t.z = fmaf(m, rb[i][l].z, t.z);
-          t.w = fmaf(m, rb[i][l].w, t.w);
-        }
-        *reinterpret_cast<float4*>(b + (k * BK + lb_k + 16 * i) * BN + lb_c) = t;
-      }
-  };
-
-  zero_acc();
   const int nk1 = (K + BK - 1) / BK;
-  fetch1(0);
-  for (int c = 0; c < nk1; ++c) {
-    const int buf = c & 1;
-    store1(buf);
-    __syncthreads();
-    if (c + 1 < nk1) fetch1((c + 1) * BK);
-    mma_chunk<NS>(acc, As + buf * NS * BK * BM, BK * BM, Bs + buf * NS * BK * BN, BK * BN, w,
-                  lane);
+  for (int s = 0; s < S - 1; ++s) {
+    if (s < nk1) issue1(s);
+    cp_commit();
   }
-  __syncthreads();  // every warp is done with the stage buffers
+  zero_acc();
+  for (int c = 0; c < nk1; ++c) {
+    cp_wait<S - 2>();  // this thread's copies of chunk c have landed
+    transform1(c);
+    __syncthreads();   // chunk c complete; every warp is done with chunk c - 1
+    if (c + S - 1 < nk1) issue1(c + S - 1);
+    cp_commit();
+    const float* slot = ring + (c % S) * kSlot;
+    mma_chunk<NS>(acc, slot, BK * BM, slot + kA, BK * BN, w, lane);
+  }
+  cp_wait<0>();
+  __syncthreads();  // every warp is done with the ring
   acc_to_red<NS>(red, acc, w, lane);
   __syncthreads();
 
@@ -237,30 +277,25 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
       *reinterpret_cast<float4*>(Tp + ((size_t)k * K2p + c0 + col) * BM + rr) = v;
     }
   }
+  __syncthreads();  // red is no longer read: the ring may be refilled
+
   // ---------------------------------------------------- stage 2: Z = T B~
-  auto fetch2 = [&](int k0) {
-#pragma unroll
-    for (int k = 0; k < NS; ++k)
-#pragma unroll
-      for (int i = 0; i < 4; ++i)
-        rb[i][k] = ld4(B + k * sB, N, N, k0 + lb_k + 16 * i, c0 + lb_c, vec);
-  };
-  fetch2(0);       // in flight across the cluster barrier
+  const int nk2 = K2p / BK;
+  for (int s = 0; s < S - 1; ++s) {  // in flight across the cluster barrier
+    if (s < nk2) issue2(s);
+    cp_commit();
+  }
   cluster.sync();  // the whole panel of T is in this CTA's shared memory
   zero_acc();
-  const int nk2 = K2p / BK;
   for (int c = 0; c < nk2; ++c) {
-    const int buf = c & 1;
-    float* b = Bs + buf * NS * BK * BN;
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int k = 0; k < NS; ++k)
-        *reinterpret_cast<float4*>(b + (k * BK + lb_k + 16 * i) * BN + lb_c) = rb[i][k];
+    cp_wait<S - 2>();
     __syncthreads();
-    if (c + 1 < nk2) fetch2((c + 1) * BK);
-    mma_chunk<NS>(acc, Tt + c * BK * BM, K2p * BM, b, BK * BN, w, lane);
+    if (c + S - 1 < nk2) issue2(c + S - 1);
+    cp_commit();
+    const float* slot = ring + (c % S) * kSlot;
+    mma_chunk<NS>(acc, Tt + c * BK * BM, K2p * BM, slot + kA, BK * BN, w, lane);
   }
+  cp_wait<0>();
   __syncthreads();
   acc_to_red<NS>(red, acc, w, lane);
   __syncthreads();
@@ -295,7 +330,7 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
         y[3] = fmaf(m, z[k].w, y[3]);
       }
       const size_t o = (size_t)l * sY + (size_t)gr * N + gc;
-      if (vec && gc + 3 < N) {
+      if (VEC) {  // gc + 3 < N: N is a multiple of 4
         float4 out = make_float4(ca * y[0], ca * y[1], ca * y[2], ca * y[3]);
         if (ep.prev) {
           const float4 pv = *reinterpret_cast<const float4*>(ep.prev + o);
@@ -320,11 +355,11 @@ k_cprod2(const float* __restrict__ A, const float* __restrict__ X,
       }
     }
   }
-  if (ep.red.out) reduce_finish((double)local, ep.red);
+  if (ep.red.out) reduce_finish(local, ep.red);
 }
 
-template <int NS>
-int run2(const float* A, const float* X, const float* B, float* Y, int M, int K, int N,
+template <int NS, bool VEC>
+int run2(const float* At, const float* X, const float* B, float* Y, int M, int K, int N,
          const Mix& f, const Epi& ep, cudaStream_t st) {
   const int CS = (N + BN - 1) / BN;
   cudaLaunchConfig_t cfg = {};
@@ -339,18 +374,30 @@ int run2(const float* A, const float* X, const float* B, float* Y, int M, int K,
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  TC_CUDA(cudaLaunchKernelEx(&cfg, k_cprod2<NS>, A, X, B, Y, M, K, N, f, ep));
+  TC_CUDA(cudaLaunchKernelEx(&cfg, k_cprod2<NS, VEC>, At, X, B, Y, M, K, N, f, ep));
   return TC_OK;
 }
 
 template <int NS>
+int run2v(bool vec, const float* At, const float* X, const float* B, float* Y, int M, int K,
+          int N, const Mix& f, const Epi& ep, cudaStream_t st) {
+  return vec ? run2<NS, true>(At, X, B, Y, M, K, N, f, ep, st)
+             : run2<NS, false>(At, X, B, Y, M, K, N, f, ep, st);
+}
+
+template <int NS>
 int init2() {
-  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const int c = cudaSharedmemCarveoutMaxShared;
+  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)Lay<NS>::bytes(CS_MAX)));
-  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                               cudaSharedmemCarveoutMaxShared));
+  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)Lay<NS>::bytes(CS_MAX)));
+  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_cprod2<NS, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   return TC_OK;
 }
+
+bool al16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
 }  // namespace
 
@@ -364,7 +411,7 @@ int cprod2_init() {
   return TC_OK;
 }
 
-int launch_cprod2(const float* A, const float* X, const float* B, float* Y, int M, int K,
+int launch_cprod2(const float* At, const float* X, const float* B, float* Y, int M, int K,
                   int N, int nslices, const float* pro, const float* epi, const Epi& ep,
                   cudaStream_t st) {
   TC_CHECK(nslices >= 1 && nslices <= TC_MAX_FUSED && cprod2_fits(N) && M >= 1 && K >= 1);
@@ -373,10 +420,12 @@ int launch_cprod2(const float* A, const float* X, const float* B, float* Y, int 
     f.pro[i] = pro[i];
     f.epi[i] = epi[i];
   }
+  const bool vec = M % 4 == 0 && N % 4 == 0 && al16(At) && al16(X) && al16(B) && al16(Y) &&
+                   (!ep.prev || al16(ep.prev)) && (!ep.red.other || al16(ep.red.other));
   switch (nslices) {
-    case 1: return run2<1>(A, X, B, Y, M, K, N, f, ep, st);
-    case 2: return run2<2>(A, X, B, Y, M, K, N, f, ep, st);
-    case 3: return run2<3>(A, X, B, Y, M, K, N, f, ep, st);
-    default: return run2<4>(A, X, B, Y, M, K, N, f, ep, st);
+    case 1: return run2v<1>(vec, At, X, B, Y, M, K, N, f, ep, st);
+    case 2: return run2v<2>(vec, At, X, B, Y, M, K, N, f, ep, st);
+    case 3: return run2v<3>(vec, At, X, B, Y, M, K, N, f, ep, st);
+    default: return run2v<4>(vec, At, X, B, Y, M, K, N, f, ep, st);
   }
 }

@@ -49,7 +49,7 @@ k_fro_norm_static(const float* __restrict__ x, size_t n, double* out, unsigned c
     const float v = x[i];
     s = fmaf(v, v, s);
   }
-  reduce_finish((double)s, red);
+  reduce_finish(s, red);
 }
 
 // Device address of g_scratch on the current device, looked up once per device.

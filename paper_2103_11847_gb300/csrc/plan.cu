@@ -118,7 +118,7 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     if (!p->two_sided)
       return launch_slice_gemm(p->Ah, X, Y, n1, s, n2, n3, p->hM, p->hMinv, ep, st);
     if (cprod2_fits(s))
-      return launch_cprod2(p->Ah, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep, st);
+      return launch_cprod2(p->AhT, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep, st);
     TC_TRY(launch_slice_gemm(p->Ah, X, p->tmp1, n1, s, n2, n3, p->hM, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->Bh, Y, n1, s, s, n3, nullptr, p->hMinv, ep, st);
   }
@@ -149,7 +149,7 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     if (!p->two_sided)
       return launch_slice_gemm(p->AhT, Y, X, n2, s, n1, n3, p->hMinvT, p->hMT, ep, st);
     if (cprod2_fits(s))
-      return launch_cprod2(p->AhT, Y, p->BhT, X, n2, n1, s, n3, p->hMinvT, p->hMT, ep, st);
+      return launch_cprod2(p->Ah, Y, p->BhT, X, n2, n1, s, n3, p->hMinvT, p->hMT, ep, st);
     TC_TRY(launch_slice_gemm(p->AhT, Y, p->tmp1, n2, s, n1, n3, p->hMinvT, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->BhT, X, n2, s, s, n3, nullptr, p->hMT, ep, st);
   }

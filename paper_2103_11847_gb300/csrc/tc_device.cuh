@@ -38,32 +38,40 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Reduce one value per thread over the CTA (fixed tree), store the CTA partial,
-// and let the last CTA to arrive sum all partials in CTA order in FP64.
-// Must be called by every thread of every CTA of the launch.
-__device__ __forceinline__ void reduce_finish(double v, const Red& red) {
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce one value per thread over the CTA (fixed FP32 tree: a CTA sums at
+// most a few thousand FP32 terms), store the CTA partial in FP64, and let the
+// last CTA to arrive sum all partials in CTA order in FP64. The ticket is an
+// acquire-release atomic: it publishes this CTA's partial and, for the last
+// CTA, makes every other partial visible. Must be called by every thread of
+// every CTA of the launch.
+__device__ __forceinline__ void reduce_finish(float v, const Red& red) {
   __shared__ double sh_w[32];
   __shared__ int sh_last;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
   const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  v = warp_sum(v);
+  v = warp_sum_f(v);
   if ((tid & 31) == 0) sh_w[tid >> 5] = v;
   __syncthreads();
   if (tid < 32) {
-    double w = (tid < (nthr + 31) / 32) ? sh_w[tid] : 0.0;
-    w = warp_sum(w);
+    float wf = (tid < (nthr + 31) / 32) ? (float)sh_w[tid] : 0.f;
+    wf = warp_sum_f(wf);
     if (tid == 0) {
-      red.partials[bid] = w;
-      __threadfence();
-      unsigned t = atomicAdd(red.ticket, 1u);
+      red.partials[bid] = (double)wf;
+      unsigned t;
+      asm volatile("atom.add.acq_rel.gpu.u32 %0, [%1], 1;" : "=r"(t) : "l"(red.ticket) : "memory");
       sh_last = (t == nblk - 1);
     }
   }
   __syncthreads();
   if (!sh_last) return;
-  __threadfence();
   double acc = 0.0;
   for (unsigned i = tid; i < nblk; i += nthr) acc += __ldcg(red.partials + i);
   acc = warp_sum(acc);

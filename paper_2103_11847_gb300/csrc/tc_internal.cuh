@@ -132,10 +132,11 @@ int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, in
                       cudaStream_t st);
 // gemm2.cu: the whole two-sided fused product Y = epi[ A_k (pro X)_k B_k ]
 // in one launch of thread-block clusters, for N = s <= 256 (cprod2_fits).
-// A: M x K per slice, X: K x N, B: N x N, Y/prev: M x N.
+// At: the left factor K-major (K x M per slice: A_k^T), X: K x N, B: N x N,
+// Y/prev: M x N.
 bool cprod2_fits(int s);
 int cprod2_init();
-int launch_cprod2(const float* A, const float* X, const float* B, float* Y, int M, int K,
+int launch_cprod2(const float* At, const float* X, const float* B, float* Y, int M, int K,
                   int N, int nslices, const float* pro, const float* epi, const Epi& ep,
                   cudaStream_t st);
 // transform.cu: out[k][p] = ca * sum_l T[k][l] in[l][p] + cp * prev[k][p] over P pixels.

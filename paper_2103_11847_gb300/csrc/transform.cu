@@ -175,7 +175,7 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
       }
     }
   }
-  if (ep.red.out) reduce_finish((double)local, ep.red);
+  if (ep.red.out) reduce_finish(local, ep.red);
 }
 
 template <int KPW, int OUT>

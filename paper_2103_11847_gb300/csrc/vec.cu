@@ -25,7 +25,7 @@ k_reduce(const float* __restrict__ x, const float* __restrict__ other, size_t n,
     const float v = x[i];
     s = fmaf(v, other ? other[i] : v, s);
   }
-  reduce_finish((double)s, red);
+  reduce_finish(s, red);
 }
 
 __global__ void __launch_bounds__(NT)
@@ -160,7 +160,7 @@ k_mgs_pass(float* W, const float* __restrict__ Vi, const double* h, const float*
     W[i] = w;
     s = fmaf(w, Vnext ? Vnext[i] : w, s);
   }
-  reduce_finish((double)s, red);
+  reduce_finish(s, red);
 }
 
 }  // namespace
