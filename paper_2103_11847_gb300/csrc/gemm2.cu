@@ -146,6 +146,7 @@ template <int NS, bool VEC>
 __global__ void __launch_bounds__(NT, 1)
 k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
          const float* __restrict__ B, float* Y, int M, int K, int N, Mix f, Epi ep) {
+  pdl_wait();
   if (ep.skip && *ep.skip) return;  // uniform over the grid: no CTA reaches a barrier alone
   extern __shared__ __align__(16) float smem[];
   __shared__ float sh_coef[2];
@@ -296,6 +297,7 @@ k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
     mma_chunk<NS>(acc, Tt + c * BK * BM, K2p * BM, slot + kA, BK * BN, w, lane);
   }
   cp_wait<0>();
+  pdl_trigger();
   __syncthreads();
   acc_to_red<NS>(red, acc, w, lane);
   __syncthreads();
@@ -367,13 +369,15 @@ int run2(const float* At, const float* X, const float* B, float* Y, int M, int K
   cfg.blockDim = dim3(NT);
   cfg.dynamicSmemBytes = Lay<NS>::bytes(CS);
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = CS;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   TC_CUDA(cudaLaunchKernelEx(&cfg, k_cprod2<NS, VEC>, At, X, B, Y, M, K, N, f, ep));
   return TC_OK;
 }

@@ -32,6 +32,18 @@ __device__ __forceinline__ void coef_compute(const Coef& c, float* sh2) {
   }
 }
 
+// Programmatic dependent launch. A kernel launched with the programmatic
+// stream-serialization attribute may start while its predecessor finishes;
+// pdl_wait() blocks until every predecessor grid has completed and its
+// memory is visible, so it comes before the first read of anything a
+// predecessor wrote. pdl_trigger() lets the next launch start being
+// scheduled (it still waits in its own pdl_wait()). Both are no-ops for a
+// kernel launched without the attribute.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -63,6 +63,7 @@ k_lsqr_update(float* __restrict__ X, float* __restrict__ W, const float* __restr
               const double* beta, double* rhobar, double* phibar, double* phibar_hist,
               double* rgiv, int j, double tol, int* flags, const int* done_in, int* done_out,
               const int* stop_at) {
+  pdl_wait();
   if (*done_in) {
     if (blockIdx.x == 0 && threadIdx.x == 0) *done_out = 1;
     return;
@@ -78,6 +79,7 @@ k_lsqr_update(float* __restrict__ X, float* __restrict__ W, const float* __restr
     x[u] = i < n ? X[i] : 0.f;
     v[u] = i < n ? V[i] : 0.f;
   }
+  pdl_trigger();
   if (threadIdx.x == 0) {
     const double b = beta[j + 1], a = alpha[j + 1];
     const double rb = rhobar[j], pb = phibar[j];
@@ -199,10 +201,18 @@ int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, si
                        const int* stop_at) {
   const size_t blocks = (n + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
   TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
-  k_lsqr_update<<<(unsigned)blocks, NT, 0, st>>>(X, W, V, basis_slot, n, alpha, beta, rhobar,
-                                                 phibar, phibar_hist, rgiv, j, tol, flags,
-                                                 done_in, done_out, stop_at);
-  TC_CUDA(cudaGetLastError());
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)blocks);
+  cfg.blockDim = dim3(NT);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update, X, W, V, basis_slot, n, alpha, beta, rhobar,
+                             phibar, phibar_hist, rgiv, j, tol, flags, done_in, done_out,
+                             stop_at));
   return TC_OK;
 }
 
