@@ -71,8 +71,12 @@ def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp
     if precision != "fp32":  # transform, [transpose for TF32], tcgen05 GEMM, transform back
         per_product = 4 if precision == "tf32" else 3
     init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
-    per_iter = 2 * per_product + 1  # product, adjoint, update
-    tail = (5 if keep_basis else 0) + 1  # 3 GCV grid levels, final, combine; info
+    # product, adjoint, and the LSQR step: inside the next product on the
+    # two-sided fused route (s <= 256), else its own launch; the last step
+    # always has its own launch
+    inside = fused and two_sided and s <= 256 and precision == "fp32"
+    per_iter = 2 * per_product + (0 if inside else 1)
+    tail = (1 if inside else 0) + (5 if keep_basis else 0) + 1  # GCV levels, final, combine; info
     return init + iters * per_iter + tail
 
 

@@ -142,12 +142,31 @@ __device__ __forceinline__ void acc_to_red(float* red, const float (&acc)[NS][BM
 
 // At: the left factor K-major (NS x K x M, the slice transposes), X: NS x K x
 // N, B: NS x N x N, Y / prev / other: NS x M x N.
+//
+// A non-empty `step` (the previous LSQR step, which the forward product does
+// not depend on: it reads V~ and normalises it through its coefficient) is
+// run by the CTAs of this launch first: every CTA computes the same scalars
+// and updates its share of X and W while its first operand chunks are in
+// flight; the step's stop decision replaces ep.skip.
 template <int NS, bool VEC>
 __global__ void __launch_bounds__(NT, 1)
 k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
-         const float* __restrict__ B, float* Y, int M, int K, int N, Mix f, Epi ep) {
+         const float* __restrict__ B, float* Y, int M, int K, int N, Mix f, Epi ep,
+         LsqrStep step) {
   pdl_wait();
-  if (ep.skip && *ep.skip) return;  // uniform over the grid: no CTA reaches a barrier alone
+  __shared__ float sh_step[3];
+  __shared__ int sh_stop;
+  if (step.n) {
+    if (*step.done_in) {  // the solve stopped before this step
+      if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) *step.done_out = 1;
+      return;
+    }
+    if (threadIdx.x == 0)
+      sh_stop = lsqr_step_scalars(step, sh_step, blockIdx.x == 0 && blockIdx.y == 0);
+    __syncthreads();
+  } else if (ep.skip && *ep.skip) {
+    return;  // uniform over the grid: no CTA reaches a barrier alone
+  }
   extern __shared__ __align__(16) float smem[];
   __shared__ float sh_coef[2];
   float* ring = smem;
@@ -163,9 +182,6 @@ k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
   const int r0 = blockIdx.y * BM, c0 = q * BN;
   const size_t sA = (size_t)K * M, sX = (size_t)K * N, sB = (size_t)N * N, sY = (size_t)M * N;
   coef_compute(ep.coef, sh_coef);  // read after the barriers below
-  // Every CTA of the cluster must be running before a peer stores into its
-  // shared memory: arrive now, wait just before the first remote store.
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
 
   // zero the rounding rows of this CTA's panel (no peer writes them)
   for (int i = tid; i < NS * (K2p - K2) * BM; i += NT) {
@@ -243,6 +259,21 @@ k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
     if (s < nk1) issue1(s);
     cp_commit();
   }
+  if (step.n) {  // this CTA's share of the LSQR step, under the first copies
+    const size_t nb = (size_t)gridDim.x * gridDim.y;
+    const size_t b = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+    const size_t per = (step.n + nb - 1) / nb;
+    const size_t beg = b * per < step.n ? b * per : step.n;
+    const size_t end = beg + per < step.n ? beg + per : step.n;
+    lsqr_step_vectors(step, beg, end, sh_step[0], sh_step[1], sh_step[2], sh_stop != 0, NT);
+    if (sh_stop) {  // uniform: every CTA took the same decision
+      cp_wait<0>();
+      return;
+    }
+  }
+  // Every CTA of the cluster must be running before a peer stores into its
+  // shared memory: arrive now, wait just before the first remote store.
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory");
   zero_acc();
   for (int c = 0; c < nk1; ++c) {
     cp_wait<S - 2>();  // this thread's copies of chunk c have landed
@@ -362,7 +393,7 @@ k_cprod2(const float* __restrict__ At, const float* __restrict__ X,
 
 template <int NS, bool VEC>
 int run2(const float* At, const float* X, const float* B, float* Y, int M, int K, int N,
-         const Mix& f, const Epi& ep, cudaStream_t st) {
+         const Mix& f, const Epi& ep, const LsqrStep& step, cudaStream_t st) {
   const int CS = (N + BN - 1) / BN;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(CS, (M + BM - 1) / BM, 1);
@@ -378,15 +409,15 @@ int run2(const float* At, const float* X, const float* B, float* Y, int M, int K
   attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  TC_CUDA(cudaLaunchKernelEx(&cfg, k_cprod2<NS, VEC>, At, X, B, Y, M, K, N, f, ep));
+  TC_CUDA(cudaLaunchKernelEx(&cfg, k_cprod2<NS, VEC>, At, X, B, Y, M, K, N, f, ep, step));
   return TC_OK;
 }
 
 template <int NS>
 int run2v(bool vec, const float* At, const float* X, const float* B, float* Y, int M, int K,
-          int N, const Mix& f, const Epi& ep, cudaStream_t st) {
-  return vec ? run2<NS, true>(At, X, B, Y, M, K, N, f, ep, st)
-             : run2<NS, false>(At, X, B, Y, M, K, N, f, ep, st);
+          int N, const Mix& f, const Epi& ep, const LsqrStep& step, cudaStream_t st) {
+  return vec ? run2<NS, true>(At, X, B, Y, M, K, N, f, ep, step, st)
+             : run2<NS, false>(At, X, B, Y, M, K, N, f, ep, step, st);
 }
 
 template <int NS>
@@ -417,7 +448,7 @@ int cprod2_init() {
 
 int launch_cprod2(const float* At, const float* X, const float* B, float* Y, int M, int K,
                   int N, int nslices, const float* pro, const float* epi, const Epi& ep,
-                  cudaStream_t st) {
+                  const LsqrStep& step, cudaStream_t st) {
   TC_CHECK(nslices >= 1 && nslices <= TC_MAX_FUSED && cprod2_fits(N) && M >= 1 && K >= 1);
   Mix f{};
   for (int i = 0; i < nslices * nslices; ++i) {
@@ -427,9 +458,9 @@ int launch_cprod2(const float* At, const float* X, const float* B, float* Y, int
   const bool vec = M % 4 == 0 && N % 4 == 0 && al16(At) && al16(X) && al16(B) && al16(Y) &&
                    (!ep.prev || al16(ep.prev)) && (!ep.red.other || al16(ep.red.other));
   switch (nslices) {
-    case 1: return run2v<1>(vec, At, X, B, Y, M, K, N, f, ep, st);
-    case 2: return run2v<2>(vec, At, X, B, Y, M, K, N, f, ep, st);
-    case 3: return run2v<3>(vec, At, X, B, Y, M, K, N, f, ep, st);
-    default: return run2v<4>(vec, At, X, B, Y, M, K, N, f, ep, st);
+    case 1: return run2v<1>(vec, At, X, B, Y, M, K, N, f, ep, step, st);
+    case 2: return run2v<2>(vec, At, X, B, Y, M, K, N, f, ep, step, st);
+    case 3: return run2v<3>(vec, At, X, B, Y, M, K, N, f, ep, step, st);
+    default: return run2v<4>(vec, At, X, B, Y, M, K, N, f, ep, step, st);
   }
 }

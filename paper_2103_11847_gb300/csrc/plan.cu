@@ -110,15 +110,18 @@ Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* sta
 }
 
 // Y = A *c X [*c B] with the epilogue `ep` on the last stage.
-int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st) {
+int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
+              const LsqrStep* step) {
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  if (fused(p) && p->two_sided && cprod2_fits(s))  // the step runs inside the product
+    return launch_cprod2(p->AhT, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep,
+                         step ? *step : LsqrStep{}, st);
+  if (step) TC_TRY(launch_lsqr_update(*step, st));
   Epi mid;
   mid.skip = ep.skip;
   if (fused(p)) {
     if (!p->two_sided)
       return launch_slice_gemm(p->Ah, X, Y, n1, s, n2, n3, p->hM, p->hMinv, ep, st);
-    if (cprod2_fits(s))
-      return launch_cprod2(p->AhT, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep, st);
     TC_TRY(launch_slice_gemm(p->Ah, X, p->tmp1, n1, s, n2, n3, p->hM, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->Bh, Y, n1, s, s, n3, nullptr, p->hMinv, ep, st);
   }
@@ -149,7 +152,8 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     if (!p->two_sided)
       return launch_slice_gemm(p->AhT, Y, X, n2, s, n1, n3, p->hMinvT, p->hMT, ep, st);
     if (cprod2_fits(s))
-      return launch_cprod2(p->Ah, Y, p->BhT, X, n2, n1, s, n3, p->hMinvT, p->hMT, ep, st);
+      return launch_cprod2(p->Ah, Y, p->BhT, X, n2, n1, s, n3, p->hMinvT, p->hMT, ep,
+                           LsqrStep{}, st);
     TC_TRY(launch_slice_gemm(p->AhT, Y, p->tmp1, n2, s, n1, n3, p->hMinvT, nullptr, mid, st));
     return launch_slice_gemm(p->tmp1, p->BhT, X, n2, s, s, n3, nullptr, p->hMT, ep, st);
   }

@@ -171,8 +171,35 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags, done);
   TC_CUDA(cudaGetLastError());
 
+  // Step j's Givens recurrences and X, W updates ((c)-(g)) need alpha_{j+1}
+  // from the adjoint of step j; the forward product of step j + 1 does not
+  // need them, so step j runs at the start of that product (inside the
+  // product kernel on the two-sided fused route), and the last step after
+  // the loop.
+  auto make_step = [&](int j) {
+    LsqrStep u;
+    u.X = a.X;
+    u.W = W;
+    u.V = V;
+    u.basis_slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
+    u.n = p->Tx;
+    u.alpha = alpha;
+    u.beta = beta;
+    u.rhobar = rhobar;
+    u.phibar = phibar;
+    u.phibar_hist = a.hist;
+    u.rgiv = keep ? rgiv : nullptr;
+    u.j = j;
+    u.tol = a.tol;
+    u.flags = flags;
+    u.done_in = done + j;
+    u.done_out = done + j + 1;
+    u.stop_at = a.mlp ? flags + 6 : nullptr;
+    return u;
+  };
   for (int j = 0; j < a.itermax; ++j) {
-    // (a) U~_{j+1} = A V_j - alpha_j U_j = (1/alpha_j) A V~_j - (alpha_j/beta_j) U~_j
+    // (a) U~_{j+1} = A V_j - alpha_j U_j = (1/alpha_j) A V~_j - (alpha_j/beta_j) U~_j,
+    // preceded by step j - 1 (which decides done[j])
     {
       Epi ep;
       ep.coef.rule = COEF_GK;
@@ -181,8 +208,12 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.prev = (j == 0) ? a.C : U;
       ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
-      TC_TRY(cprod_epi(p, V, U, ep, st));
+      const LsqrStep prev = j > 0 ? make_step(j - 1) : LsqrStep{};
+      TC_TRY(cprod_epi(p, V, U, ep, st, j > 0 ? &prev : nullptr));
     }
+    // the learned predictor reads the first MLP_FEAT_STEPS steps
+    if (a.mlp && j == MLP_FEAT_STEPS)
+      TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
     // (b) V~_{j+1} = (1/beta_{j+1}) A^T U~_{j+1} - (beta_{j+1}/alpha_j) V~_j
     {
       Epi ep;
@@ -194,14 +225,10 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.skip = done + j;
       TC_TRY(adjoint_epi(p, U, V, ep, st));
     }
-    // (c)-(g) Givens recurrences and the X, W updates
-    float* slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
-    TC_TRY(launch_lsqr_update(a.X, W, V, slot, p->Tx, alpha, beta, rhobar, phibar, a.hist,
-                              keep ? rgiv : nullptr, j, a.tol, flags, done + j, done + j + 1,
-                              st, a.mlp ? flags + 6 : nullptr));
-    if (a.mlp && j + 1 == MLP_FEAT_STEPS)
-      TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   }
+  TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));
+  if (a.mlp && a.itermax == MLP_FEAT_STEPS)
+    TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   if (keep) {
     TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
                              a.mlp ? -1.0 : a.lambda, gwork, lam, y, gcv, st,

@@ -99,3 +99,76 @@ __device__ __forceinline__ void reduce_finish(float v, const Red& red) {
     }
   }
 }
+
+// LSQR step scalars (Algorithm 6 steps (c)-(g), 0-based step j):
+//   rho = hypot(rhobar_j, beta_{j+1}), c = rhobar_j/rho, s = beta_{j+1}/rho,
+//   theta = s alpha_{j+1}, rhobar_{j+1} = c alpha_{j+1},
+//   phi = c phibar_j, phibar_{j+1} = -s phibar_j,
+//   X += (phi/rho) W,  W = V_{j+1} - (theta/rho) W,  V_{j+1} = V~/alpha_{j+1}.
+// Called by one thread per CTA: every CTA derives the same values from the
+// same device scalars; `writer` (one thread of the grid) stores index j+1 of
+// the state, the history, the flags and done_out. sh = (phi/rho, 1/alpha,
+// theta/rho); returns the stop decision (breakdown, convergence, non-finite,
+// or the learned stop index reached).
+__device__ __forceinline__ bool lsqr_step_scalars(const LsqrStep& u, float* sh, bool writer) {
+  const int j = u.j;
+  const double b = u.beta[j + 1], a = u.alpha[j + 1];
+  const double rb = u.rhobar[j], pb = u.phibar[j];
+  const double rho = hypot(rb, b);
+  const double irho = 1.0 / rho;
+  const double c = rb * irho, s = b * irho;
+  const double theta = s * a;
+  const double phi = c * pb;
+  const double pbn = -s * pb;
+  const bool finite = isfinite(a) && isfinite(b) && isfinite(rho);
+  const bool brk = (a == 0.0);
+  const bool conv = fabs(pbn) < u.tol || (u.stop_at && *u.stop_at > 0 && j + 1 >= *u.stop_at);
+  sh[0] = (float)(phi * irho);
+  sh[1] = brk ? 0.f : (float)(1.0 / a);
+  sh[2] = (float)(theta * irho);
+  const bool stop = brk || conv || !finite;
+  if (writer) {
+    u.rhobar[j + 1] = c * a;
+    u.phibar[j + 1] = pbn;
+    if (u.rgiv) {  // R_k and f_k of Q_k [C~_k beta_1 e_1] (§3.3): rho, theta, phi
+      u.rgiv[3 * j] = rho;
+      u.rgiv[3 * j + 1] = theta;
+      u.rgiv[3 * j + 2] = phi;
+    }
+    if (u.phibar_hist) u.phibar_hist[j] = fabs(pbn);
+    u.flags[1] = j + 1;
+    if (!finite) u.flags[2] = TC_ENONFINITE;
+    else if (brk) u.flags[2] = TC_EBREAKDOWN;
+    else if (conv) u.flags[2] = 1;
+    *u.done_out = stop ? 1 : 0;
+  }
+  return stop;
+}
+
+// The vector part of an LSQR step on elements [beg, end), by the threads of
+// one CTA (nt threads), four loads in flight per thread.
+__device__ __forceinline__ void lsqr_step_vectors(const LsqrStep& u, size_t beg, size_t end,
+                                                  float cx, float cv, float cw, bool stop,
+                                                  int nt) {
+  for (size_t i0 = beg + threadIdx.x; i0 < end; i0 += 4 * (size_t)nt) {
+    float w[4], x[4], v[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t i = i0 + (size_t)q * nt;
+      w[q] = i < end ? u.W[i] : 0.f;
+      x[q] = i < end ? u.X[i] : 0.f;
+      v[q] = i < end ? u.V[i] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const size_t i = i0 + (size_t)q * nt;
+      if (i >= end) break;
+      u.X[i] = fmaf(cx, w[q], x[q]);
+      if (!stop) {
+        const float vn = cv * v[q];
+        u.W[i] = fmaf(-cw, w[q], vn);
+        if (u.basis_slot) u.basis_slot[i] = vn;
+      }
+    }
+  }
+}

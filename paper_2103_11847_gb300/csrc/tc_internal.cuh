@@ -53,6 +53,31 @@ struct Epi {
   const int* skip = nullptr;      // nonzero: the whole kernel returns at once
 };
 
+// One LSQR step (Algorithm 6 steps (c)-(g), iteration j, 0-based): the Givens
+// recurrences on the device scalars and the X, W (and basis) updates. Run by
+// its own kernel, or by the CTAs of the next forward product before their
+// GEMM (n == 0: no step). done_in = done[j] gates it; done_out = done[j+1] is
+// written by CTA 0. flags: [1] iterations, [2] status.
+struct LsqrStep {
+  float* X = nullptr;
+  float* W = nullptr;
+  const float* V = nullptr;       // V~_{j+1} (unnormalised)
+  float* basis_slot = nullptr;    // V_{j+1} is stored here when non-null
+  size_t n = 0;
+  const double* alpha = nullptr;
+  const double* beta = nullptr;
+  double* rhobar = nullptr;
+  double* phibar = nullptr;
+  double* phibar_hist = nullptr;
+  double* rgiv = nullptr;
+  int j = 0;
+  double tol = 0.0;
+  int* flags = nullptr;
+  const int* done_in = nullptr;
+  int* done_out = nullptr;
+  const int* stop_at = nullptr;   // learned stop index, or null
+};
+
 // --------------------------------------------------------------- workspaces --
 struct Scratch {
   double* partials = nullptr;
@@ -136,9 +161,10 @@ int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, in
 // Y/prev: M x N.
 bool cprod2_fits(int s);
 int cprod2_init();
+// A non-empty `step` is run by the product's CTAs first (and decides the skip).
 int launch_cprod2(const float* At, const float* X, const float* B, float* Y, int M, int K,
                   int N, int nslices, const float* pro, const float* epi, const Epi& ep,
-                  cudaStream_t st);
+                  const LsqrStep& step, cudaStream_t st);
 // transform.cu: out[k][p] = ca * sum_l T[k][l] in[l][p] + cp * prev[k][p] over P pixels.
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
                  const Epi& ep, cudaStream_t st);
@@ -154,11 +180,7 @@ int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
                   const int* skip, cudaStream_t st);
 int launch_scale(const float* in, float* out, size_t n, const Coef& c, const float* prev,
                  const int* skip, cudaStream_t st);
-int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
-                       double* alpha, double* beta, double* rhobar, double* phibar,
-                       double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       const int* done_in, int* done_out, cudaStream_t st,
-                       const int* stop_at = nullptr);
+int launch_lsqr_update(const LsqrStep& step, cudaStream_t st);
 int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
                    const int* kdev, const double* y, size_t n, const int* skip,
                    cudaStream_t st);
@@ -180,7 +202,11 @@ int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alph
                       double factor = 0.0, int* fallback = nullptr);
 
 // plan.cu helpers used by solvers
-int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st);
+// With a non-null `step`, the LSQR step runs before the product: inside the
+// product kernel (two-sided fused route) or as its own launch; ep.skip must
+// then be step->done_out.
+int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
+              const LsqrStep* step = nullptr);
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st);
 Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
 int tc_kernels_init();

@@ -44,87 +44,42 @@ k_scale(const float* __restrict__ in, float* out, size_t n, Coef c, const float*
   }
 }
 
-// LSQR, Algorithm 6 steps (c)-(g) for iteration j (0-based; the paper's j+1):
-//   rho = hypot(rhobar_j, beta_{j+1}), c = rhobar_j/rho, s = beta_{j+1}/rho,
-//   theta = s alpha_{j+1}, rhobar_{j+1} = c alpha_{j+1},
-//   phi = c phibar_j, phibar_{j+1} = -s phibar_j,
-//   X += (phi/rho) W,  W = V_{j+1} - (theta/rho) W,  V_{j+1} = Vt/alpha_{j+1}.
-// Every CTA derives the same scalars from alpha[j+1], beta[j+1], rhobar[j],
-// phibar[j]; CTA 0 writes index j+1 of the state, so no CTA reads a value
-// another CTA of this launch writes. Each thread loads its UPT elements of W,
-// X and V before thread 0's FP64 scalar chain, so the two latencies overlap.
-// done_in (= done[j]) gates the launch; done_out (= done[j+1], read by every
-// launch of the next step and by nothing in this one) is written by CTA 0.
-// flags: [1] iterations, [2] status.
+// One LSQR step as its own launch (lsqr_step_scalars, lsqr_step_vectors):
+// CTA b updates elements [b * 1024, (b + 1) * 1024). Each thread loads its
+// elements of W, X and V before thread 0's FP64 scalar chain, so the two
+// latencies overlap; CTA 0 writes the state.
 constexpr int UPT = 4;
-__global__ void __launch_bounds__(NT)
-k_lsqr_update(float* __restrict__ X, float* __restrict__ W, const float* __restrict__ V,
-              float* __restrict__ basis_slot, size_t n, const double* alpha,
-              const double* beta, double* rhobar, double* phibar, double* phibar_hist,
-              double* rgiv, int j, double tol, int* flags, const int* done_in, int* done_out,
-              const int* stop_at) {
+__global__ void __launch_bounds__(NT) k_lsqr_update(LsqrStep u) {
   pdl_wait();
-  if (*done_in) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) *done_out = 1;
+  if (*u.done_in) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *u.done_out = 1;
     return;
   }
-  __shared__ float sh[4];
+  __shared__ float sh[3];
   __shared__ int sh_stop;
   const size_t base = (size_t)blockIdx.x * (NT * UPT) + threadIdx.x;
   float w[UPT], x[UPT], v[UPT];
 #pragma unroll
-  for (int u = 0; u < UPT; ++u) {
-    const size_t i = base + (size_t)u * NT;
-    w[u] = i < n ? W[i] : 0.f;
-    x[u] = i < n ? X[i] : 0.f;
-    v[u] = i < n ? V[i] : 0.f;
+  for (int q = 0; q < UPT; ++q) {
+    const size_t i = base + (size_t)q * NT;
+    w[q] = i < u.n ? u.W[i] : 0.f;
+    x[q] = i < u.n ? u.X[i] : 0.f;
+    v[q] = i < u.n ? u.V[i] : 0.f;
   }
   pdl_trigger();
-  if (threadIdx.x == 0) {
-    const double b = beta[j + 1], a = alpha[j + 1];
-    const double rb = rhobar[j], pb = phibar[j];
-    const double rho = hypot(rb, b);
-    const double irho = 1.0 / rho;
-    const double c = rb * irho, s = b * irho;
-    const double theta = s * a;
-    const double phi = c * pb;
-    const double pbn = -s * pb;
-    const bool finite = isfinite(a) && isfinite(b) && isfinite(rho);
-    const bool brk = (a == 0.0);
-    // converged, or reached the step count a learned predictor chose
-    const bool conv = fabs(pbn) < tol || (stop_at && *stop_at > 0 && j + 1 >= *stop_at);
-    sh[0] = (float)(phi * irho);
-    sh[1] = brk ? 0.f : (float)(1.0 / a);
-    sh[2] = (float)(theta * irho);
-    sh_stop = brk || conv || !finite;
-    if (blockIdx.x == 0) {
-      rhobar[j + 1] = c * a;
-      phibar[j + 1] = pbn;
-      if (rgiv) {  // R_k and f_k of Q_k [C~_k beta_1 e_1] (§3.3): rho, theta, phi
-        rgiv[3 * j] = rho;
-        rgiv[3 * j + 1] = theta;
-        rgiv[3 * j + 2] = phi;
-      }
-      if (phibar_hist) phibar_hist[j] = fabs(pbn);
-      flags[1] = j + 1;
-      if (!finite) flags[2] = TC_ENONFINITE;
-      else if (brk) flags[2] = TC_EBREAKDOWN;
-      else if (conv) flags[2] = 1;
-      *done_out = (!finite || brk || conv) ? 1 : 0;
-    }
-  }
+  if (threadIdx.x == 0) sh_stop = lsqr_step_scalars(u, sh, blockIdx.x == 0);
   __syncthreads();
   const float cx = sh[0], cv = sh[1], cw = sh[2];
   const bool stop = sh_stop;
 #pragma unroll
-  for (int u = 0; u < UPT; ++u) {
-    const size_t i = base + (size_t)u * NT;
-    if (i >= n) break;
-    X[i] = fmaf(cx, w[u], x[u]);
+  for (int q = 0; q < UPT; ++q) {
+    const size_t i = base + (size_t)q * NT;
+    if (i >= u.n) break;
+    u.X[i] = fmaf(cx, w[q], x[q]);
     if (!stop) {
-      const float vn = cv * v[u];
-      W[i] = fmaf(-cw, w[u], vn);
-      if (basis_slot) basis_slot[i] = vn;
+      const float vn = cv * v[q];
+      u.W[i] = fmaf(-cw, w[q], vn);
+      if (u.basis_slot) u.basis_slot[i] = vn;
     }
   }
 }
@@ -194,12 +149,8 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
   return TC_OK;
 }
 
-int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, size_t n,
-                       double* alpha, double* beta, double* rhobar, double* phibar,
-                       double* phibar_hist, double* rgiv, int j, double tol, int* flags,
-                       const int* done_in, int* done_out, cudaStream_t st,
-                       const int* stop_at) {
-  const size_t blocks = (n + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
+int launch_lsqr_update(const LsqrStep& step, cudaStream_t st) {
+  const size_t blocks = (step.n + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
   TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
@@ -210,9 +161,7 @@ int launch_lsqr_update(float* X, float* W, const float* V, float* basis_slot, si
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update, X, W, V, basis_slot, n, alpha, beta, rhobar,
-                             phibar, phibar_hist, rgiv, j, tol, flags, done_in, done_out,
-                             stop_at));
+  TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update, step));
   return TC_OK;
 }
 
