@@ -18,13 +18,17 @@
 //
 // Search: the same three nested 200-point log grids as the general path
 // (first level [1e-10 s, s] with s = ||C~_k||_F). Each point of a level runs on
-// its own CTA, so the serial O(k) chains of the 200 points overlap across SMs.
+// its own CTA, so the serial O(k) FP64 chains of the 200 points spread over
+// the SMs (packing several points per SM measured slower: they share the
+// SM's narrow FP64 pipe).
 #include "gcv_eval.cuh"
 
 namespace {
 
 constexpr int NGRID = 200;
 constexpr int NLEVEL = 3;
+constexpr int PPC = 1;  // grid points (warps) per CTA: FP64 throughput per SM bounds
+                        // the chains, so one point per CTA spreads them widest
 
 // First index of the smallest of v[0..n) over one warp (ties to the lower index).
 __device__ int warp_argmin(const double* v, int n) {
@@ -44,14 +48,15 @@ __device__ int warp_argmin(const double* v, int n) {
   return bi < n ? bi : 0;
 }
 
-// One level of the search: CTA i evaluates grid point i of this level.
+// One level of the search: warp w of CTA b evaluates grid point PPC b + w.
 __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const double* alpha, const double* beta,
                                const int* kdev, int kmax, int variant, int level, double* lams,
                                double* vals) {
   const int k = kdev ? min(*kdev, kmax) : kmax;
-  const int i = blockIdx.x;
+  const int i = blockIdx.x * PPC + (threadIdx.x >> 5);
+  if (i >= NGRID) return;
   if (k <= 0) {
-    if (threadIdx.x == 0) {
+    if ((threadIdx.x & 31) == 0) {
       lams[level * NGRID + i] = nan("");
       vals[level * NGRID + i] = nan("");
     }
@@ -61,7 +66,7 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
   if (level == 0) {
     // ||C~_k||_F^2: diagonal alpha_1..alpha_k, subdiagonal beta_2..beta_{k+1}
     double s2 = 0.0;
-    for (int j = threadIdx.x; j < k; j += 32) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
+    for (int j = threadIdx.x & 31; j < k; j += 32) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s2 += __shfl_xor_sync(0xffffffffu, s2, o);
     hi = log(sqrt(s2));
@@ -72,7 +77,7 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
     lo = log(pl[max(b - 1, 0)]);
     hi = log(pl[min(b + 1, NGRID - 1)]);
   }
-  if (threadIdx.x != 0) return;
+  if ((threadIdx.x & 31) != 0) return;
   const double step = (hi - lo) / (NGRID - 1);
   const double lam = exp(i == NGRID - 1 ? hi : lo + i * step);
   const double pb = phibar[k];
@@ -128,8 +133,8 @@ int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alph
   double* vals = work + NLEVEL * NGRID;
   if (!(lambda_in >= 0.0)) {
     for (int level = 0; level < NLEVEL; ++level) {
-      k_gcv_bd_level<<<NGRID, 32, 0, st>>>(rg, phibar, alpha, beta, kdev, kmax, variant, level,
-                                           lams, vals);
+      k_gcv_bd_level<<<(NGRID + PPC - 1) / PPC, 32 * PPC, 0, st>>>(
+          rg, phibar, alpha, beta, kdev, kmax, variant, level, lams, vals);
       TC_CUDA(cudaGetLastError());
     }
   }

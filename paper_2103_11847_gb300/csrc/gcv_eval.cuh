@@ -22,7 +22,21 @@
 // With w~_j = d_j w_j, Rh^T w = P f and Rh u = w become
 //   w~_j = f'_j - g_{j-1} w~_{j-1},   u_j = w~_j / r2_j - g_j u_{j+1}.
 // y_l = R^T z, z = P u. FP64 throughout; GB300's FP64 latency is long, so the
-// chain is kept to about ten dependent operations per column.
+// chain is kept to about ten dependent operations per column, and 1 / r2 is
+// the hardware's approximate FP64 reciprocal refined by two Newton-Raphson
+// steps (y <- y + y (1 - x y), quadratic convergence from the approximation's
+// relative error, far below 2^-20, to the FP64 rounding level) instead of a
+// full IEEE division with its special-case paths: r2 >= l^2 > 0 is finite
+// and positive here.
+__device__ __forceinline__ double recip_nr(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 __device__ __forceinline__ double gcv_bd_eval(const double* rg, int k, double pbar2, double lam, int variant,
                               double* y) {
   double inv[TC_MAX_PROJ], gg[TC_MAX_PROJ], wt[TC_MAX_PROJ];
@@ -33,7 +47,7 @@ __device__ __forceinline__ double gcv_bd_eval(const double* rg, int k, double pb
     const double p = rg[3 * jr];
     const double t = (j + 1 < k) ? rg[3 * (jr - 1) + 1] : 0.0;
     const double r2 = fma(p, p, m2);
-    const double iv = 1.0 / r2;
+    const double iv = recip_nr(r2);
     const double g = p * t * iv;
     D = fma(T, iv, D);
     T = fma(g * g, T, 1.0);
