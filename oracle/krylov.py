@@ -133,11 +133,12 @@ def dc_gk(op, adj, C, m, variant="paper", lam=None):
                 gkb=g)
 
 
-def lsqr(op, adj, C, itermax, tol=0.0, keep_basis=False):
+def lsqr(op, adj, C, itermax, tol=0.0, keep_basis=False, keep_iterates=False):
     """Algorithm 6, DC-LSQR from X_0 = 0.
 
     Returns dict(X, phibar (|phibar_{j+1}| per iteration), alpha, beta, iters,
-    V (the normalised V_1..V_iters when keep_basis), status)."""
+    V (the normalised V_1..V_iters when keep_basis), Xs (the iterates
+    X_1..X_iters when keep_iterates), status)."""
     beta1 = fro(C)
     U = C / beta1
     t = adj(U)
@@ -148,6 +149,7 @@ def lsqr(op, adj, C, itermax, tol=0.0, keep_basis=False):
     rhobar, phibar = alpha1, beta1
     alphas, betas, phis = [alpha1], [beta1], []
     basis = [V] if keep_basis else None
+    iterates = [] if keep_iterates else None
     status = "maxiter"
     iters = 0
     for j in range(itermax):
@@ -171,6 +173,8 @@ def lsqr(op, adj, C, itermax, tol=0.0, keep_basis=False):
         X = X + (phi / rho) * W
         iters = j + 1
         phis.append(abs(phibar))
+        if keep_iterates:
+            iterates.append(X)
         if a == 0.0:  # beta_{j+1} = 0 or alpha_{j+1} = 0: X is the LS solution
             status = "breakdown"
             break
@@ -185,6 +189,8 @@ def lsqr(op, adj, C, itermax, tol=0.0, keep_basis=False):
                beta=np.array(betas), iters=iters, status=status)
     if keep_basis:
         out["V"] = basis[:iters]
+    if keep_iterates:
+        out["Xs"] = iterates
     return out
 
 
