@@ -87,6 +87,8 @@ typedef struct {
   double lambda; /* Tikhonov parameter used (NaN if none) */
   double gcv;    /* GCV value at lambda (NaN if none) */
   double beta1;  /* ||C||_F */
+  int kopt;      /* tc_lsqr_c_lcurve: the L-curve corner k_opt (0 otherwise) */
+  int reserved;
 } tc_solve_info;
 
 /* Library version string, and the message of the last TC_ECUDA (or of a
@@ -136,11 +138,33 @@ int tc_gkb_step(tc_plan* plan, int j, float* U, float* V, double* alpha,
  *     X_reg = V_k (*) y_lambda with lambda = `lambda` if it is >= 0, else the
  *     GCV minimiser (opts.gcv_variant).
  *   itermax: 1 .. 4096.  tol: stop when |phibar_{j+1}| < tol (0: never).
+ *     |phibar_{j+1}| = ||C - M(X_j)||_F, so tol = eta ||N||_F with a known
+ *     noise norm and eta slightly above 1 is the discrepancy principle named
+ *     in §2 (reading R19): the first iterate whose residual reaches the noise.
  *   phibar_hist: device double[itermax] or NULL: |phibar_{j+1}| per iteration.
  *   info: device tc_solve_info (required). */
 int tc_lsqr_c(tc_plan* plan, const float* C, float* X, float* X_reg,
               int itermax, double tol, double lambda, double* phibar_hist,
               tc_solve_info* info, tc_stream_t stream);
+
+/* DC-LSQR stopped at the L-curve corner k_opt (§3.3, after Algorithm 6).
+ * Runs up to kmax steps of Algorithm 6 from X_0 = 0 (tol as in tc_lsqr_c),
+ * then takes the K steps done as the curve P_k = (log ||R_k||_F,
+ * log ||X_k||_F), k = 1..K, and k_opt as the point of largest signed Menger
+ * curvature (the curvature of the circle through P_{k-1}, P_k, P_{k+1},
+ * positive for the L-curve's turn; smallest k on ties; k_opt = K when
+ * K < 3). The norms come from LSQR's rotations: ||R_k||_F = |phibar_{k+1}|
+ * and ||X_k||_F = ||y_k||_2 with R_k y_k = f_k, which equal the definitions
+ * for the orthonormal basis of Algorithm 4.
+ *   C: device n1 x s x n3.  X: device n2 x s x n3, the last iterate X_K.
+ *   X_opt: device n2 x s x n3, X_{k_opt} = V_k (*) y_k (§3.1 eq. (xm)).
+ *   kmax: 1 .. 128.  curve: device double[2 kmax] or NULL: ||R_k|| at
+ *   [k-1] and ||X_k|| at [kmax + k - 1] for k <= K.
+ *   info: device tc_solve_info (required): iters = K, kopt = k_opt,
+ *   resid = ||R_{k_opt}||_F, lambda and gcv NaN.
+ * Replayed as one captured CUDA graph like tc_lsqr_c when the plan allows. */
+int tc_lsqr_c_lcurve(tc_plan* plan, const float* C, float* X, float* X_opt, int kmax,
+                     double tol, double* curve, tc_solve_info* info, tc_stream_t stream);
 
 /* Restarted DC-GMRES(m) with Tikhonov/GCV, Algorithms 2 and 3 (§3.1).
  * Needs a square operator: n1 == n2 (the input and output shapes agree).

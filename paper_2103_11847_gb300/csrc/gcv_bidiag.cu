@@ -121,7 +121,89 @@ __global__ void k_gcv_bd_final(const double* rg, const double* phibar, const int
   if (gcv_out) *gcv_out = gv;
 }
 
+// L-curve corner (§3.3; reading: log-log curve, signed Menger curvature,
+// smallest k on ties). Thread t takes k = t + 1 <= K:
+//   ||R_k|| = |phibar_{k+1}|, ||X_k|| = ||y_k|| with R_k y_k = f_k solved
+//   upward (y_{k-1} = phi_{k-1} / rho_{k-1}, y_i = (phi_i - theta_{i+1} y_{i+1}) / rho_i),
+// then the curvature of the circle through P_{k-1}, P_k, P_{k+1} in log
+// coordinates, 2 (-cross) / (|P_k - P_{k-1}| |P_{k+1} - P_k| |P_{k+1} - P_{k-1}|),
+// and one warp takes the first maximum. Thread 0 writes y_{k_opt} (zero
+// beyond k_opt) for the basis combination. One CTA of TC_MAX_PROJ threads.
+__global__ void __launch_bounds__(TC_MAX_PROJ)
+k_lcurve(const double* rg, const double* phibar, const int* kdev, int kmax, double* curve,
+         double* y, int* kopt) {
+  __shared__ double s_ir[TC_MAX_PROJ], s_lr[TC_MAX_PROJ], s_lx[TC_MAX_PROJ], s_kap[TC_MAX_PROJ];
+  __shared__ int s_k;
+  const int K = max(0, min(*kdev, kmax));
+  const int t = threadIdx.x;
+  if (t < K) s_ir[t] = 1.0 / rg[3 * t];
+  __syncthreads();
+  if (t < K) {
+    const int k = t + 1;
+    double yi = rg[3 * (k - 1) + 2] * s_ir[k - 1];
+    double ss = yi * yi;
+    for (int i = k - 2; i >= 0; --i) {
+      yi = (rg[3 * i + 2] - rg[3 * i + 1] * yi) * s_ir[i];
+      ss = fma(yi, yi, ss);
+    }
+    const double rn = fabs(phibar[k]), xn = sqrt(ss);
+    if (curve) {
+      curve[t] = rn;
+      curve[kmax + t] = xn;
+    }
+    s_lr[t] = log(rn);
+    s_lx[t] = log(xn);
+  }
+  __syncthreads();
+  s_kap[t] = -INFINITY;
+  if (t >= 1 && t + 1 < K) {
+    const double ax = s_lr[t] - s_lr[t - 1], ay = s_lx[t] - s_lx[t - 1];
+    const double bx = s_lr[t + 1] - s_lr[t], by = s_lx[t + 1] - s_lx[t];
+    const double cx = s_lr[t + 1] - s_lr[t - 1], cy = s_lx[t + 1] - s_lx[t - 1];
+    const double den = hypot(ax, ay) * hypot(bx, by) * hypot(cx, cy);
+    const double cr = ax * by - ay * bx;
+    s_kap[t] = den == 0.0 ? 0.0 : -2.0 * cr / den;
+  }
+  __syncthreads();
+  if (t < 32) {
+    double best = -INFINITY;
+    int bi = TC_MAX_PROJ;
+    for (int i = t; i < TC_MAX_PROJ; i += 32)
+      if (s_kap[i] > best) { best = s_kap[i]; bi = i; }  // ascending i: first maximum kept
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+    }
+    if (t == 0) s_k = (K < 3) ? K : bi + 1;
+  }
+  __syncthreads();
+  const int ko = s_k;
+  for (int i = t; i < kmax; i += blockDim.x)
+    if (i >= ko) y[i] = 0.0;
+  if (t == 0) {
+    *kopt = ko;
+    if (ko > 0) {
+      double yi = rg[3 * (ko - 1) + 2] * s_ir[ko - 1];
+      y[ko - 1] = yi;
+      for (int i = ko - 2; i >= 0; --i) {
+        yi = (rg[3 * i + 2] - rg[3 * i + 1] * yi) * s_ir[i];
+        y[i] = yi;
+      }
+    }
+  }
+}
+
 }  // namespace
+
+int launch_lcurve(const double* rg, const double* phibar, const int* kdev, int kmax,
+                  double* curve, double* y, int* kopt, cudaStream_t st) {
+  TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ);
+  k_lcurve<<<1, TC_MAX_PROJ, 0, st>>>(rg, phibar, kdev, kmax, curve, y, kopt);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
 
 int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alpha,
                       const double* beta, const int* kdev, int kmax, int variant,

@@ -71,17 +71,21 @@ __global__ void k_lsqr_init(const double* alpha, const double* beta, double* rho
   done[0] = flags[2] != 0;
 }
 
+// kopt: the L-curve corner (then resid is ||R_{k_opt}||), or null.
 __global__ void k_lsqr_info(tc_solve_info* info, const int* flags, const double* phibar,
-                            const double* beta, const double* lam, const double* gcv) {
+                            const double* beta, const double* lam, const double* gcv,
+                            const int* kopt) {
   const int it = flags[1];
   info->iters = it;
   info->status = flags[2];
   info->cycles = 0;
   info->fallback = flags[7];
-  info->resid = fabs(phibar[it]);
+  info->resid = fabs(phibar[kopt ? *kopt : it]);
   info->lambda = lam ? *lam : nan("");
   info->gcv = gcv ? *gcv : nan("");
   info->beta1 = beta[0];
+  info->kopt = kopt ? *kopt : 0;
+  info->reserved = 0;
 }
 
 // GMRES helpers. flags: [0] done, [1] total steps, [2] status, [3] steps in the
@@ -123,6 +127,8 @@ __global__ void k_gmres_info(tc_solve_info* info, const int* flags, const double
   info->lambda = *lam;
   info->gcv = *gcv;
   info->beta1 = *beta1;
+  info->kopt = 0;
+  info->reserved = 0;
 }
 
 }  // namespace
@@ -229,37 +235,30 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));
   if (a.mlp && a.itermax == MLP_FEAT_STEPS)
     TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
-  if (keep) {
+  const bool gcv_on = keep && !a.lcurve;
+  if (keep && a.lcurve) {  // X_reg = X_{k_opt} at the L-curve corner (flags[8] = k_opt)
+    TC_TRY(launch_lcurve(rgiv, phibar, flags + 1, kp, a.curve, y, flags + 8, st));
+    TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 8, y, p->Tx, nullptr,
+                          st));
+  } else if (keep) {
     TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
                              a.mlp ? -1.0 : a.lambda, gwork, lam, y, gcv, st,
                              a.mlp ? lam_pred : nullptr, a.factor, flags + 7));
     TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
                           st));
   }
-  k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, keep ? lam : nullptr,
-                               keep ? gcv : nullptr);
+  k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, gcv_on ? lam : nullptr,
+                               gcv_on ? gcv : nullptr, (keep && a.lcurve) ? flags + 8 : nullptr);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 
-extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int itermax,
-                         double tol, double lambda, double* phibar_hist, tc_solve_info* info,
-                         tc_stream_t stream) {
-  if (!p || !C || !X || !info) return TC_EINVAL;
-  if (itermax < 1 || itermax > 4096 || !(tol >= 0.0)) return TC_EINVAL;
-  if (X_reg && itermax > TC_MAX_PROJ) return TC_EINVAL;
-  if ((const void*)C == (const void*)X || (X_reg && (X_reg == X))) return TC_EINVAL;
-  TC_TRY(ensure_lsqr(p, itermax, X_reg != nullptr));
-  cudaStream_t st = (cudaStream_t)stream;
-  LsqrArgs a{C, X, X_reg, itermax, tol, lambda, phibar_hist, info};
-  if (!p->opts.use_graphs) return lsqr_enqueue(p, a, st);
+namespace {
 
-  uint64_t tb, lb;
-  std::memcpy(&tb, &tol, 8);
-  std::memcpy(&lb, &lambda, 8);
-  const uintptr_t key[8] = {(uintptr_t)C, (uintptr_t)X, (uintptr_t)X_reg, (uintptr_t)itermax,
-                            (uintptr_t)tb, (uintptr_t)lb, (uintptr_t)phibar_hist,
-                            (uintptr_t)info};
+// Run a c-LSQR solve: enqueue it directly, or replay the plan's captured
+// graph, capturing it again when the solve's parameters (key) changed.
+int run_lsqr(tc_plan* p, const LsqrArgs& a, const uintptr_t (&key)[10], cudaStream_t st) {
+  if (!p->opts.use_graphs) return lsqr_enqueue(p, a, st);
   if (!p->lsqr_graph || std::memcmp(key, p->lsqr_key, sizeof(key)) != 0) {
     if (p->lsqr_graph) {
       cudaGraphExecDestroy(p->lsqr_graph);
@@ -288,6 +287,44 @@ extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int
   }
   TC_CUDA(cudaGraphLaunch(p->lsqr_graph, st));
   return TC_OK;
+}
+
+}  // namespace
+
+extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int itermax,
+                         double tol, double lambda, double* phibar_hist, tc_solve_info* info,
+                         tc_stream_t stream) {
+  if (!p || !C || !X || !info) return TC_EINVAL;
+  if (itermax < 1 || itermax > 4096 || !(tol >= 0.0)) return TC_EINVAL;
+  if (X_reg && itermax > TC_MAX_PROJ) return TC_EINVAL;
+  if ((const void*)C == (const void*)X || (X_reg && (X_reg == X))) return TC_EINVAL;
+  TC_TRY(ensure_lsqr(p, itermax, X_reg != nullptr));
+  LsqrArgs a{C, X, X_reg, itermax, tol, lambda, phibar_hist, info};
+  uint64_t tb, lb;
+  std::memcpy(&tb, &tol, 8);
+  std::memcpy(&lb, &lambda, 8);
+  const uintptr_t key[10] = {(uintptr_t)C, (uintptr_t)X, (uintptr_t)X_reg, (uintptr_t)itermax,
+                             (uintptr_t)tb, (uintptr_t)lb, (uintptr_t)phibar_hist,
+                             (uintptr_t)info, 0, 0};
+  return run_lsqr(p, a, key, (cudaStream_t)stream);
+}
+
+extern "C" int tc_lsqr_c_lcurve(tc_plan* p, const float* C, float* X, float* X_opt, int kmax,
+                                double tol, double* curve, tc_solve_info* info,
+                                tc_stream_t stream) {
+  if (!p || !C || !X || !X_opt || !info) return TC_EINVAL;
+  if (kmax < 1 || kmax > TC_MAX_PROJ || !(tol >= 0.0)) return TC_EINVAL;
+  if ((const void*)C == (const void*)X || (const void*)C == (const void*)X_opt || X_opt == X)
+    return TC_EINVAL;
+  TC_TRY(ensure_lsqr(p, kmax, true));
+  LsqrArgs a{C, X, X_opt, kmax, tol, -1.0, nullptr, info};
+  a.lcurve = 1;
+  a.curve = curve;
+  uint64_t tb;
+  std::memcpy(&tb, &tol, 8);
+  const uintptr_t key[10] = {(uintptr_t)C, (uintptr_t)X, (uintptr_t)X_opt, (uintptr_t)kmax,
+                             (uintptr_t)tb, 0, 0, (uintptr_t)info, 1, (uintptr_t)curve};
+  return run_lsqr(p, a, key, (cudaStream_t)stream);
 }
 
 // ------------------------------------------------------------ Golub-Kahan ----

@@ -123,7 +123,7 @@ struct tc_plan {
   cudaStream_t cap_stream = nullptr;
   // graph cache for tc_lsqr_c
   cudaGraphExec_t lsqr_graph = nullptr;
-  uintptr_t lsqr_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  uintptr_t lsqr_key[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
 };
 
 // ----------------------------------------------------------- error helpers --
@@ -201,6 +201,13 @@ int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alph
                       double* gcv_out, cudaStream_t st, const double* lam_pred = nullptr,
                       double factor = 0.0, int* fallback = nullptr);
 
+// gcv_bidiag.cu: the L-curve corner k_opt from LSQR's rotations (rg as in
+// launch_gcv_bidiag); writes *kopt, y_{k_opt} (kmax doubles, zero beyond
+// k_opt) and, when curve is non-null, ||R_k|| at [k-1] and ||X_k|| at
+// [kmax + k - 1].
+int launch_lcurve(const double* rg, const double* phibar, const int* kdev, int kmax,
+                  double* curve, double* y, int* kopt, cudaStream_t st);
+
 // plan.cu helpers used by solvers
 // With a non-null `step`, the LSQR step runs before the product: inside the
 // product kernel (two-sided fused route) or as its own launch; ep.skip must
@@ -223,6 +230,8 @@ struct LsqrArgs {
   tc_solve_info* info;
   const tc_mlp* mlp = nullptr;  // learned stop index and lambda (learned.cu)
   double factor = 1.05;         // GCV fallback threshold for the learned lambda
+  int lcurve = 0;               // X_reg = X_{k_opt} at the L-curve corner, no GCV
+  double* curve = nullptr;      // L-curve norms (2 itermax doubles) or null
 };
 // learned.cu: after MLP_FEAT_STEPS steps, features -> network -> lam_pred and
 // stop_at (the step count to stop after).

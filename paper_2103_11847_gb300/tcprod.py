@@ -29,7 +29,7 @@ class tc_opts(ctypes.Structure):
 class tc_solve_info(ctypes.Structure):
     _fields_ = [("iters", c_int), ("status", c_int), ("cycles", c_int), ("fallback", c_int),
                 ("resid", c_double), ("lambda_", c_double), ("gcv", c_double),
-                ("beta1", c_double)]
+                ("beta1", c_double), ("kopt", c_int), ("reserved", c_int)]
 
 
 _SIGS = {
@@ -46,6 +46,8 @@ _SIGS = {
                     c_int),
     "tc_lsqr_c": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_double, c_void_p,
                    c_void_p, c_void_p], c_int),
+    "tc_lsqr_c_lcurve": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_double, c_void_p,
+                          c_void_p, c_void_p], c_int),
     "tc_gmres_c": ([c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_int, c_double, c_double,
                     c_void_p, c_void_p], c_int),
     "tc_tikhonov_gcv": ([c_void_p, c_int, c_void_p, c_int, c_double, c_void_p, c_void_p,
@@ -177,7 +179,7 @@ def read_info(buf):
     info = tc_solve_info.from_buffer_copy(raw)
     return dict(iters=info.iters, status=STATUS_NAMES.get(info.status, info.status),
                 cycles=info.cycles, fallback=info.fallback, resid=info.resid, lam=info.lambda_, gcv=info.gcv,
-                beta1=info.beta1)
+                beta1=info.beta1, kopt=info.kopt)
 
 
 def tc_lsqr_c(h, C, X, X_reg, itermax, tol, lam, phibar_hist, info, stream=None):
@@ -185,6 +187,12 @@ def tc_lsqr_c(h, C, X, X_reg, itermax, tol, lam, phibar_hist, info, stream=None)
                                         -1.0 if lam is None else float(lam),
                                         _ptr(phibar_hist, torch.float64),
                                         _ptr(info, torch.uint8), _stream(stream)))
+
+
+def tc_lsqr_c_lcurve(h, C, X, X_opt, kmax, tol, curve, info, stream=None):
+    _check("tc_lsqr_c_lcurve", lib().tc_lsqr_c_lcurve(h, _ptr(C), _ptr(X), _ptr(X_opt), kmax, tol,
+                                                      _ptr(curve, torch.float64),
+                                                      _ptr(info, torch.uint8), _stream(stream)))
 
 
 def tc_gmres_c(h, C, X0, X, m, itermax, tol, lam, info, stream=None):
@@ -370,6 +378,16 @@ class Plan:
         info = new_info()
         tc_lsqr_c(self.handle, C, X, Xr, itermax, tol, lam, hist, info)
         return X, Xr, hist, info
+
+    def lsqr_lcurve(self, C, kmax, tol=0.0):
+        """c-LSQR stopped at the L-curve corner: (X_K, X_{k_opt}, curve, info);
+        curve[:kmax] holds ||R_k||, curve[kmax:] ||X_k|| for k = 1..K."""
+        X = torch.empty(self.xshape(), device="cuda")
+        Xo = torch.empty(self.xshape(), device="cuda")
+        curve = torch.full((2 * kmax,), float("nan"), dtype=torch.float64, device="cuda")
+        info = new_info()
+        tc_lsqr_c_lcurve(self.handle, C, X, Xo, kmax, tol, curve, info)
+        return X, Xo, curve, info
 
     def gmres(self, C, m, itermax, tol=0.0, lam=None, X0=None):
         X = torch.empty(self.xshape(), device="cuda")

@@ -4,6 +4,8 @@ match the header's sizes."""
 import ctypes
 import os
 import re
+import shutil
+import subprocess
 
 import pytest
 
@@ -52,10 +54,31 @@ def test_version_string_without_gpu(libpath):
     assert b"sm_103a" in lib.tc_version()
 
 
-def test_binding_structs_match_header():
+def _c_layout(tmp_path, struct, fields):
+    """sizeof and offsetof of a header struct, from the host C compiler."""
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if not gcc:
+        pytest.skip("no host C compiler")
+    src = tmp_path / "layout.c"
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "tcprod.h"', 'int main(void) {',
+             f'  printf("%zu\\n", sizeof({struct}));']
+    lines += [f'  printf("%zu\\n", offsetof({struct}, {f}));' for f in fields]
+    lines += ['  return 0;', '}']
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    return int(out[0]), [int(x) for x in out[1:]]
+
+
+def test_binding_structs_match_header(tmp_path):
     from paper_2103_11847_gb300 import tcprod
-    assert ctypes.sizeof(tcprod.tc_opts) == 8 * 4
-    assert ctypes.sizeof(tcprod.tc_solve_info) == 4 * 4 + 4 * 8
+    for cls, struct in ((tcprod.tc_opts, "tc_opts"), (tcprod.tc_solve_info, "tc_solve_info")):
+        names = [f[0] for f in cls._fields_]
+        cnames = ["lambda" if n == "lambda_" else n for n in names]
+        size, offs = _c_layout(tmp_path, struct, cnames)
+        assert ctypes.sizeof(cls) == size, struct
+        assert [getattr(cls, n).offset for n in names] == offs, struct
     assert set(tcprod._SIGS) == set(declared_functions())
 
 
