@@ -368,6 +368,68 @@ def graph_time(call, reps):
     return e0.elapsed_time(e1) / reps
 
 
+# Tables 1-4 (§4): image size, noise, and the iteration counts the paper used
+# for DC-GMRES(10) (itermax), DC-GK (mmax, Tikhonov/GCV on the projected
+# problem) and DC-LSQR (k_opt), with the paper's CPU seconds for context.
+PAPER_TABLES = [
+    (256, 1e-3, dict(gmres=(10, 5.21), gk=(15, 1.62), lsqr=(14, 1.23))),
+    (256, 1e-2, dict(gmres=(15, 7.14), gk=(20, 1.92), lsqr=(15, 1.23))),
+    (1024, 1e-3, dict(gmres=(10, 100.35), gk=(20, 25.33), lsqr=(15, 19.45))),
+    (1024, 1e-2, dict(gmres=(15, 137.43), gk=(25, 30.22), lsqr=(20, 26.43))),
+]
+
+
+def paper_shaped(reps=3):
+    """The paper's three methods on paper-shaped synthetic problems (the image
+    sizes, blur and iteration counts of Tables 1-4; inputs.paper_deblur), each
+    solve timed on the device (median of `reps` after a warm-up) with its
+    relative error and SNR against the clean image."""
+    import torch
+    from paper_2103_11847_gb300 import inputs, tcprod
+    dev = torch.device("cuda")
+    st = torch.cuda.current_stream()
+    rows = []
+    for n, nu, methods in PAPER_TABLES:
+        w = inputs.paper_deblur(n=n, nu=nu)
+        A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+        B = torch.from_numpy(w["B"].astype(np.float32)).to(dev)
+        Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
+        G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
+        plan = tcprod.Plan(A, B, s=n)
+        Cc = plan.cprod(Xt)
+        C = (Cc + (nu * Cc.norm() / G.norm()) * G).contiguous()
+        X = torch.empty(plan.xshape(), device=dev)
+        Xr = torch.empty(plan.xshape(), device=dev)
+        info = tcprod.new_info()
+        calls = {
+            "DC-LSQR": (methods["lsqr"], lambda k: tcprod.tc_lsqr_c(plan.handle, C, X, None, k, 0.0,
+                                                                    None, None, info), X),
+            "DC-GK": (methods["gk"], lambda k: tcprod.tc_lsqr_c(plan.handle, C, X, Xr, k, 0.0, None,
+                                                                None, info), Xr),
+            "DC-GMRES(10)": (methods["gmres"], lambda k: tcprod.tc_gmres_c(plan.handle, C, None, X, 10,
+                                                                          k, 0.0, None, info), X),
+        }
+        for name, ((k, paper_s), call, out) in calls.items():
+            call(k)
+            torch.cuda.synchronize()
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(st)
+                call(k)
+                e1.record(st)
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            err = float((out - Xt).norm() / Xt.norm())
+            snr = float(10.0 * torch.log10(((Xt - Xt.mean()) ** 2).sum() / ((out - Xt) ** 2).sum()))
+            inf = tcprod.read_info(info)
+            rows.append({"image": f"{n}x{n}x3", "nu": nu, "method": name, "iterations": k,
+                         "gpu_ms": statistics.median(ts), "paper_cpu_s": paper_s,
+                         "rel_err": err, "snr_db": snr, "lambda": inf["lam"]})
+        plan.close()
+    return rows
+
+
 def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -581,11 +643,17 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
                     help="slice-GEMM inputs of the main workload (tensor-core forms need "
                          "one-sided plans: video_512 or colour_64)")
+    ap.add_argument("--paper-shaped", action="store_true",
+                    help="time the paper's three methods on the shapes of its Tables 1-4")
     ap.add_argument("--cpu-worker", default=None)
     ap.add_argument("--cpu-budget", type=float, default=12.0)
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args.cpu_worker, args.cpu_budget)
+        return
+    if args.paper_shaped:
+        for row in paper_shaped():
+            print(json.dumps(row))
         return
     if args.impl == "reference":
         run_reference(args)

@@ -122,6 +122,21 @@ def two_sided_deblur(n=256, n3=3, sigma_a=3.0, sigma_b=2.0, r=8, nu=1e-3, seed=1
                 name=f"two_sided_{n}x{n}x{n3}")
 
 
+def paper_deblur(n=256, nu=1e-3, sigma=4.0, r=6, weights=(1.0, 0.7, 0.7), seed=7):
+    """Paper-shaped colour deblur, the shapes of Tables 1-4 (§4): two-sided
+    A *c X *c B (n x n x 3) with the within-channel Gaussian G_{4,6} on both
+    sides. Slice k of A is weights[k] G (the eigenvalues 1, 0.7, 0.7 of the
+    paper's cross-channel matrix, placed on the slices directly), every slice
+    of B is G."""
+    rng = rng_for(seed)
+    G = gaussian_blur(n, sigma, r)
+    A = np.stack([w * G for w in weights])
+    B = np.stack([G] * len(weights))
+    X = image(n, rng, channels=len(weights))
+    return dict(A=A, B=B, X_true=X, G=gaussian_noise(X.shape, rng), nu=nu,
+                name=f"paper_{n}x{n}x{len(weights)}")
+
+
 def video_deblur(n=512, frames=64, sigma0=1.5, sigma1=3.5, nu=1e-3, seed=2):
     """Video (n x n x frames), one-sided: frame k of A is G_{s_k, ceil(3 s_k)}
     with s_k linear from sigma0 to sigma1."""
