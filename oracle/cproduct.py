@@ -32,6 +32,7 @@ Readings (where the text is ambiguous):
     under the TH product.
 """
 import numpy as np
+import scipy.fft
 
 
 # ----------------------------------------------------------------- §2.1 -----
@@ -200,3 +201,43 @@ def circledast(VV, y):
     for v, c in zip(VV, y):
         out = out + c * np.asarray(v, np.float64)
     return out
+
+
+# ----------------------------------------------- the ORTHODCT variant -----
+# Algorithm 1 taken literally (reading R20): A~ = dct(A, [], 3), the
+# orthonormal DCT-II of every tube (the library routine scipy.fft.dct, type 2,
+# norm "ortho", stands for MATLAB's dct), then Y~_k = A~_k X~_k [B~_k] and
+# Y = idct(Y~, [], 3). The transform is orthogonal, so the exact adjoint of
+# X -> A *c X [*c B] applies A~_k^T (and B~_k^T) between dct and idct, which is
+# the same product with the slice-transposed factors.
+
+def dct3(A):
+    """dct(A, [], 3): orthonormal DCT-II along mode 3 (axis 0 here)."""
+    return scipy.fft.dct(np.asarray(A, np.float64), type=2, norm="ortho", axis=0)
+
+
+def idct3(A):
+    """idct(A, [], 3), the inverse of dct3."""
+    return scipy.fft.idct(np.asarray(A, np.float64), type=2, norm="ortho", axis=0)
+
+
+def cprod_orthodct(A, X, B=None):
+    """Algorithm 1 with dct/idct: Y = idct(dct(A)_k dct(X)_k [dct(B)_k])."""
+    Yh = np.einsum('kij,kjl->kil', dct3(A), dct3(X))
+    if B is not None:
+        Yh = np.einsum('kij,kjl->kil', Yh, dct3(B))
+    return idct3(Yh)
+
+
+def cprod_adjoint_orthodct(A, Y, B=None):
+    """Exact adjoint of the ORTHODCT product: idct(dct(A)_k^T dct(Y)_k [dct(B)_k^T])."""
+    Xh = np.einsum('kji,kjl->kil', dct3(A), dct3(Y))
+    if B is not None:
+        Xh = np.einsum('kij,klj->kil', Xh, dct3(B))
+    return idct3(Xh)
+
+
+def identity_tensor_orthodct(n, n3):
+    """The tensor whose dct along mode 3 is I_n in every slice."""
+    return idct3(np.broadcast_to(np.eye(n), (n3, n, n)).copy())
+
