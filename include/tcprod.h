@@ -67,11 +67,18 @@ typedef enum {
   TC_GCV_FULL = 1   /* GCV of the (k+1) x k projected least-squares problem */
 } tc_gcv_variant;
 
+typedef enum {
+  TC_TH = 0,       /* A~ = A x_3 M, M = W^{-1} C (I + Z): Definition 2.1, Remark 2.1 */
+  TC_ORTHODCT = 1  /* A~ = dct(A, [], 3): Algorithm 1 as printed (orthonormal DCT-II;
+                      the slice transpose is then the adjoint) */
+} tc_product;
+
 typedef struct {
   int precision;   /* tc_precision */
   int gcv_variant; /* tc_gcv_variant */
   int use_graphs;  /* nonzero: solves replay a captured CUDA graph */
-  int reserved[5]; /* must be zero */
+  int product;     /* tc_product (default TC_TH) */
+  int reserved[4]; /* must be zero */
 } tc_opts;
 
 /* Outcome of a solve, written to DEVICE memory by the solve (copy it back
@@ -100,7 +107,7 @@ const char* tc_last_error(void);
  * once with its slice transposes, and keeps them with its workspaces in
  * device memory it allocates (freed by tc_plan_destroy).
  *   A: device, n1 x n2 x n3.   B: device s x s x n3, or NULL for A *c X.
- *   opts: may be NULL (FP32, paper GCV, graphs on).
+ *   opts: may be NULL (FP32, paper GCV, graphs on, TH product).
  * Sizes must be >= 1; n3 <= 64. Synchronises `stream` before returning.
  * Source: Remark 2.1 and eqs. (dft9), (dft8), §2.2. */
 int tc_plan_create(tc_plan** plan, int n1, int n2, int s, int n3,

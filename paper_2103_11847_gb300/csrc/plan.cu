@@ -176,10 +176,21 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
 }
 
 namespace {
+// ORTHODCT (Algorithm 1 as printed): M = C_{n3}, M^{-1} = C_{n3}^T.
+void transform_pair_orthodct(int n, std::vector<double>& M, std::vector<double>& Mi) {
+  dct2(n, M);
+  Mi.assign((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) Mi[(size_t)i * n + j] = M[(size_t)j * n + i];
+}
+
 int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
   std::vector<double> M, Mi;
-  transform_pair(n3, M, Mi);
+  if (p->opts.product == TC_ORTHODCT)
+    transform_pair_orthodct(n3, M, Mi);
+  else
+    transform_pair(n3, M, Mi);
   // M Mi must be the identity; anything else is a bug in the closed forms.
   for (int i = 0; i < n3; ++i)
     for (int j = 0; j < n3; ++j) {
@@ -306,6 +317,7 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
     if (o.precision != TC_FP32 && o.precision != TC_TF32 && o.precision != TC_BF16)
       return TC_EINVAL;
     if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
+    if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
   }
   if (o.precision != TC_FP32) {
     // tensor-core forms: one-sided, every dimension a multiple of 8 (16-byte

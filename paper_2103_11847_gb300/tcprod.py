@@ -17,13 +17,14 @@ TC_OK, TC_EINVAL, TC_ECUDA, TC_EBREAKDOWN, TC_ENONFINITE, TC_ETIMEOUT, TC_ENOMEM
     TC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 TC_FP32, TC_TF32, TC_BF16 = 0, 1, 2
 TC_GCV_PAPER, TC_GCV_FULL = 0, 1
+TC_TH, TC_ORTHODCT = 0, 1
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
                 TC_ENONFINITE: "nonfinite"}
 
 
 class tc_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("gcv_variant", c_int), ("use_graphs", c_int),
-                ("reserved", c_int * 5)]
+                ("product", c_int), ("reserved", c_int * 4)]
 
 
 class tc_solve_info(ctypes.Structure):
@@ -129,7 +130,7 @@ def tc_version():
 
 
 def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                   use_graphs=True, stream=None):
+                   use_graphs=True, stream=None, product=TC_TH):
     """A: (n3, n1, n2); B: (n3, s, s) or None (then s must be given)."""
     n3, n1, n2 = A.shape
     if B is not None:
@@ -137,7 +138,7 @@ def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPE
         _ptr(B, shape=(n3, s, s), name="B")
     if s is None:
         raise ValueError("s (columns of X) is required for a one-sided plan")
-    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)))
+    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)), product)
     h = c_void_p()
     _check("tc_plan_create", lib().tc_plan_create(ctypes.byref(h), n1, n2, s, n3, _ptr(A, name="A"),
                                                   _ptr(B, name="B"), ctypes.byref(o),
@@ -338,11 +339,12 @@ class Plan:
     """Owns a tc_plan for A (and B); methods allocate outputs as torch tensors."""
 
     def __init__(self, A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                 use_graphs=True):
+                 use_graphs=True, product=TC_TH):
         self.n3, self.n1, self.n2 = A.shape
         self.s = B.shape[1] if B is not None else s
         self.two_sided = B is not None
-        self.handle = tc_plan_create(A, B, s, precision, gcv_variant, use_graphs)
+        self.handle = tc_plan_create(A, B, s, precision, gcv_variant, use_graphs,
+                                     product=product)
 
     def close(self):
         if self.handle is not None:
