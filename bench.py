@@ -248,6 +248,31 @@ def precision_forms(dev, peaks, steps=3):
     for name in ("tf32", "bf16"):
         out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
         out[name]["speedup_vs_fp32"] = out[name]["iters_per_s"] / out["fp32"]["iters_per_s"]
+    # Algorithm 1's dct reading (ORTHODCT): off the fused route LSQR runs in the
+    # transform domain (slice GEMMs + epilogue pass, no per-product transforms)
+    od = {}
+    for name, code in (("fp32", tcprod.TC_FP32), ("bf16", tcprod.TC_BF16)):
+        plan = tcprod.Plan(A, s=s, precision=code, product=tcprod.TC_ORTHODCT)
+        Cc = plan.cprod(Xt)
+        Co = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
+        X = torch.empty(plan.xshape(), device=dev)
+        Xr = torch.empty(plan.xshape(), device=dev)
+        info = tcprod.new_info()
+        tcprod.tc_lsqr_c(plan.handle, Co, X, Xr, iters, 0.0, None, None, info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            tcprod.tc_lsqr_c(plan.handle, Co, X, Xr, iters, 0.0, None, None, info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        od[name] = {"iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+                    "rel_err_reg": float((Xr - Xt).norm() / Xt.norm())}
+        plan.close()
+    od["bf16"]["matched_error"] = bool(abs(od["bf16"]["rel_err_reg"] - od["fp32"]["rel_err_reg"])
+                                       <= 0.02 * od["fp32"]["rel_err_reg"])
+    out["orthodct_transform_domain"] = od
     return out
 
 
@@ -458,7 +483,8 @@ def run_gpu(args):
     Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
     G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
     prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16}[args.precision]
-    plan = tcprod.Plan(A, B, s=s, precision=prec)
+    product = {"th": tcprod.TC_TH, "orthodct": tcprod.TC_ORTHODCT}[args.product]
+    plan = tcprod.Plan(A, B, s=s, precision=prec, product=product)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
     Cc = plan.cprod(Xt)
     C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
@@ -572,7 +598,7 @@ def run_gpu(args):
             "config": {"workload": f"{args.workload}: c-LSQR {iters} it + Tikhonov/GCV, "
                                    f"A {n1}x{n2}x{n3}" + (f", B {s}x{s}x{n3}" if two else "")
                                    + f", X {n2}x{s}x{n3}",
-                       "precision": args.precision,
+                       "precision": args.precision, "product": args.product,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roof,
@@ -643,6 +669,9 @@ def main():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
                     help="slice-GEMM inputs of the main workload (tensor-core forms need "
                          "one-sided plans: video_512 or colour_64)")
+    ap.add_argument("--product", default="th", choices=["th", "orthodct"],
+                    help="c-product reading: Definition 2.1 (th) or Algorithm 1's dct "
+                         "(orthodct; off the fused route LSQR then runs in the transform domain)")
     ap.add_argument("--paper-shaped", action="store_true",
                     help="time the paper's three methods on the shapes of its Tables 1-4")
     ap.add_argument("--cpu-worker", default=None)

@@ -200,6 +200,7 @@ extern "C" int tc_lsqr_label(tc_plan* p, const float* C, const float* X_true, in
   tc_solve_info* info =
       reinterpret_cast<tc_solve_info*>(base + (need - 256 + 0));  // 256-byte slot at the end
   LsqrArgs a{C, X, Xr, kmax, 0.0, 0.0, nullptr, info};
+  a.spatial_basis = 1;  // the labels compare the basis with X_true
   TC_TRY(lsqr_enqueue(p, a, st));
   const size_t L = (size_t)kmax + 2;
   double* alpha = p->dscal;

@@ -143,6 +143,55 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
   return launch_mode3(src, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
 }
 
+// Transform-domain products (ORTHODCT plans off the fused route): the
+// operand and result stay in the transform domain, so a product is the slice
+// GEMMs plus the epilogue pass. The DCT is orthogonal, so Definition 2.2's
+// inner products and norms are the same there, and LSQR can run on the
+// transformed tensors throughout.
+bool td_route(const tc_plan* p) { return p->opts.product == TC_ORTHODCT && !fused(p); }
+
+int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st) {
+  const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  Epi mid;
+  mid.skip = ep.skip;
+  const float* src = p->tmp2;
+  if (lowp(p)) {
+    int* err = ep.red.status ? ep.red.status : p->dev_err;
+    TC_TRY(launch_round(Xt, p->tmp1, (size_t)n2 * s * n3, p->opts.precision == TC_BF16, st,
+                        ep.skip));
+    if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
+    TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
+  } else {
+    TC_TRY(launch_slice_gemm(p->Ah, Xt, p->tmp2, n1, s, n2, n3, nullptr, nullptr, mid, st));
+    if (p->two_sided) {
+      TC_TRY(launch_slice_gemm(p->tmp2, p->Bh, p->tmp1, n1, s, s, n3, nullptr, nullptr, mid, st));
+      src = p->tmp1;
+    }
+  }
+  return launch_epi(src, Yt, p->Ty, ep, st);
+}
+
+int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st) {
+  const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
+  Epi mid;
+  mid.skip = ep.skip;
+  const float* src = p->tmp2;
+  if (lowp(p)) {
+    int* err = ep.red.status ? ep.red.status : p->dev_err;
+    TC_TRY(launch_round(Yt, p->tmp1, (size_t)n1 * s * n3, p->opts.precision == TC_BF16, st,
+                        ep.skip));
+    if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
+    TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
+  } else {
+    TC_TRY(launch_slice_gemm(p->AhT, Yt, p->tmp2, n2, s, n1, n3, nullptr, nullptr, mid, st));
+    if (p->two_sided) {
+      TC_TRY(launch_slice_gemm(p->tmp2, p->BhT, p->tmp1, n2, s, s, n3, nullptr, nullptr, mid, st));
+      src = p->tmp1;
+    }
+  }
+  return launch_epi(src, Xt, p->Tx, ep, st);
+}
+
 // X = M^T [ A~_k^T (M^{-T} Y)_k (B~_k^T) ] with the epilogue `ep` on the last stage.
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st) {
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
@@ -280,7 +329,7 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   float* fs[] = {p->Ah, p->AhT, p->Bh, p->BhT, p->dM, p->dMinv, p->dMinvT, p->dMT,
                  p->tmp1, p->tmp2, p->tmp3, p->lsqr_U, p->lsqr_V, p->lsqr_W, p->basis,
-                 p->gm_basis};
+                 p->gm_basis, p->lsqr_Ct, p->lsqr_Xt};
   for (float* f : fs) dfree(f);
   dfree(p->scratch.partials);
   dfree(p->scratch.tickets);

@@ -42,6 +42,11 @@ int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
     if (cudaMalloc((void**)&p->lsqr_V, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
     if (cudaMalloc((void**)&p->lsqr_W, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
   }
+  if (td_route(p) && !p->lsqr_Ct) {
+    moved = true;
+    if (cudaMalloc((void**)&p->lsqr_Ct, p->Ty * 4) != cudaSuccess) return TC_ENOMEM;
+    if (cudaMalloc((void**)&p->lsqr_Xt, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
+  }
   if (!p->iflags && cudaMalloc((void**)&p->iflags, 16 * sizeof(int)) != cudaSuccess)
     return TC_ENOMEM;
   const size_t L = (size_t)itermax + 2;
@@ -155,15 +160,36 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
 
   TC_CUDA(cudaMemsetAsync(flags, 0, 16 * sizeof(int), st));
   TC_CUDA(cudaMemsetAsync(done, 0, L * sizeof(int), st));
+  // Transform-domain route (ORTHODCT off the fused route): iterate on C~ =
+  // dct(C) and X~ with products of slice GEMMs only; X (and X_reg) are
+  // transformed back once at the end. Norms are unchanged by the orthogonal
+  // transform, so every scalar of the solve is the same.
+  const bool td = td_route(p) && !a.spatial_basis;
+  const float* Cin = a.C;
+  float* Xw = a.X;
+  if (td) {
+    Epi none;
+    TC_TRY(launch_mode3(a.C, p->lsqr_Ct, p->dM, p->n3, p->Ty / p->n3, none, st));
+    Cin = p->lsqr_Ct;
+    Xw = p->lsqr_Xt;
+  }
+  auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
+    if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
+    if (step) TC_TRY(launch_lsqr_update(*step, st));
+    return cprod_td(p, Xv, Yv, ep, st);
+  };
+  auto adj = [&](const float* Yv, float* Xv, const Epi& ep) -> int {
+    return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st);
+  };
   // beta_1 = ||C||_F
-  TC_TRY(launch_reduce(a.C, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
+  TC_TRY(launch_reduce(Cin, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
   // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
   {
     Epi ep;
     ep.coef.rule = COEF_INV;
     ep.coef.s0 = beta;
     ep.red = make_red(p, alpha, 1, nullptr, flags + 2);
-    TC_TRY(adjoint_epi(p, a.C, V, ep, st));
+    TC_TRY(adj(Cin, V, ep));
   }
   // W_1 = V_1 = V~_1 / alpha_1; X_0 = 0
   {
@@ -173,7 +199,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     TC_TRY(launch_scale(V, W, p->Tx, c, nullptr, nullptr, st));
     if (keep) TC_TRY(launch_scale(V, p->basis, p->Tx, c, nullptr, nullptr, st));
   }
-  TC_CUDA(cudaMemsetAsync(a.X, 0, p->Tx * sizeof(float), st));
+  TC_CUDA(cudaMemsetAsync(Xw, 0, p->Tx * sizeof(float), st));
   k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags, done);
   TC_CUDA(cudaGetLastError());
 
@@ -184,7 +210,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   // the loop.
   auto make_step = [&](int j) {
     LsqrStep u;
-    u.X = a.X;
+    u.X = Xw;
     u.W = W;
     u.V = V;
     u.basis_slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
@@ -211,11 +237,11 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.coef.rule = COEF_GK;
       ep.coef.s0 = alpha + j;
       ep.coef.s1 = beta + j;
-      ep.prev = (j == 0) ? a.C : U;
+      ep.prev = (j == 0) ? Cin : U;
       ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
       const LsqrStep prev = j > 0 ? make_step(j - 1) : LsqrStep{};
-      TC_TRY(cprod_epi(p, V, U, ep, st, j > 0 ? &prev : nullptr));
+      TC_TRY(fwd(V, U, ep, j > 0 ? &prev : nullptr));
     }
     // the learned predictor reads the first MLP_FEAT_STEPS steps
     if (a.mlp && j == MLP_FEAT_STEPS)
@@ -229,23 +255,30 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.prev = V;
       ep.red = make_red(p, alpha + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
-      TC_TRY(adjoint_epi(p, U, V, ep, st));
+      TC_TRY(adj(U, V, ep));
     }
   }
   TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));
   if (a.mlp && a.itermax == MLP_FEAT_STEPS)
     TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   const bool gcv_on = keep && !a.lcurve;
+  // the basis combination lands in X_reg, or in a workspace to transform back
+  float* Xr_w = td ? p->tmp2 : a.X_reg;
   if (keep && a.lcurve) {  // X_reg = X_{k_opt} at the L-curve corner (flags[8] = k_opt)
     TC_TRY(launch_lcurve(rgiv, phibar, flags + 1, kp, a.curve, y, flags + 8, st));
-    TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 8, y, p->Tx, nullptr,
+    TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, flags + 8, y, p->Tx, nullptr,
                           st));
   } else if (keep) {
     TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
                              a.mlp ? -1.0 : a.lambda, gwork, lam, y, gcv, st,
                              a.mlp ? lam_pred : nullptr, a.factor, flags + 7));
-    TC_TRY(launch_combine(a.X_reg, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
+    TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
                           st));
+  }
+  if (td) {  // back to the spatial domain: X = idct(X~), X_reg likewise
+    Epi none;
+    TC_TRY(launch_mode3(Xw, a.X, p->dMinv, p->n3, p->Tx / p->n3, none, st));
+    if (keep) TC_TRY(launch_mode3(Xr_w, a.X_reg, p->dMinv, p->n3, p->Tx / p->n3, none, st));
   }
   k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, gcv_on ? lam : nullptr,
                                gcv_on ? gcv : nullptr, (keep && a.lcurve) ? flags + 8 : nullptr);

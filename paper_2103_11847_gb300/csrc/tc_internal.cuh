@@ -105,6 +105,7 @@ struct tc_plan {
   Scratch scratch;
   // solver workspaces (grow-only)
   float* lsqr_U = nullptr; float* lsqr_V = nullptr; float* lsqr_W = nullptr;
+  float* lsqr_Ct = nullptr; float* lsqr_Xt = nullptr;  // transform-domain route: C~ and X~
   float* basis = nullptr; size_t basis_elems = 0;
   double* dscal = nullptr; size_t dscal_elems = 0;
   int* iflags = nullptr;
@@ -173,9 +174,12 @@ int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t
 int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                       int bf16, const int* skip, cudaStream_t st);
 // Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
-int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st);
+int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
+                 const int* skip = nullptr);
 // vec.cu
 int vec_init();  // shared-memory carveout preference of the vector passes
+// out = ca * in + cp * prev and the fused reduction (the Krylov epilogue as a pass)
+int launch_epi(const float* in, float* out, size_t n, const Epi& ep, cudaStream_t st);
 int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
                   const int* skip, cudaStream_t st);
 int launch_scale(const float* in, float* out, size_t n, const Coef& c, const float* prev,
@@ -216,6 +220,11 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
               const LsqrStep* step = nullptr);
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st);
 Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
+// Transform-domain products (ORTHODCT plans off the fused route; td_route):
+// operand and result are transformed tensors, the epilogue applies to them.
+bool td_route(const tc_plan* p);
+int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st);
+int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st);
 int tc_kernels_init();
 
 // solvers.cu: the c-LSQR solve as a sequence of launches on one stream
@@ -231,6 +240,7 @@ struct LsqrArgs {
   const tc_mlp* mlp = nullptr;  // learned stop index and lambda (learned.cu)
   double factor = 1.05;         // GCV fallback threshold for the learned lambda
   int lcurve = 0;               // X_reg = X_{k_opt} at the L-curve corner, no GCV
+  int spatial_basis = 0;        // keep the basis in the spatial domain (no transform-domain route)
   double* curve = nullptr;      // L-curve norms (2 itermax doubles) or null
 };
 // learned.cu: after MLP_FEAT_STEPS steps, features -> network -> lam_pred and

@@ -196,9 +196,44 @@ int pick(const float* in, void* out, const float* T, int n3, size_t P, const Epi
   return run<8, OUT>(in, out, T, n3, P, ep, st);
 }
 
-__global__ void k_round(const float* __restrict__ in, void* out, size_t n, int kind) {
+// Elementwise rounding to the GEMM input type; four elements per thread and
+// iteration when in is 16-byte aligned (the output then is 8- or 16-byte
+// aligned too), with four such groups of loads in flight.
+__global__ void k_round(const float* __restrict__ in, void* out, size_t n, int kind,
+                        const int* skip) {
+  if (skip && *skip) return;
   const size_t st = (size_t)gridDim.x * blockDim.x;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += st) {
+  const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t done = 0;
+  if ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+    const size_t n4 = n / 4;
+    for (size_t i0 = gt; i0 < n4; i0 += 4 * st) {
+      float4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t i = i0 + u * st;
+        v[u] = i < n4 ? reinterpret_cast<const float4*>(in)[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const size_t i = i0 + u * st;
+        if (i >= n4) break;
+        if (kind == OUT_BF16) {
+          __nv_bfloat162 lo = __floats2bfloat162_rn(v[u].x, v[u].y);
+          __nv_bfloat162 hi = __floats2bfloat162_rn(v[u].z, v[u].w);
+          uint2 pk;
+          pk.x = *reinterpret_cast<uint32_t*>(&lo);
+          pk.y = *reinterpret_cast<uint32_t*>(&hi);
+          reinterpret_cast<uint2*>(out)[i] = pk;
+        } else {
+          reinterpret_cast<float4*>(out)[i] = make_float4(round_tf32(v[u].x), round_tf32(v[u].y),
+                                                          round_tf32(v[u].z), round_tf32(v[u].w));
+        }
+      }
+    }
+    done = 4 * n4;
+  }
+  for (size_t i = done + gt; i < n; i += st) {
     if (kind == OUT_BF16)
       static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(in[i]);
     else
@@ -223,8 +258,9 @@ int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, si
               : pick<OUT_TF32>(in, out, T_dev, n3, P, ep, st);
 }
 
-int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st) {
-  k_round<<<152 * 8, 256, 0, st>>>(in, out, n, bf16 ? OUT_BF16 : OUT_TF32);
+int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
+                 const int* skip) {
+  k_round<<<152 * 8, 256, 0, st>>>(in, out, n, bf16 ? OUT_BF16 : OUT_TF32, skip);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

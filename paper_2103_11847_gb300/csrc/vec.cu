@@ -127,6 +127,66 @@ k_combine(float* X, const float* X0, const float* __restrict__ basis, size_t str
   }
 }
 
+// The Krylov epilogue as its own pass: out = ca * in + cp * prev (prev may
+// alias out), then the fused reduction of out. Used by the transform-domain
+// products, whose slice GEMMs store plainly. Each thread keeps UNR float4
+// loads of every operand in flight; one element is read and written by one
+// thread only, so prev aliasing out is safe.
+constexpr int UNR = 4;
+__global__ void __launch_bounds__(NT)
+k_epi(const float* __restrict__ in, float* out, size_t n, Epi ep, int vec) {
+  if (ep.skip && *ep.skip) return;
+  __shared__ float sh[2];
+  coef_compute(ep.coef, sh);
+  __syncthreads();
+  const float ca = sh[0], cp = sh[1];
+  float local = 0.f;
+  const size_t gt = (size_t)blockIdx.x * NT + threadIdx.x;
+  const size_t stride = (size_t)gridDim.x * NT;
+  size_t done = 0;
+  if (vec) {
+    const size_t n4 = n / 4;
+    const float4* in4 = reinterpret_cast<const float4*>(in);
+    const float4* pv4 = reinterpret_cast<const float4*>(ep.prev);
+    const float4* ot4 = reinterpret_cast<const float4*>(ep.red.other);
+    float4* out4 = reinterpret_cast<float4*>(out);
+    for (size_t i0 = gt; i0 < n4; i0 += UNR * stride) {
+      float4 v[UNR], pv[UNR], ov[UNR];
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const size_t i = i0 + u * stride;
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        v[u] = i < n4 ? in4[i] : z;
+        pv[u] = (ep.prev && i < n4) ? pv4[i] : z;
+        ov[u] = (ep.red.other && i < n4) ? ot4[i] : z;
+      }
+#pragma unroll
+      for (int u = 0; u < UNR; ++u) {
+        const size_t i = i0 + u * stride;
+        if (i >= n4) break;
+        float4 o = make_float4(ca * v[u].x, ca * v[u].y, ca * v[u].z, ca * v[u].w);
+        if (ep.prev) {
+          o.x = fmaf(cp, pv[u].x, o.x); o.y = fmaf(cp, pv[u].y, o.y);
+          o.z = fmaf(cp, pv[u].z, o.z); o.w = fmaf(cp, pv[u].w, o.w);
+        }
+        out4[i] = o;
+        if (ep.red.out) {
+          const float4 q = ep.red.other ? ov[u] : o;
+          local = fmaf(o.x, q.x, fmaf(o.y, q.y, fmaf(o.z, q.z, fmaf(o.w, q.w, local))));
+        }
+      }
+    }
+    done = 4 * n4;
+  }
+  for (size_t i = done + gt; i < n; i += stride) {
+    float o = ca * in[i];
+    if (ep.prev) o = fmaf(cp, ep.prev[i], o);
+    out[i] = o;
+    if (ep.red.out) local = fmaf(o, ep.red.other ? ep.red.other[i] : o, local);
+  }
+  if (ep.red.out) reduce_finish(local, ep.red);
+}
+
 // Algorithm 2 step 3(b): W -= h V_i, then <V_next, W> (or ||W||^2) for the next step.
 __global__ void __launch_bounds__(NT)
 k_mgs_pass(float* W, const float* __restrict__ Vi, const double* h, const float* Vnext,
@@ -159,6 +219,16 @@ int vec_init() {
   TC_CUDA(cudaFuncSetAttribute(k_combine<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_combine<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_mgs_pass, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_epi, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  return TC_OK;
+}
+
+int launch_epi(const float* in, float* out, size_t n, const Epi& ep, cudaStream_t st) {
+  auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const int vec = al(in) && al(out) && (!ep.prev || al(ep.prev)) &&
+                  (!ep.red.other || al(ep.red.other));
+  k_epi<<<grid_for(n, 4 * UNR), NT, 0, st>>>(in, out, n, ep, vec);
+  TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 

@@ -98,3 +98,55 @@ def test_orthodct_lsqr_matches_oracle(tc, two):
     assert tc.read_info(info)["iters"] == ref["iters"]
     assert rel(X.cpu().numpy(), ref["X"]) < 1e-3
     plan.close()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+def test_transform_domain_lsqr(tc, precision):
+    # ORTHODCT plans off the fused route (n3 > 4, or a tensor-core form)
+    # iterate on dct(C) with slice GEMMs only and transform X, X_reg back at
+    # the end (reading R21). FP32: the iterate to 1e-3 of the oracle's at 15
+    # steps; every form: the regularised reconstruction error within 1% (FP32)
+    # or 2% (TF32/BF16) of the oracle's.
+    w = inputs.video_deblur(n=64, frames=9, seed=4)
+    A = f32(w["A"]).astype(np.float64)
+    op = lambda X: cp.cprod_orthodct(A, X)
+    adj = lambda Y: cp.cprod_adjoint_orthodct(A, Y)
+    Xt = w["X_true"]
+    C = f32(inputs.scale_noise(op(Xt), w["G"], 1e-2)).astype(np.float64)
+    ref = kr.lsqr_gcv(op, adj, C, itermax=15)
+    prec = {"fp32": tc.TC_FP32, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16}[precision]
+    plan = tc.Plan(dev(A), s=64, precision=prec, product=tc.TC_ORTHODCT)
+    for _ in range(2):  # the second call replays the captured graph
+        X, Xr, _, info = plan.lsqr(dev(C), 15, regularize=True)
+        torch.cuda.synchronize()
+        assert tc.read_info(info)["iters"] == 15
+        e_ref = rel(ref["X_reg"], Xt)
+        e_gpu = rel(Xr.cpu().numpy(), Xt)
+        if precision == "fp32":
+            assert rel(X.cpu().numpy(), ref["X"]) < 1e-3
+            assert abs(e_gpu - e_ref) <= 0.01 * e_ref
+        else:
+            assert abs(e_gpu - e_ref) <= 0.02 * e_ref
+    plan.close()
+
+
+def test_transform_domain_lcurve(tc):
+    from oracle import lcurve as lc
+    w = inputs.video_deblur(n=48, frames=6, seed=5)
+    A = f32(w["A"]).astype(np.float64)
+    op = lambda X: cp.cprod_orthodct(A, X)
+    adj = lambda Y: cp.cprod_adjoint_orthodct(A, Y)
+    C = f32(inputs.scale_noise(op(w["X_true"]), w["G"], 1e-2)).astype(np.float64)
+    ref = lc.lsqr_lcurve(op, adj, C, 12)
+    plan = tc.Plan(dev(A), s=48, product=tc.TC_ORTHODCT)
+    X, Xo, curve, info = plan.lsqr_lcurve(dev(C), 12)
+    torch.cuda.synchronize()
+    inf = tc.read_info(info)
+    cv = curve.cpu().numpy()
+    assert np.max(np.abs(cv[:12] - ref["resnorm"]) / ref["resnorm"]) < 1e-4
+    assert np.max(np.abs(cv[12:] - ref["solnorm"]) / ref["solnorm"]) < 1e-4
+    k = inf["kopt"]
+    kap = ref["curvature"]
+    assert k == ref["kopt"] or kap[k - 1] >= np.nanmax(kap) * (1 - 1e-3)
+    assert rel(Xo.cpu().numpy(), ref["Xs"][k - 1]) < 1e-3
+    plan.close()
