@@ -171,6 +171,19 @@ int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t
   return launch_epi(src, Yt, p->Ty, ep, st);
 }
 
+// BF16 transform-domain products with the epilogue in the GEMM store (plans
+// with umf_td): the forward GEMM reads bf16(V~) from lowV and writes U~ and
+// bf16(U~) to lowU; the adjoint reads lowU and writes V~ and lowV.
+int cprod_tdf(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st) {
+  int* err = ep.red.status ? ep.red.status : p->dev_err;
+  return launch_umma_epi(*p->umf_td, Yt, static_cast<__nv_bfloat16*>(p->lowU), ep, err, st);
+}
+
+int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st) {
+  int* err = ep.red.status ? ep.red.status : p->dev_err;
+  return launch_umma_epi(*p->uma_td, Xt, static_cast<__nv_bfloat16*>(p->lowV), ep, err, st);
+}
+
 int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st) {
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
   Epi mid;
@@ -312,6 +325,17 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
     const void* bop = bf16 ? (const void*)p->tmp1 : (const void*)p->tmp3;
     TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3));
     TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3));
+    if (bf16 && p->opts.product == TC_ORTHODCT) {
+      // transform-domain LSQR with the epilogue in the GEMM: each product's
+      // store also writes the BF16 operand of the next one, so the forward and
+      // adjoint GEMMs read separate buffers (bV: V~, n2 x s; bU: U~, n1 x s)
+      TC_CUDA(cudaMalloc(&p->lowV, (size_t)n2 * s * n3 * 2));
+      TC_CUDA(cudaMalloc(&p->lowU, (size_t)n1 * s * n3 * 2));
+      p->umf_td = new UmmaMaps();
+      p->uma_td = new UmmaMaps();
+      TC_TRY(make_umma_maps(p->umf_td, 0, p->AhL, p->lowV, n1, s, n2, n3));
+      TC_TRY(make_umma_maps(p->uma_td, 0, p->AhTL, p->lowU, n2, s, n1, n3));
+    }
   }
   TC_TRY(dalloc(&p->scratch.partials, np));
   TC_TRY(dalloc(&p->scratch.tickets, 16));
@@ -344,6 +368,10 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   dfree(p->AhTL);
   delete p->umf;
   delete p->uma;
+  delete p->umf_td;
+  delete p->uma_td;
+  dfree(p->lowV);
+  dfree(p->lowU);
   delete p;
   return TC_OK;
 }

@@ -173,12 +173,17 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     Cin = p->lsqr_Ct;
     Xw = p->lsqr_Xt;
   }
+  // BF16 plans with fused epilogues keep the GEMM operands as BF16 copies that
+  // each product's store writes for the next one; the first is bf16(C~).
+  const bool tdf = td && p->umf_td != nullptr;
+  if (tdf) TC_TRY(launch_round(Cin, p->lowU, p->Ty, 1, st));
   auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
     if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
     if (step) TC_TRY(launch_lsqr_update(*step, st));
-    return cprod_td(p, Xv, Yv, ep, st);
+    return tdf ? cprod_tdf(p, Yv, ep, st) : cprod_td(p, Xv, Yv, ep, st);
   };
   auto adj = [&](const float* Yv, float* Xv, const Epi& ep) -> int {
+    if (tdf) return adjoint_tdf(p, Xv, ep, st);
     return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st);
   };
   // beta_1 = ||C||_F

@@ -118,6 +118,10 @@ struct tc_plan {
   void* AhTL = nullptr;           // its slice transposes
   UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
   UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
+  void* lowV = nullptr;           // BF16 ORTHODCT plans: bf16(V~) and bf16(U~), the operands
+  void* lowU = nullptr;           // of the transform-domain GEMMs with fused epilogues
+  UmmaMaps* umf_td = nullptr;     // A~ times lowV
+  UmmaMaps* uma_td = nullptr;     // A~^T times lowU
   int* dev_err = nullptr;         // set by a tensor-core GEMM whose bounded wait gave up
   void* aux = nullptr;            // tc_lsqr_label workspace (grow-only)
   size_t aux_bytes = 0;
@@ -225,6 +229,10 @@ Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* sta
 bool td_route(const tc_plan* p);
 int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st);
 int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st);
+// With a fused-epilogue BF16 plan (umf_td set): operands from lowV / lowU,
+// and each product writes the other's operand (see plan.cu).
+int cprod_tdf(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st);
+int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st);
 int tc_kernels_init();
 
 // solvers.cu: the c-LSQR solve as a sequence of launches on one stream

@@ -126,10 +126,15 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 
 // KIND 0: BF16 inputs (kind::f16), KIND 1: TF32 inputs (kind::tf32).
 // BKMAJ: B given as N x K per slice (K contiguous) instead of K x N.
-template <int KIND, int BKMAJ>
+// EPI: the Krylov epilogue in the store: D = ca * acc + cp * prev (prev may
+// alias D; each element is read and written by one thread), an optional BF16
+// copy of D into dlow (the next GEMM's operand), and the fused reduction of D.
+// Without EPI the accumulator is stored as is.
+template <int KIND, int BKMAJ, bool EPI>
 __global__ void __launch_bounds__(NT, 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            float* __restrict__ D, int M, int N, int K, int* err, const int* skip) {
+            float* D, int M, int N, int K, int* err, const int* skip, Epi ep,
+            __nv_bfloat16* dlow) {
   constexpr int ES = KIND == 0 ? 2 : 4;       // bytes per element
   constexpr int BKE = 128 / ES;               // K elements per stage
   constexpr int UK = KIND == 0 ? 16 : 8;      // K per MMA instruction
@@ -151,6 +156,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   uint64_t* done = empty + STAGES;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ int sh_fail;
+  __shared__ float sh_coef[2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
@@ -165,6 +171,27 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh_fail = 0;
   }
+  if (EPI && threadIdx.x == 64) {  // warp 2 is idle until the epilogue
+    double ca = 1.0, cp = 0.0;
+    const Coef& c = ep.coef;
+    if (c.rule == COEF_GK) {
+      const double s0 = *c.s0, s1 = *c.s1;
+      ca = (s0 != 0.0) ? 1.0 / s0 : 0.0;
+      cp = (s1 != 0.0) ? -s0 / s1 : 0.0;
+    } else if (c.rule == COEF_INV) {
+      const double s0 = *c.s0;
+      ca = (s0 != 0.0) ? 1.0 / s0 : 0.0;
+    } else if (c.rule == COEF_RESID) {
+      ca = -1.0;
+      cp = 1.0;
+    } else if (c.rule == COEF_NEG) {
+      ca = -1.0;
+    } else if (c.rule == COEF_AXPY) {
+      cp = -*c.s0;
+    }
+    sh_coef[0] = (float)ca;
+    sh_coef[1] = (float)cp;
+  }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tslot)),
@@ -177,6 +204,21 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
   int issued = 0;  // stages the producer armed (for the bounded drain on failure)
+  // EPI: prev does not depend on the GEMM, so every thread loads its row's
+  // BN values of prev now and the loads overlap the main loop (whole 32-column
+  // chunks with N % 4 == 0; the edge chunks read prev in the epilogue).
+  float4 pre[EPI ? BN / 4 : 1];
+  if (EPI) {
+    const int prow = m0 + warp * 32 + lane;
+#pragma unroll
+    for (int q = 0; q < BN / 4; ++q) {
+      const int col = n0 + 4 * q;
+      const bool whole = ep.prev && prow < M && (N & 3) == 0 && n0 + (q / 8) * 32 + 32 <= N;
+      pre[q] = whole ? *reinterpret_cast<const float4*>(ep.prev + (size_t)z * M * N +
+                                                         (size_t)prow * N + col)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+  }
 
   if (warp == 0 && lane == 0) {
     for (int kb = 0; kb < nk; ++kb) {
@@ -221,16 +263,81 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncwarp();
   const bool ok = mbar_wait(done, 0) && !sh_fail;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  float local = 0.f;  // EPI: this thread's share of the reduction
   if (ok) {
     const int row = m0 + warp * 32 + lane;
-#pragma unroll 1
+#pragma unroll
     for (int c = 0; c < BN / 32; ++c) {
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, v);
       const int col0 = n0 + c * 32;
       if (row < M) {
-        float* dst = D + (size_t)z * M * N + (size_t)row * N + col0;
-        if (col0 + 32 <= N && (N & 3) == 0) {
+        const size_t o = (size_t)z * M * N + (size_t)row * N + col0;
+        float* dst = D + o;
+        if (EPI) {
+          const float ca = sh_coef[0], cp = sh_coef[1];
+          const bool vec = col0 + 32 <= N && (N & 3) == 0;
+          if (vec) {  // this thread's 32 contiguous values of prev, loaded above
+            if (ep.prev) {
+              float4 pv[8];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) pv[q] = pre[8 * c + q];
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                v[4 * q] = fmaf(cp, pv[q].x, ca * v[4 * q]);
+                v[4 * q + 1] = fmaf(cp, pv[q].y, ca * v[4 * q + 1]);
+                v[4 * q + 2] = fmaf(cp, pv[q].z, ca * v[4 * q + 2]);
+                v[4 * q + 3] = fmaf(cp, pv[q].w, ca * v[4 * q + 3]);
+              }
+            } else {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) v[j] *= ca;
+            }
+          } else {
+            for (int j = 0; j < 32 && col0 + j < N; ++j) {
+              float y = ca * v[j];
+              if (ep.prev) y = fmaf(cp, ep.prev[o + j], y);
+              v[j] = y;
+            }
+          }
+          if (vec) {
+#pragma unroll
+            for (int j = 0; j < 32; j += 4)
+              *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            if (dlow) {
+#pragma unroll
+              for (int j = 0; j < 32; j += 4) {
+                __nv_bfloat162 lo = __floats2bfloat162_rn(v[j], v[j + 1]);
+                __nv_bfloat162 hi = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
+                uint2 pk;
+                pk.x = *reinterpret_cast<uint32_t*>(&lo);
+                pk.y = *reinterpret_cast<uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(dlow + o + j) = pk;
+              }
+            }
+          } else {
+            for (int j = 0; j < 32 && col0 + j < N; ++j) {
+              dst[j] = v[j];
+              if (dlow) dlow[o + j] = __float2bfloat16_rn(v[j]);
+            }
+          }
+          if (ep.red.out) {
+            if (vec && ep.red.other) {
+#pragma unroll
+              for (int q = 0; q < 8; ++q) {
+                const float4 ov = *reinterpret_cast<const float4*>(ep.red.other + o + 4 * q);
+                local = fmaf(v[4 * q], ov.x, fmaf(v[4 * q + 1], ov.y,
+                        fmaf(v[4 * q + 2], ov.z, fmaf(v[4 * q + 3], ov.w, local))));
+              }
+            } else if (vec) {
+#pragma unroll
+              for (int j = 0; j < 32; ++j) local = fmaf(v[j], v[j], local);
+            } else {
+              for (int j = 0; j < 32 && col0 + j < N; ++j)
+                local = fmaf(v[j], ep.red.other ? ep.red.other[o + j] : v[j], local);
+            }
+          }
+        } else if (col0 + 32 <= N && (N & 3) == 0) {
 #pragma unroll
           for (int j = 0; j < 32; j += 4)
             *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
@@ -246,6 +353,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
     for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
       mbar_wait(full + kb % STAGES, (kb / STAGES) & 1);
   }
+  if (EPI && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1)
@@ -260,10 +368,12 @@ PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 }  // namespace
 
 int umma_init() {
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes()));
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<1, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem_bytes()));
+  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<1, 1, false>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -315,10 +425,23 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
 
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
   dim3 grid((m.N + BN - 1) / BN, (m.M + BM - 1) / BM, m.slices);
+  Epi none;
   if (m.kind == 0)
-    k_umma_gemm<0, 0><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
+    k_umma_gemm<0, 0, false><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
+                                                              skip, none, nullptr);
   else
-    k_umma_gemm<1, 1><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err, skip);
+    k_umma_gemm<1, 1, false><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
+                                                              skip, none, nullptr);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
+                    cudaStream_t st) {
+  TC_CHECK(m.kind == 0);
+  dim3 grid((m.N + BN - 1) / BN, (m.M + BM - 1) / BM, m.slices);
+  k_umma_gemm<0, 0, true><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
+                                                           ep.skip, ep, dlow);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

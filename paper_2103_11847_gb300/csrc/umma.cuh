@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include "tc_internal.cuh"
 
@@ -17,3 +18,8 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
 // D_z = A_z B_z in FP32 for every slice; *err is set to TC_ETIMEOUT if a
 // bounded wait gives up.
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st);
+// BF16 maps only: the same GEMM with the Krylov epilogue in its store
+// (D = ca * acc + cp * ep.prev, the reduction ep.red of D, ep.skip) and, when
+// dlow is non-null, a BF16 copy of D written beside it.
+int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
+                    cudaStream_t st);
