@@ -294,5 +294,6 @@ int tc_kernels_init() {
                                200 * 1024));
   TC_TRY(cprod2_init());
   TC_TRY(vec_init());
+  TC_TRY(transform_init());
   return TC_OK;
 }

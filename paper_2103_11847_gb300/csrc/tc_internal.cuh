@@ -178,6 +178,7 @@ int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t
 int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                       int bf16, const int* skip, cudaStream_t st);
 // Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
+int transform_init();  // shared-memory limits of the transform passes
 int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
                  const int* skip = nullptr);
 // vec.cu

@@ -4,9 +4,10 @@
 // 128 consecutive pixels p of every slice: warp w computes the KPW contiguous
 // outputs k = w*KPW .. w*KPW + KPW - 1 (coefficients read as float4
 // broadcasts) and lane q the pixels 4q..4q+3. T is staged in shared memory
-// once; inputs stream through two shared-memory stages of 16 slices, filled
-// with cp.async while the other stage is consumed. HBM traffic is one read of
-// `in` (and `prev`) and one write of `out`.
+// once. The CTA's whole input block (every slice of its 128 pixels, 32 KB at
+// n3 = 64) is requested at once with cp.async in groups of 16 slices, and
+// each group is consumed as it lands, so a CTA keeps its whole input in
+// flight. HBM traffic is one read of `in` (and `prev`) and one write of `out`.
 #include <cuda_bf16.h>
 
 #include "tc_device.cuh"
@@ -25,7 +26,7 @@ __device__ __forceinline__ float round_tf32(float x) {
 }
 
 constexpr int PB = 128;  // pixels per CTA
-constexpr int LC = 16;   // input slices per shared-memory stage (double-buffered)
+constexpr int LC = 16;   // input slices per cp.async group
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool valid) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -34,15 +35,29 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem, bool va
                : "memory");
 }
 
+// Dynamic shared memory of k_mode3<KPW, .>: T^T (8 KPW x 8 KPW) and the whole
+// input block (8 KPW slices x PB pixels).
+template <int KPW>
+constexpr size_t mode3_smem() { return (size_t)(8 * KPW) * (8 * KPW + PB) * sizeof(float); }
+
+__device__ __forceinline__ void cp_wait_upto(int n) {  // at most n groups pending
+  if (n <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+  else if (n == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+  else if (n == 2) asm volatile("cp.async.wait_group 2;" ::: "memory");
+  else asm volatile("cp.async.wait_group 3;" ::: "memory");
+}
+
 template <int KPW, int OUT>
 __global__ void __launch_bounds__(256, 3)
 k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, int n3,
         size_t P, Epi ep) {
   if (ep.skip && *ep.skip) return;
-  // ts: T transposed (ts[l][k] = T[k][l]) for all l, loaded once;
-  // xs: two stages of LC input slices x PB pixels
-  __shared__ __align__(16) float ts[8 * KPW][8 * KPW];  // <= 16 KB (n3 <= 64)
-  __shared__ __align__(16) float xs[2][LC][PB];
+  // ts: T transposed (ts[l][k] = T[k][l]), loaded once; xs: the CTA's whole
+  // input block, every slice of its PB pixels, requested at once in groups of
+  // LC slices so that all of it is in flight while the first groups compute
+  extern __shared__ __align__(16) float m3_smem[];
+  float(*ts)[8 * KPW] = reinterpret_cast<float(*)[8 * KPW]>(m3_smem);
+  float(*xs)[PB] = reinterpret_cast<float(*)[PB]>(m3_smem + (8 * KPW) * (8 * KPW));
   __shared__ float sh_coef[2];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const size_t p0 = (size_t)blockIdx.x * PB;
@@ -56,43 +71,37 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
 #pragma unroll
     for (int e = 0; e < 4; ++e) acc[q][e] = 0.f;
 
-  for (int idx = tid; idx < n3 * 8 * KPW; idx += 256) {
-    const int l = idx / (8 * KPW), k = idx % (8 * KPW);
-    ts[l][k] = (k < n3) ? __ldg(T + (size_t)k * n3 + l) : 0.f;
-  }
-  const int nch = (n3 + LC - 1) / LC;
-  auto stage = [&](int c) {
+  const int nch = (n3 + LC - 1) / LC;  // <= 4 (n3 <= 64)
+  for (int c = 0; c < nch; ++c) {
     const int l0 = c * LC, lc_n = min(LC, n3 - l0);
-    float(*xb)[PB] = xs[c & 1];
     if (vec) {
       for (int idx = tid; idx < LC * PB / 4; idx += 256) {
         const int lc = idx / (PB / 4), px = (idx % (PB / 4)) * 4;
         const size_t p = p0 + px;
-        const bool ok = lc < lc_n && p < P;
-        cp_async16(&xb[lc][px], ok ? in + (size_t)(l0 + lc) * P + p : in, ok);
+        if (lc < lc_n) {
+          const bool ok = p < P;
+          cp_async16(&xs[l0 + lc][px], ok ? in + (size_t)(l0 + lc) * P + p : in, ok);
+        }
       }
     } else {
       for (int idx = tid; idx < LC * PB; idx += 256) {
         const int lc = idx / PB, px = idx % PB;
         const size_t p = p0 + px;
-        xb[lc][px] = (lc < lc_n && p < P) ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
+        if (lc < lc_n) xs[l0 + lc][px] = p < P ? __ldg(in + (size_t)(l0 + lc) * P + p) : 0.f;
       }
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
-  };
-  stage(0);
+  }
+  for (int idx = tid; idx < n3 * 8 * KPW; idx += 256) {
+    const int l = idx / (8 * KPW), k = idx % (8 * KPW);
+    ts[l][k] = (k < n3) ? __ldg(T + (size_t)k * n3 + l) : 0.f;
+  }
   for (int c = 0; c < nch; ++c) {
-    if (c + 1 < nch) {
-      stage(c + 1);
-      asm volatile("cp.async.wait_group 1;" ::: "memory");
-    } else {
-      asm volatile("cp.async.wait_group 0;" ::: "memory");
-    }
-    __syncthreads();
+    cp_wait_upto(nch - 1 - c);  // this thread's copies of group c have landed
+    __syncthreads();            // everyone's, and T
     const int l0 = c * LC, lc_n = min(LC, n3 - l0);
-    float(*xb)[PB] = xs[c & 1];
     for (int lc = 0; lc < lc_n; ++lc) {
-      const float4 x = *reinterpret_cast<const float4*>(&xb[lc][lane * 4]);
+      const float4 x = *reinterpret_cast<const float4*>(&xs[l0 + lc][lane * 4]);
       float t[KPW];  // warp w owns the contiguous outputs k = w*KPW .. w*KPW + KPW - 1
       if (KPW % 4 == 0) {
 #pragma unroll
@@ -112,7 +121,6 @@ k_mode3(const float* __restrict__ in, void* out_v, const float* __restrict__ T, 
         acc[q][3] = fmaf(t[q], x.w, acc[q][3]);
       }
     }
-    __syncthreads();  // the stage about to be refilled is no longer read
   }
 
   if (OUT != OUT_F32) {  // operand of a tensor-core GEMM: store only
@@ -182,7 +190,7 @@ template <int KPW, int OUT>
 int run(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
         cudaStream_t st) {
   const size_t blocks = (P + PB - 1) / PB;
-  k_mode3<KPW, OUT><<<(unsigned)blocks, 256, 0, st>>>(in, out, T, n3, P, ep);
+  k_mode3<KPW, OUT><<<(unsigned)blocks, 256, mode3_smem<KPW>(), st>>>(in, out, T, n3, P, ep);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -256,6 +264,24 @@ int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, si
   ep.skip = skip;
   return bf16 ? pick<OUT_BF16>(in, out, T_dev, n3, P, ep, st)
               : pick<OUT_TF32>(in, out, T_dev, n3, P, ep, st);
+}
+
+namespace {
+template <int KPW>
+int init_kpw() {
+  for (auto fn : {k_mode3<KPW, OUT_F32>, k_mode3<KPW, OUT_BF16>, k_mode3<KPW, OUT_TF32>})
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)mode3_smem<KPW>()));
+  return TC_OK;
+}
+}  // namespace
+
+int transform_init() {
+  TC_TRY(init_kpw<1>());
+  TC_TRY(init_kpw<2>());
+  TC_TRY(init_kpw<4>());
+  TC_TRY(init_kpw<8>());
+  return TC_OK;
 }
 
 int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
