@@ -294,18 +294,23 @@ def batched_form(dev, iters=40, count=128, steps=2):
     out = {"workload": f"{count} problems n x n x 3, n in {{64..512}} (sum n^2 = "
                        f"{sum(n * n for n in sizes)}), c-LSQR {iters} it + Tikhonov/GCV",
            "launch": "one CUDA graph of per-problem child graphs"}
-    C_dev = None
+    C_by_product = {}
     st = torch.cuda.current_stream()
-    for name, code in (("fp32", tcprod.TC_FP32), ("bf16", tcprod.TC_BF16)):
-        h = tcprod.tc_batch_create(As, sizes, precision=code)
-        if C_dev is None:  # observations C = A *c X + N, formed by the library
+    forms = (("fp32", tcprod.TC_FP32, tcprod.TC_TH), ("bf16", tcprod.TC_BF16, tcprod.TC_TH),
+             ("fp32_orthodct", tcprod.TC_FP32, tcprod.TC_ORTHODCT),
+             ("bf16_orthodct", tcprod.TC_BF16, tcprod.TC_ORTHODCT))
+    for name, code, product in forms:
+        h = tcprod.tc_batch_create(As, sizes, precision=code, product=product)
+        if product not in C_by_product:  # C = A *c X + N, formed by the library's product
             C_dev = []
             for i, (w, A) in enumerate(Cs):
-                p = tcprod.Plan(A, s=sizes[i])
+                p = tcprod.Plan(A, s=sizes[i], product=product)
                 Cc = p.cprod(Xt[i])
                 G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
                 C_dev.append((Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous())
                 p.close()
+            C_by_product[product] = C_dev
+        C_dev = C_by_product[product]
         Xs = [torch.empty_like(c) for c in C_dev]
         Xr = [torch.empty_like(c) for c in C_dev]
         infos = tcprod.new_infos(count)
@@ -325,6 +330,12 @@ def batched_form(dev, iters=40, count=128, steps=2):
         tcprod.tc_batch_destroy(h)
     base = out["fp32"]["mean_rel_err_reg"]
     out["bf16"]["matched_error"] = bool(abs(out["bf16"]["mean_rel_err_reg"] - base) <= 0.02 * base)
+    # ORTHODCT is a different product (Algorithm 1's dct): matched against its own FP32
+    bo = out["fp32_orthodct"]["mean_rel_err_reg"]
+    out["bf16_orthodct"]["matched_error"] = bool(
+        abs(out["bf16_orthodct"]["mean_rel_err_reg"] - bo) <= 0.02 * bo)
+    out["bf16_orthodct"]["note"] = ("Algorithm 1's dct product; transform-domain iteration, "
+                                    "epilogue in the tcgen05 GEMM")
     return out
 
 

@@ -229,14 +229,15 @@ def _ptr_array(ts, name):
     return arr
 
 
-def tc_batch_create(As, ss, precision=TC_FP32, gcv_variant=TC_GCV_PAPER, stream=None):
+def tc_batch_create(As, ss, precision=TC_FP32, gcv_variant=TC_GCV_PAPER, stream=None,
+                    product=TC_TH):
     """As: list of (n3, n1_i, n2_i) CUDA tensors; ss: list of column counts."""
     n = len(As)
     n3 = As[0].shape[0]
     n1 = (c_int * n)(*[a.shape[1] for a in As])
     n2 = (c_int * n)(*[a.shape[2] for a in As])
     sv = (c_int * n)(*ss)
-    o = tc_opts(precision, gcv_variant, 1)
+    o = tc_opts(precision, gcv_variant, 1, product)
     h = c_void_p()
     _check("tc_batch_create", lib().tc_batch_create(ctypes.byref(h), n, n1, n2, sv, n3,
                                                     _ptr_array(As, "A"), ctypes.byref(o),
