@@ -1,22 +1,29 @@
 // Frontal-slice GEMMs on the 5th-generation tensor cores (tcgen05), for the
 // TF32 and BF16 precision forms of the c-product (Algorithm 1, step 2):
 //   D_z = A_z B_z,  A_z: M x K (K contiguous), B_z: K x N (N contiguous),
-//   D_z: M x N FP32, for every slice z of the grid.
+//   D_z: M x N FP32, for every slice z.
 //
-// One CTA computes a 128 x 128 tile of one slice with a 128-lane x 128-column
-// FP32 accumulator in tensor memory:
-//   warp 0, one lane : TMA producer (cp.async.bulk.tensor.3d, 128B swizzle),
+// A persistent kernel, two CTAs per SM, each looping over 128 x 128 output
+// tiles (tile t, t + gridDim.x, ...; columns fastest, then rows, then slices).
+// The FP32 accumulator is double-buffered in tensor memory (2 x 128 columns
+// a CTA, the SM's 512 between two CTAs), so the store of one tile overlaps
+// the MMAs of the next:
+//   warp 0, one lane : TMA producer (cp.async.bulk.tensor.3d, 128B swizzle)
+//                      over every (tile, K block) of the CTA, into a
 //                      STAGES-deep ring of (A, B) stages in shared memory;
-//   warp 1, one lane : issues tcgen05.mma (kind::f16 with BF16 inputs, or
-//                      kind::tf32) and tcgen05.commit to release each stage;
-//   all four warps   : epilogue, tcgen05.ld of 32 lanes x 32 columns at a time.
+//   warp 1, one lane : tcgen05.mma (kind::f16 with BF16 inputs, or
+//                      kind::tf32) into accumulator buffer (i & 1) of the
+//                      CTA's i-th tile; tcgen05.commit releases each stage
+//                      and then hands the buffer to the epilogue;
+//   warps 2..5       : epilogue; warp w reads tensor-memory lanes
+//                      32 (w % 4) .. + 31, the lanes that warp may access.
 // A is read K-major. B is read MN-major straight from the row-major K x N
 // operand for BF16. For TF32 it is read K-major from a per-slice transposed
 // copy (N x K): kind::tf32 with an MN-major B left the accumulator unchanged
 // on this part. Each CTA fetches its own tiles (no cluster multicast).
 //
-// Every mbarrier wait is bounded. A wait that gives up raises *err, and the
-// CTA skips the rest of its work, waits (bounded) for the copies it issued,
+// Every mbarrier wait is bounded. A wait that gives up raises *err, ends every
+// role's loop, and the CTA waits (bounded) for the copies and MMAs it issued,
 // frees its tensor memory and returns.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -27,7 +34,7 @@
 
 namespace {
 
-constexpr int BM = 128, BN = 128, STAGES = 3, NT = 128;  // 97 KB smem: 2 CTAs per SM
+constexpr int BM = 128, BN = 128, STAGES = 3;  // 105 KB smem: 2 CTAs per SM
 constexpr uint32_t A_BYTES = BM * 128;   // 128 rows of one 128-byte K slab
 constexpr uint32_t B_BYTES = 128 * BN;   // (128 / elem) K rows x BN columns
 constexpr int kSpin = 1 << 22;           // try_wait polls before giving up
@@ -107,22 +114,29 @@ __device__ __forceinline__ void umma_commit(uint64_t* bar) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// Split form of tmem_ld16: issue now, wait later. The wait names the
+// registers as read-write operands so that nothing reads them before it.
+__device__ __forceinline__ void tmem_ld16_issue(uint32_t taddr, uint32_t* r) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, "
-      "%29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-        "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-        "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
+
+__device__ __forceinline__ void tmem_ld16_wait(uint32_t* r) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+int g_nsm = 0;  // SMs of the device (persistent grid size: 2 CTAs per SM)
 
 // KIND 0: BF16 inputs (kind::f16), KIND 1: TF32 inputs (kind::tf32).
 // BKMAJ: B given as N x K per slice (K contiguous) instead of K x N.
@@ -130,19 +144,29 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 // alias D; each element is read and written by one thread), an optional BF16
 // copy of D into dlow (the next GEMM's operand), and the fused reduction of D.
 // Without EPI the accumulator is stored as is.
+constexpr int NT = 192;  // warps 0, 1: producer, MMA; warps 2..5: epilogue
+
+size_t smem_bytes() {
+  return 1024 + STAGES * (A_BYTES + B_BYTES) + 4 * 32 * 16 * 4 + (2 * STAGES + 5) * 8 + 16;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(su32(bar)) : "memory");
+}
+
 template <int KIND, int BKMAJ, bool EPI>
 __global__ void __launch_bounds__(NT, 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-            float* D, int M, int N, int K, int* err, const int* skip, Epi ep,
+            float* D, int M, int N, int K, int Z, int* err, const int* skip, Epi ep,
             __nv_bfloat16* dlow) {
-  constexpr int ES = KIND == 0 ? 2 : 4;       // bytes per element
-  constexpr int BKE = 128 / ES;               // K elements per stage
-  constexpr int UK = KIND == 0 ? 16 : 8;      // K per MMA instruction
-  constexpr int NATOM = 128 / ES;             // N elements per B swizzle atom column
-  constexpr int NBOX = BN / NATOM;            // B boxes per stage
-  constexpr uint32_t B_COL = BKE * 128;       // bytes of one B atom column
-  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;  // BF16 : TF32
-  constexpr uint32_t BMAJ = BKMAJ ? 0u : 1u;  // 0: K-major, 1: MN-major
+  constexpr int ES = KIND == 0 ? 2 : 4;
+  constexpr int BKE = 128 / ES;
+  constexpr int UK = KIND == 0 ? 16 : 8;
+  constexpr int NATOM = 128 / ES;
+  constexpr int NBOX = BN / NATOM;
+  constexpr uint32_t B_COL = BKE * 128;
+  constexpr uint32_t FMT = KIND == 0 ? 1u : 2u;
+  constexpr uint32_t BMAJ = BKMAJ ? 0u : 1u;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | (0u << 15) | (BMAJ << 16) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
   if (skip && *skip) return;
@@ -151,15 +175,19 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
   uint8_t* sB = base + STAGES * A_BYTES;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sB + STAGES * B_BYTES);
+  float* sE = reinterpret_cast<float*>(sB + STAGES * B_BYTES);  // 4 warps x 32 x 16 floats
+  uint64_t* full = reinterpret_cast<uint64_t*>(sE + 4 * 32 * 16);
   uint64_t* empty = full + STAGES;
-  uint64_t* done = empty + STAGES;
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  uint64_t* accf = empty + STAGES;  // [2]: accumulator buffer ready for the epilogue
+  uint64_t* acce = accf + 2;        // [2]: accumulator buffer drained by the epilogue
+  uint64_t* fin = acce + 2;         // every MMA of this CTA completed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
   __shared__ int sh_fail;
   __shared__ float sh_coef[2];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN, z = blockIdx.z;
+  const int tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
+  const int ntile = tm * tn * Z;
   const int nk = (K + BKE - 1) / BKE;
 
   if (threadIdx.x == 0) {
@@ -167,11 +195,15 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
-    mbar_init(done, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(accf + b, 1);
+      mbar_init(acce + b, 4);  // one arrival per epilogue warp
+    }
+    mbar_init(fin, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     sh_fail = 0;
   }
-  if (EPI && threadIdx.x == 64) {  // warp 2 is idle until the epilogue
+  if (EPI && threadIdx.x == 64) {  // an epilogue thread, idle until the first tile
     double ca = 1.0, cp = 0.0;
     const Coef& c = ep.coef;
     if (c.rule == COEF_GK) {
@@ -195,7 +227,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tslot)),
-                 "r"(BN)
+                 "r"(2 * BN)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -203,177 +235,215 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  int issued = 0;  // stages the producer armed (for the bounded drain on failure)
-  // EPI: prev does not depend on the GEMM, so every thread loads its row's
-  // BN values of prev now and the loads overlap the main loop (whole 32-column
-  // chunks with N % 4 == 0; the edge chunks read prev in the epilogue).
-  float4 pre[EPI ? BN / 4 : 1];
-  if (EPI) {
-    const int prow = m0 + warp * 32 + lane;
-#pragma unroll
-    for (int q = 0; q < BN / 4; ++q) {
-      const int col = n0 + 4 * q;
-      const bool whole = ep.prev && prow < M && (N & 3) == 0 && n0 + (q / 8) * 32 + 32 <= N;
-      pre[q] = whole ? *reinterpret_cast<const float4*>(ep.prev + (size_t)z * M * N +
-                                                         (size_t)prow * N + col)
-                     : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-  }
+  volatile int* vfail = &sh_fail;
+  float local = 0.f;
+  int issued = 0;  // producer: K blocks armed (for the bounded drain on failure)
 
-  if (warp == 0 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(empty + s, ph ^ 1)) {
-        sh_fail = 1;
-        break;
-      }
-      mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-      tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, z, full + s);
-      if (BKMAJ) {
-        tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, z, full + s);
-      } else {
-#pragma unroll
-        for (int b = 0; b < NBOX; ++b)
-          tma_load_3d(sB + s * B_BYTES + b * B_COL, &tmB, n0 + b * NATOM, kb * BKE, z, full + s);
-      }
-      issued = kb + 1;
-    }
-  } else if (warp == 1 && lane == 0) {
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t ph = (kb / STAGES) & 1;
-      if (!mbar_wait(full + s, ph)) {
-        sh_fail = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < BKE / UK; ++kk) {
-        const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);  // K-major: advance in the row
-        const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
-                                  : smem_desc(b0 + kk * UK * 128, B_COL, 1024);  // MN: UK rows
-        umma<KIND>(tmem, ad, bd, IDESC, (kb | kk) != 0);
-      }
-      umma_commit(empty + s);
-    }
-    umma_commit(done);
-  }
-  __syncwarp();
-  const bool ok = mbar_wait(done, 0) && !sh_fail;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  float local = 0.f;  // EPI: this thread's share of the reduction
-  if (ok) {
-    const int row = m0 + warp * 32 + lane;
-#pragma unroll
-    for (int c = 0; c < BN / 32; ++c) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c * 32, v);
-      const int col0 = n0 + c * 32;
-      if (row < M) {
-        const size_t o = (size_t)z * M * N + (size_t)row * N + col0;
-        float* dst = D + o;
-        if (EPI) {
-          const float ca = sh_coef[0], cp = sh_coef[1];
-          const bool vec = col0 + 32 <= N && (N & 3) == 0;
-          if (vec) {  // this thread's 32 contiguous values of prev, loaded above
-            if (ep.prev) {
-              float4 pv[8];
-#pragma unroll
-              for (int q = 0; q < 8; ++q) pv[q] = pre[8 * c + q];
-#pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                v[4 * q] = fmaf(cp, pv[q].x, ca * v[4 * q]);
-                v[4 * q + 1] = fmaf(cp, pv[q].y, ca * v[4 * q + 1]);
-                v[4 * q + 2] = fmaf(cp, pv[q].z, ca * v[4 * q + 2]);
-                v[4 * q + 3] = fmaf(cp, pv[q].w, ca * v[4 * q + 3]);
-              }
-            } else {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) v[j] *= ca;
-            }
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x) {
+        const int z = t / (tm * tn), r = t % (tm * tn);
+        const int m0 = (r / tn) * BM, n0 = (r % tn) * BN;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (!mbar_wait(empty + s, ph ^ 1)) {
+            *vfail = 1;
+            break;
+          }
+          mbar_expect_tx(full + s, A_BYTES + B_BYTES);
+          tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, z, full + s);
+          if (BKMAJ) {
+            tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, z, full + s);
           } else {
-            for (int j = 0; j < 32 && col0 + j < N; ++j) {
-              float y = ca * v[j];
-              if (ep.prev) y = fmaf(cp, ep.prev[o + j], y);
-              v[j] = y;
-            }
+#pragma unroll
+            for (int bx = 0; bx < NBOX; ++bx)
+              tma_load_3d(sB + s * B_BYTES + bx * B_COL, &tmB, n0 + bx * NATOM, kb * BKE, z,
+                          full + s);
           }
-          if (vec) {
-#pragma unroll
-            for (int j = 0; j < 32; j += 4)
-              *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-            if (dlow) {
-#pragma unroll
-              for (int j = 0; j < 32; j += 4) {
-                __nv_bfloat162 lo = __floats2bfloat162_rn(v[j], v[j + 1]);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(v[j + 2], v[j + 3]);
-                uint2 pk;
-                pk.x = *reinterpret_cast<uint32_t*>(&lo);
-                pk.y = *reinterpret_cast<uint32_t*>(&hi);
-                *reinterpret_cast<uint2*>(dlow + o + j) = pk;
-              }
-            }
-          } else {
-            for (int j = 0; j < 32 && col0 + j < N; ++j) {
-              dst[j] = v[j];
-              if (dlow) dlow[o + j] = __float2bfloat16_rn(v[j]);
-            }
-          }
-          if (ep.red.out) {
-            if (vec && ep.red.other) {
-#pragma unroll
-              for (int q = 0; q < 8; ++q) {
-                const float4 ov = *reinterpret_cast<const float4*>(ep.red.other + o + 4 * q);
-                local = fmaf(v[4 * q], ov.x, fmaf(v[4 * q + 1], ov.y,
-                        fmaf(v[4 * q + 2], ov.z, fmaf(v[4 * q + 3], ov.w, local))));
-              }
-            } else if (vec) {
-#pragma unroll
-              for (int j = 0; j < 32; ++j) local = fmaf(v[j], v[j], local);
-            } else {
-              for (int j = 0; j < 32 && col0 + j < N; ++j)
-                local = fmaf(v[j], ep.red.other ? ep.red.other[o + j] : v[j], local);
-            }
-          }
-        } else if (col0 + 32 <= N && (N & 3) == 0) {
-#pragma unroll
-          for (int j = 0; j < 32; j += 4)
-            *reinterpret_cast<float4*>(dst + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
-        } else {
-          for (int j = 0; j < 32 && col0 + j < N; ++j) dst[j] = v[j];
+          issued = g + 1;
         }
       }
     }
-  } else if (threadIdx.x == 0) {
-    atomicExch(err, TC_ETIMEOUT);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int g = 0, i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int b = i & 1, u = i >> 1;
+        if (!mbar_wait(acce + b, (uint32_t)(u & 1) ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(b * BN);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % STAGES;
+          const uint32_t ph = (g / STAGES) & 1;
+          if (!mbar_wait(full + s, ph)) {
+            *vfail = 1;
+            ok = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < BKE / UK; ++kk) {
+            const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);
+            const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
+                                      : smem_desc(b0 + kk * UK * 128, B_COL, 1024);
+            umma<KIND>(acc, ad, bd, IDESC, (kb | kk) != 0);
+          }
+          umma_commit(empty + s);
+        }
+        if (!ok) break;
+        umma_commit(accf + b);
+      }
+      umma_commit(fin);  // completes once every MMA issued above has
+    }
+  } else {  // epilogue warps 2..5
+    // Each 32-row x 16-column chunk goes tensor memory -> registers (one row
+    // a lane) -> shared memory -> registers in a coalesced layout: lane l takes
+    // float4 (l & 3) of rows 8 i + (l >> 2), so a warp instruction covers 8
+    // rows x 64 contiguous bytes of D, prev and dlow instead of 32 rows x 16.
+    // The float4 slot of (row r, quad j) is j ^ ((r >> 1) & 3): conflict-free
+    // on both sides.
+    const int eq = warp & 3;  // tensor-memory lanes 32 eq .. 32 eq + 31
+    float* sw = sE + eq * (32 * 16);
+    const int rsub = lane >> 2, jq = lane & 3;
+    const bool nvec = (N & 3) == 0;
+    int i = 0;  // the loop exit and the waits are warp-uniform: tcgen05.ld is .sync.aligned
+    for (int t = blockIdx.x; t < ntile && !__any_sync(0xffffffffu, *vfail); t += gridDim.x, ++i) {
+      const int b = i & 1, u = i >> 1;
+      const int z = t / (tm * tn), r = t % (tm * tn);
+      const int m0 = (r / tn) * BM + eq * 32, n0 = (r % tn) * BN;
+      const size_t zoff = (size_t)z * M * N;
+      // prev of chunk c (rows 8 i + rsub, columns 16 c + 4 jq) sits in
+      // pre[4 (c % PD) + i], loaded PD chunks ahead; the first PD chunks load
+      // before the wait, as they do not depend on this tile's MMAs.
+      constexpr int NCH = BN / 16, PD = 4;
+      float4 pre[EPI ? 4 * PD : 1];
+      auto load_prev = [&](int c, int ii) {
+        const int row = m0 + 8 * ii + rsub, col = n0 + 16 * c + 4 * jq;
+        const bool whole = ep.prev && nvec && row < M && col + 4 <= N;
+        return whole ? *reinterpret_cast<const float4*>(ep.prev + zoff + (size_t)row * N + col)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+      };
+      if (EPI) {
+#pragma unroll
+        for (int q = 0; q < 4 * PD; ++q) pre[q] = load_prev(q >> 2, q & 3);
+      }
+      if (!__all_sync(0xffffffffu, mbar_wait(accf + b, (uint32_t)(u & 1)))) {
+        *vfail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const float ca = EPI ? sh_coef[0] : 1.f, cp = EPI ? sh_coef[1] : 0.f;
+      const uint32_t tacc = tmem + ((uint32_t)(eq * 32) << 16) + (uint32_t)(b * BN);
+      uint32_t rg[2][16];  // chunk c in rg[c & 1]; chunk c + 1 loads while c is stored
+      tmem_ld16_issue(tacc, rg[0]);
+      tmem_ld16_wait(rg[0]);
+#pragma unroll
+      for (int c = 0; c < NCH; ++c) {
+        const uint32_t* v = rg[c & 1];
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          *reinterpret_cast<float4*>(sw + lane * 16 + 4 * (j ^ ((lane >> 1) & 3))) =
+              make_float4(__uint_as_float(v[4 * j]), __uint_as_float(v[4 * j + 1]),
+                          __uint_as_float(v[4 * j + 2]), __uint_as_float(v[4 * j + 3]));
+        __syncwarp();
+        if (c + 1 < NCH) tmem_ld16_issue(tacc + (uint32_t)((c + 1) * 16), rg[(c + 1) & 1]);
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii) {
+          const int rr = 8 * ii + rsub;
+          float4 y = *reinterpret_cast<const float4*>(sw + rr * 16 + 4 * (jq ^ ((rr >> 1) & 3)));
+          const int row = m0 + rr, col = n0 + 16 * c + 4 * jq;
+          if (row >= M || col >= N) continue;
+          const size_t o = zoff + (size_t)row * N + col;
+          if (nvec) {  // col + 4 <= N
+            if (EPI) {
+              if (ep.prev) {
+                const float4 pv = pre[4 * (c % PD) + ii];
+                y.x = fmaf(cp, pv.x, ca * y.x);
+                y.y = fmaf(cp, pv.y, ca * y.y);
+                y.z = fmaf(cp, pv.z, ca * y.z);
+                y.w = fmaf(cp, pv.w, ca * y.w);
+              } else {
+                y.x *= ca;
+                y.y *= ca;
+                y.z *= ca;
+                y.w *= ca;
+              }
+              if (ep.red.out) {
+                const float4 ov = ep.red.other
+                                      ? *reinterpret_cast<const float4*>(ep.red.other + o)
+                                      : y;
+                local = fmaf(y.x, ov.x, fmaf(y.y, ov.y, fmaf(y.z, ov.z, fmaf(y.w, ov.w, local))));
+              }
+            }
+            *reinterpret_cast<float4*>(D + o) = y;
+            if (EPI && dlow) {
+              __nv_bfloat162 lo = __floats2bfloat162_rn(y.x, y.y);
+              __nv_bfloat162 hi = __floats2bfloat162_rn(y.z, y.w);
+              uint2 pk;
+              pk.x = *reinterpret_cast<uint32_t*>(&lo);
+              pk.y = *reinterpret_cast<uint32_t*>(&hi);
+              *reinterpret_cast<uint2*>(dlow + o) = pk;
+            }
+          } else {  // ragged row length: element by element
+            const float ys[4] = {y.x, y.y, y.z, y.w};
+            for (int e = 0; e < 4 && col + e < N; ++e) {
+              float w = ys[e];
+              if (EPI) {
+                w *= ca;
+                if (ep.prev) w = fmaf(cp, ep.prev[o + e], w);
+                if (ep.red.out) local = fmaf(w, ep.red.other ? ep.red.other[o + e] : w, local);
+              }
+              D[o + e] = w;
+              if (EPI && dlow) dlow[o + e] = __float2bfloat16_rn(w);
+            }
+          }
+        }
+        if (EPI && c + PD < NCH) {
+#pragma unroll
+          for (int ii = 0; ii < 4; ++ii) pre[4 * (c % PD) + ii] = load_prev(c + PD, ii);
+        }
+        __syncwarp();  // the next chunk overwrites sw
+        if (c + 1 < NCH) tmem_ld16_wait(rg[(c + 1) & 1]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(acce + b);  // this warp's lanes of buffer b are free
+    }
   }
-  if (!ok && warp == 0 && lane == 0) {  // let the copies this CTA issued land
-    for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-      mbar_wait(full + kb % STAGES, (kb / STAGES) & 1);
+
+  // wind down: every thread of the CTA
+  __syncthreads();
+  const bool failed = *vfail != 0;
+  if (warp == 1 && lane == 0) mbar_wait(fin, 0);  // the MMAs have finished with TMEM
+  if (failed && warp == 0 && lane == 0) {          // let the copies this CTA issued land
+    for (int g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
+      mbar_wait(full + g % STAGES, (g / STAGES) & 1);
+    atomicExch(err, TC_ETIMEOUT);
   }
   if (EPI && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * BN)
                  : "memory");
 }
-
-size_t smem_bytes() { return 1024 + STAGES * (A_BYTES + B_BYTES) + (2 * STAGES + 1) * 8 + 16; }
-
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 }  // namespace
 
 int umma_init() {
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<1, 1, false>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
-  TC_CUDA(cudaFuncSetAttribute(k_umma_gemm<0, 0, true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes()));
+  for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>})
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem_bytes()));
+  int dev = 0;
+  TC_CUDA(cudaGetDevice(&dev));
+  TC_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev));
   if (!g_encode) {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
@@ -423,15 +493,22 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
   return TC_OK;
 }
 
+namespace {
+unsigned grid_size(const UmmaMaps& m) {
+  const long tiles = (long)((m.N + BN - 1) / BN) * ((m.M + BM - 1) / BM) * m.slices;
+  const long cap = 2L * (g_nsm > 0 ? g_nsm : 152);
+  return (unsigned)(tiles < cap ? tiles : cap);
+}
+}  // namespace
+
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
-  dim3 grid((m.N + BN - 1) / BN, (m.M + BM - 1) / BM, m.slices);
   Epi none;
   if (m.kind == 0)
-    k_umma_gemm<0, 0, false><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
-                                                              skip, none, nullptr);
+    k_umma_gemm<0, 0, false><<<grid_size(m), NT, smem_bytes(), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
   else
-    k_umma_gemm<1, 1, false><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
-                                                              skip, none, nullptr);
+    k_umma_gemm<1, 1, false><<<grid_size(m), NT, smem_bytes(), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -439,9 +516,8 @@ int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStre
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st) {
   TC_CHECK(m.kind == 0);
-  dim3 grid((m.N + BN - 1) / BN, (m.M + BM - 1) / BM, m.slices);
-  k_umma_gemm<0, 0, true><<<grid, NT, smem_bytes(), st>>>(m.a, m.b, D, m.M, m.N, m.K, err,
-                                                           ep.skip, ep, dlow);
+  k_umma_gemm<0, 0, true><<<grid_size(m), NT, smem_bytes(), st>>>(
+      m.a, m.b, D, m.M, m.N, m.K, m.slices, err, ep.skip, ep, dlow);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
