@@ -599,7 +599,12 @@ def run_gpu(args):
                     "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src_peaks})",
                     "launch_ms": prod_ms, "algorithmic_bytes": gbytes,
-                    "note": "the mode-3 transform passes take most of this solve; see profiles"}
+                    "note": ("the mode-3 transform passes take most of this solve; see profiles"
+                             if args.product == "th" else
+                             "transform-domain iteration: the solve runs the fused form of "
+                             "this GEMM (Krylov epilogue and BF16 copy in the store, 235 MB a "
+                             "product at 512x512x64); timed here is the plain form; see "
+                             "profiles")}
         line = {
             "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
             "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,

@@ -182,7 +182,7 @@ int transform_init();  // shared-memory limits of the transform passes
 int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
                  const int* skip = nullptr);
 // vec.cu
-int vec_init();  // shared-memory carveout preference of the vector passes
+int vec_init();  // carveout preference of the vector passes; the SM count for their grids
 // out = ca * in + cp * prev and the fused reduction (the Krylov epilogue as a pass)
 int launch_epi(const float* in, float* out, size_t n, const Epi& ep, cudaStream_t st);
 int launch_reduce(const float* x, const float* other, size_t n, const Red& red,

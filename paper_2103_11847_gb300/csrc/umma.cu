@@ -322,7 +322,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       // prev of chunk c (rows 8 i + rsub, columns 16 c + 4 jq) sits in
       // pre[4 (c % PD) + i], loaded PD chunks ahead; the first PD chunks load
       // before the wait, as they do not depend on this tile's MMAs.
-      constexpr int NCH = BN / 16, PD = 4;
+      constexpr int NCH = BN / 16, PD = 3;
       float4 pre[EPI ? 4 * PD : 1];
       auto load_prev = [&](int c, int ii) {
         const int row = m0 + 8 * ii + rsub, col = n0 + 16 * c + 4 * jq;

@@ -45,10 +45,26 @@ k_scale(const float* __restrict__ in, float* out, size_t n, Coef c, const float*
 }
 
 // One LSQR step as its own launch (lsqr_step_scalars, lsqr_step_vectors):
-// CTA b updates elements [b * 1024, (b + 1) * 1024). Each thread loads its
-// elements of W, X and V before thread 0's FP64 scalar chain, so the two
-// latencies overlap; CTA 0 writes the state.
-constexpr int UPT = 4;
+// X += (phi / rho) W; V_{j+1} = V / alpha; W = V_{j+1} - (theta / rho) W.
+// One wave of CTAs strides over the tensor in units of T (float4 when every
+// pointer is 16-byte aligned and n % 4 == 0, else float), UPT units a thread
+// per pass, the next pass's loads issued before this pass's stores. Thread
+// 0's FP64 scalar chain runs once a CTA, while the first pass's loads are in
+// flight; CTA 0 writes the state.
+constexpr int UPT = 2;
+int g_sms = 152;             // SM count of the device (set by vec_init)
+int g_upd_ctas[2] = {4, 4};  // resident k_lsqr_update CTAs per SM: float, float4
+
+__device__ __forceinline__ float4 fma4(float a, float4 x, float4 y) {
+  return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+}
+__device__ __forceinline__ float4 mul4(float a, float4 x) {
+  return make_float4(a * x.x, a * x.y, a * x.z, a * x.w);
+}
+__device__ __forceinline__ float fma4(float a, float x, float y) { return fmaf(a, x, y); }
+__device__ __forceinline__ float mul4(float a, float x) { return a * x; }
+
+template <typename T>
 __global__ void __launch_bounds__(NT) k_lsqr_update(LsqrStep u) {
   pdl_wait();
   if (*u.done_in) {
@@ -57,30 +73,57 @@ __global__ void __launch_bounds__(NT) k_lsqr_update(LsqrStep u) {
   }
   __shared__ float sh[3];
   __shared__ int sh_stop;
-  const size_t base = (size_t)blockIdx.x * (NT * UPT) + threadIdx.x;
-  float w[UPT], x[UPT], v[UPT];
+  constexpr int EL = sizeof(T) / sizeof(float);
+  const size_t nu = u.n / EL;  // units; EL == 4 only when n % 4 == 0
+  T* X = reinterpret_cast<T*>(u.X);
+  T* W = reinterpret_cast<T*>(u.W);
+  const T* V = reinterpret_cast<const T*>(u.V);
+  T* Vs = reinterpret_cast<T*>(u.basis_slot);
+  const size_t per = (size_t)NT * UPT, stride = (size_t)gridDim.x * per;
+  size_t cta = (size_t)blockIdx.x * per;
+  T w[UPT], x[UPT], v[UPT];
 #pragma unroll
   for (int q = 0; q < UPT; ++q) {
-    const size_t i = base + (size_t)q * NT;
-    w[q] = i < u.n ? u.W[i] : 0.f;
-    x[q] = i < u.n ? u.X[i] : 0.f;
-    v[q] = i < u.n ? u.V[i] : 0.f;
+    const size_t i = cta + threadIdx.x + (size_t)q * NT;
+    if (i < nu) {
+      w[q] = W[i];
+      x[q] = X[i];
+      v[q] = V[i];
+    }
   }
   pdl_trigger();
   if (threadIdx.x == 0) sh_stop = lsqr_step_scalars(u, sh, blockIdx.x == 0);
   __syncthreads();
   const float cx = sh[0], cv = sh[1], cw = sh[2];
   const bool stop = sh_stop;
+  while (cta < nu) {
+    const size_t nxt = cta + stride;
+    T w2[UPT], x2[UPT], v2[UPT];
 #pragma unroll
-  for (int q = 0; q < UPT; ++q) {
-    const size_t i = base + (size_t)q * NT;
-    if (i >= u.n) break;
-    u.X[i] = fmaf(cx, w[q], x[q]);
-    if (!stop) {
-      const float vn = cv * v[q];
-      u.W[i] = fmaf(-cw, w[q], vn);
-      if (u.basis_slot) u.basis_slot[i] = vn;
+    for (int q = 0; q < UPT; ++q) {
+      const size_t i = nxt + threadIdx.x + (size_t)q * NT;
+      if (i < nu) {
+        w2[q] = W[i];
+        x2[q] = X[i];
+        v2[q] = V[i];
+      }
     }
+#pragma unroll
+    for (int q = 0; q < UPT; ++q) {
+      const size_t i = cta + threadIdx.x + (size_t)q * NT;
+      if (i < nu) {
+        X[i] = fma4(cx, w[q], x[q]);
+        if (!stop) {
+          const T vn = mul4(cv, v[q]);
+          W[i] = fma4(-cw, w[q], vn);
+          if (Vs) Vs[i] = vn;
+        }
+      }
+      w[q] = w2[q];
+      x[q] = x2[q];
+      v[q] = v2[q];
+    }
+    cta = nxt;
   }
 }
 
@@ -215,7 +258,15 @@ int vec_init() {
   const int c = cudaSharedmemCarveoutMaxShared;
   TC_CUDA(cudaFuncSetAttribute(k_reduce, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_scale, cudaFuncAttributePreferredSharedMemoryCarveout, c));
-  TC_CUDA(cudaFuncSetAttribute(k_lsqr_update, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_lsqr_update<float>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_lsqr_update<float4>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  int dev = 0;
+  TC_CUDA(cudaGetDevice(&dev));
+  TC_CUDA(cudaDeviceGetAttribute(&g_sms, cudaDevAttrMultiProcessorCount, dev));
+  TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_upd_ctas[0], k_lsqr_update<float>,
+                                                        NT, 0));
+  TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&g_upd_ctas[1], k_lsqr_update<float4>,
+                                                        NT, 0));
   TC_CUDA(cudaFuncSetAttribute(k_combine<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_combine<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_mgs_pass, cudaFuncAttributePreferredSharedMemoryCarveout, c));
@@ -247,8 +298,14 @@ int launch_scale(const float* in, float* out, size_t n, const Coef& c, const flo
 }
 
 int launch_lsqr_update(const LsqrStep& step, cudaStream_t st) {
-  const size_t blocks = (step.n + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
-  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
+  auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const bool vec = step.n % 4 == 0 && al(step.X) && al(step.W) && al(step.V) &&
+                   (!step.basis_slot || al(step.basis_slot));
+  const size_t units = vec ? step.n / 4 : step.n;
+  size_t blocks = (units + (size_t)NT * UPT - 1) / ((size_t)NT * UPT);
+  const size_t wave = (size_t)g_sms * (size_t)(g_upd_ctas[vec ? 1 : 0] > 0 ? g_upd_ctas[vec ? 1 : 0] : 1);
+  if (blocks > wave) blocks = wave;
+  if (blocks < 1) blocks = 1;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)blocks);
   cfg.blockDim = dim3(NT);
@@ -258,7 +315,10 @@ int launch_lsqr_update(const LsqrStep& step, cudaStream_t st) {
   attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update, step));
+  if (vec)
+    TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update<float4>, step));
+  else
+    TC_CUDA(cudaLaunchKernelEx(&cfg, k_lsqr_update<float>, step));
   return TC_OK;
 }
 
