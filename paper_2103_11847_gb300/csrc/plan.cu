@@ -127,11 +127,14 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
   }
   if (lowp(p)) {  // transform to the GEMM input type, tcgen05 slice GEMMs, transform back
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    TC_TRY(launch_mode3_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s,
-                             p->opts.precision == TC_BF16, ep.skip, st));
+    const int bf16 = p->opts.precision == TC_BF16;
+    const bool tct = n3 > TC_TUBE_MIN_N3;
+    TC_TRY(tct ? launch_mode3_tc_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s, bf16, ep.skip, err, st)
+               : launch_mode3_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s, bf16, ep.skip, st));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
-    return launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
+    return tct ? launch_mode3_tc(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st)
+               : launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
   }
   TC_TRY(launch_mode3(X, p->tmp1, p->dM, n3, (size_t)n2 * s, mid, st));
   TC_TRY(launch_slice_gemm(p->Ah, p->tmp1, p->tmp2, n1, s, n2, n3, nullptr, nullptr, mid, st));
@@ -221,11 +224,15 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
   }
   if (lowp(p)) {
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    TC_TRY(launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s,
-                             p->opts.precision == TC_BF16, ep.skip, st));
+    const int bf16 = p->opts.precision == TC_BF16;
+    const bool tct = n3 > TC_TUBE_MIN_N3;
+    TC_TRY(tct ? launch_mode3_tc_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, bf16, ep.skip,
+                                      err, st)
+               : launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, bf16, ep.skip, st));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
-    return launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
+    return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st)
+               : launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
   TC_TRY(launch_mode3(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, mid, st));
   TC_TRY(launch_slice_gemm(p->AhT, p->tmp1, p->tmp2, n2, s, n1, n3, nullptr, nullptr, mid, st));

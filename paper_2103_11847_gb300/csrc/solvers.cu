@@ -167,9 +167,16 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   const bool td = td_route(p) && !a.spatial_basis;
   const float* Cin = a.C;
   float* Xw = a.X;
-  if (td) {
+  // The tensor-core transform (split BF16, error near 2^-16) serves the TF32
+  // and BF16 plans above TC_TUBE_MIN_N3; the rest keep the FP32 pass.
+  const bool tct = p->opts.precision != TC_FP32 && p->n3 > TC_TUBE_MIN_N3;
+  auto mode3 = [&](const float* in, float* out, const float* T, size_t P) -> int {
     Epi none;
-    TC_TRY(launch_mode3(a.C, p->lsqr_Ct, p->dM, p->n3, p->Ty / p->n3, none, st));
+    return tct ? launch_mode3_tc(in, out, T, p->n3, P, none, p->dev_err, st)
+               : launch_mode3(in, out, T, p->n3, P, none, st);
+  };
+  if (td) {
+    TC_TRY(mode3(a.C, p->lsqr_Ct, p->dM, p->Ty / p->n3));
     Cin = p->lsqr_Ct;
     Xw = p->lsqr_Xt;
   }
@@ -281,9 +288,8 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
                           st));
   }
   if (td) {  // back to the spatial domain: X = idct(X~), X_reg likewise
-    Epi none;
-    TC_TRY(launch_mode3(Xw, a.X, p->dMinv, p->n3, p->Tx / p->n3, none, st));
-    if (keep) TC_TRY(launch_mode3(Xr_w, a.X_reg, p->dMinv, p->n3, p->Tx / p->n3, none, st));
+    TC_TRY(mode3(Xw, a.X, p->dMinv, p->Tx / p->n3));
+    if (keep) TC_TRY(mode3(Xr_w, a.X_reg, p->dMinv, p->Tx / p->n3));
   }
   k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, gcv_on ? lam : nullptr,
                                gcv_on ? gcv : nullptr, (keep && a.lcurve) ? flags + 8 : nullptr);

@@ -13,6 +13,11 @@
 // pass with the Krylov epilogue.
 #define TC_MAX_FUSED 4
 #define TC_MAX_N3 64
+// TF32/BF16 plans run the mode-3 transforms on the tensor cores for n3 above
+// this: the FP32 pass does 2 n3 FLOP per value it moves and is bound by FP32
+// issue at large n3; at or below this both are bound by HBM, and the FP32
+// pass has less fixed work per CTA.
+#define TC_TUBE_MIN_N3 32
 #define TC_MAX_PROJ 128  // largest projected problem (k) on the device
 
 // ---------------------------------------------------------------- epilogue --
@@ -177,6 +182,14 @@ int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t
 // rounded to TF32 (bf16 = 0). No epilogue.
 int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                       int bf16, const int* skip, cudaStream_t st);
+// Tensor-core forms of launch_mode3 / launch_mode3_lowp (tcgen05, operands
+// split into BF16 hi + lo pairs: relative error near 2^-16 a term), used by
+// the TF32 and BF16 precision forms; *err is set to TC_ETIMEOUT if the bounded
+// wait for the MMAs gives up.
+int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
+                    const Epi& ep, int* err, cudaStream_t st);
+int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
+                         int bf16, const int* skip, int* err, cudaStream_t st);
 // Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
 int transform_init();  // shared-memory limits of the transform passes
 int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,

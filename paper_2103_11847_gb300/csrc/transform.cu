@@ -11,6 +11,7 @@
 #include <cuda_bf16.h>
 
 #include "tc_device.cuh"
+#include "tcgen05.cuh"
 
 namespace {
 
@@ -249,6 +250,186 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
   }
 }
 
+// ---------------------------------------------------------- tensor cores ----
+// Mode-3 transform on the tcgen05 tensor cores, for the TF32 and BF16
+// precision forms: out[k][p] = sum_l T[k][l] in[l][p] (+ the Krylov
+// epilogue) as the transposed product D = in^T T^T. One CTA a tile of TP =
+// 128 pixels: A = in^T (128 pixels x 64 slices), MN-major straight from the
+// slice layout; B = T (64 outputs x 64 slices), K-major; D = 128 pixels x 64
+// outputs in tensor memory, lane = pixel, so each store (and prev load) of a
+// warp is 32 consecutive pixels of one slice. n3 < 64 pads K and N with zeros.
+// Both operands are split into BF16 pairs, x = hi + lo with hi = bf16(x) and
+// lo = bf16(x - hi), and D accumulates hi.hi + hi.lo + lo.hi in FP32
+// (kind::f16). The dropped lo.lo term and the roundings of lo leave a
+// relative error near 2^-16 a term, where one BF16 product has 2^-8.
+// Shared memory holds the four operand halves in the 128-byte swizzled
+// layouts the descriptors name (16-byte chunk j of row r at chunk j ^ (r & 7)).
+constexpr int TP = 128, TK = 64, TNT = 128;
+constexpr uint32_t TA_BYTES = TP * TK * 2;  // one BF16 half of A: 16 KB
+constexpr uint32_t TB_BYTES = TK * TK * 2;  // one BF16 half of B: 8 KB
+
+size_t tube_smem() { return 1024 + 2 * TA_BYTES + 2 * TB_BYTES + 16; }
+
+// hi and lo halves of eight values, packed as eight BF16 each
+__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
+  uint32_t h[4], l[4];
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
+    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * j] - __low2float(hb),
+                                                     x[2 * j + 1] - __high2float(hb));
+    h[j] = *reinterpret_cast<const uint32_t*>(&hb);
+    l[j] = *reinterpret_cast<const uint32_t*>(&lb);
+  }
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+template <int OUT>
+__global__ void __launch_bounds__(TNT, 4)
+k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, int n3, size_t P,
+       Epi ep, int* err) {
+  using namespace tc5;
+  // D F32; A, B BF16; A MN-major, B K-major; N = 64, M = 128
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
+                             ((uint32_t)(TK >> 3) << 17) | ((uint32_t)(TP >> 4) << 24);
+  if (ep.skip && *ep.skip) return;
+  extern __shared__ uint8_t tube_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(tube_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sAh = base;
+  uint8_t* sAl = base + TA_BYTES;
+  uint8_t* sBh = base + 2 * TA_BYTES;
+  uint8_t* sBl = sBh + TB_BYTES;
+  uint64_t* done = reinterpret_cast<uint64_t*>(sBl + TB_BYTES);
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+  __shared__ float sh_coef[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const size_t p0 = (size_t)blockIdx.x * TP;
+  const bool vec = P % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
+
+  // input: unit u = tid + 128 i is slice l = u / 16, pixels p0 + 8 (u % 16) + 0..7
+  float x[8][8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int u = tid + TNT * i, l = u >> 4;
+    const size_t p = p0 + 8 * (u & 15);
+    if (l < n3 && vec && p + 8 <= P) {
+      const float4 a = *reinterpret_cast<const float4*>(in + (size_t)l * P + p);
+      const float4 b = *reinterpret_cast<const float4*>(in + (size_t)l * P + p + 4);
+      x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+      x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 8; ++e)
+        x[i][e] = (l < n3 && p + e < P) ? in[(size_t)l * P + p + e] : 0.f;
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tslot)),
+                 "r"(TK)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (OUT == OUT_F32) coef_compute(ep.coef, sh_coef);
+  // B = T: unit u = tid + 128 j is row n = u / 8 (output k), slices 8 (u % 8) + 0..7
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int u = tid + TNT * j, n = u >> 3, c = u & 7;
+    float t[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int l = 8 * c + e;
+      t[e] = (n < n3 && l < n3) ? __ldg(T + (size_t)n * n3 + l) : 0.f;
+    }
+    uint4 hi, lo;
+    split8(t, hi, lo);
+    const uint32_t off = n * 128 + ((c ^ (n & 7)) << 4);
+    *reinterpret_cast<uint4*>(sBh + off) = hi;
+    *reinterpret_cast<uint4*>(sBl + off) = lo;
+  }
+  // A = in^T, MN-major: pixel chunk c of slice l in atom column c / 8, row l
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int u = tid + TNT * i, l = u >> 4, c = u & 15;
+    uint4 hi, lo;
+    split8(x[i], hi, lo);
+    const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
+    *reinterpret_cast<uint4*>(sAh + off) = hi;
+    *reinterpret_cast<uint4*>(sAl + off) = lo;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  if (tid == 0) {
+#pragma unroll
+    for (int pass = 0; pass < 3; ++pass) {  // hi.hi, hi.lo, lo.hi
+      const uint32_t a0 = su32(pass == 2 ? sAl : sAh), b0 = su32(pass == 1 ? sBl : sBh);
+#pragma unroll
+      for (int kk = 0; kk < TK / 16; ++kk)
+        umma<0>(tmem, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
+                smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+    }
+    umma_commit(done);
+  }
+
+  // epilogue: thread = pixel p0 + 32 warp + lane = tensor-memory lane 32 warp + lane
+  const size_t p = p0 + 32 * warp + lane;
+  const bool live = p < P;
+  float pv[32];
+  auto load_prev = [&](int k0) {
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      pv[j] = (OUT == OUT_F32 && ep.prev && live && k0 + j < n3)
+                  ? ep.prev[(size_t)(k0 + j) * P + p]
+                  : 0.f;
+  };
+  load_prev(0);  // does not depend on the MMAs
+  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));
+  float local = 0.f;
+  if (ok) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const float ca = OUT == OUT_F32 ? sh_coef[0] : 1.f, cp = OUT == OUT_F32 ? sh_coef[1] : 0.f;
+#pragma unroll
+    for (int h = 0; h < TK / 32; ++h) {
+      if (h > 0) load_prev(32 * h);
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * h), v);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k = 32 * h + j;
+        if (k >= n3 || !live) continue;
+        const size_t idx = (size_t)k * P + p;
+        if (OUT == OUT_BF16) {
+          static_cast<__nv_bfloat16*>(out_v)[idx] = __float2bfloat16_rn(v[j]);
+        } else if (OUT == OUT_TF32) {
+          static_cast<float*>(out_v)[idx] = round_tf32(v[j]);
+        } else {
+          float o = ca * v[j];
+          if (ep.prev) o = fmaf(cp, pv[j], o);
+          static_cast<float*>(out_v)[idx] = o;
+          if (ep.red.out) local = fmaf(o, ep.red.other ? ep.red.other[idx] : o, local);
+        }
+      }
+    }
+  } else if (lane == 0) {
+    atomicExch(err, TC_ETIMEOUT);
+  }
+  if (OUT == OUT_F32 && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TK)
+                 : "memory");
+}
+
 }  // namespace
 
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
@@ -276,7 +457,35 @@ int init_kpw() {
 }
 }  // namespace
 
+int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
+                    const Epi& ep, int* err, cudaStream_t st) {
+  TC_CHECK(n3 >= 1 && n3 <= TK);
+  const size_t blocks = (P + TP - 1) / TP;
+  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
+  k_tube<OUT_F32><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
+                         int bf16, const int* skip, int* err, cudaStream_t st) {
+  TC_CHECK(n3 >= 1 && n3 <= TK);
+  const size_t blocks = (P + TP - 1) / TP;
+  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
+  Epi ep;
+  ep.skip = skip;
+  if (bf16)
+    k_tube<OUT_BF16><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  else
+    k_tube<OUT_TF32><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 int transform_init() {
+  for (auto fn : {k_tube<OUT_F32>, k_tube<OUT_BF16>, k_tube<OUT_TF32>})
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tube_smem()));
   TC_TRY(init_kpw<1>());
   TC_TRY(init_kpw<2>());
   TC_TRY(init_kpw<4>());

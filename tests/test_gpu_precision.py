@@ -49,7 +49,7 @@ def rel(a, b):
 
 @pytest.mark.parametrize("name", ["tf32", "bf16"])
 @pytest.mark.parametrize("n1,n2,s,n3", [(64, 64, 64, 3), (136, 96, 40, 9), (128, 256, 200, 64),
-                                        (200, 136, 72, 1)])
+                                        (200, 136, 72, 1), (72, 40, 56, 37), (24, 40, 24, 33)])
 def test_lowp_cprod_and_adjoint(tc, name, n1, n2, s, n3):
     p = inputs.random_problem(n1, n2, s, n3, seed=n1 + s)
     A, X, Y = f32(p["A"]), f32(p["X"]), f32(p["Y"])
