@@ -264,6 +264,10 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
 // relative error near 2^-16 a term, where one BF16 product has 2^-8.
 // Shared memory holds the four operand halves in the 128-byte swizzled
 // layouts the descriptors name (16-byte chunk j of row r at chunk j ^ (r & 7)).
+// The kernel is persistent, four CTAs a SM, each looping over tiles. B is
+// split once a CTA. Once a tile's MMAs have completed, the next tile's FP32
+// input is copied (cp.async) into the 32 KB of the A halves while this tile's
+// epilogue runs. The reduction runs once a CTA.
 constexpr int TP = 128, TK = 64, TNT = 128;
 constexpr uint32_t TA_BYTES = TP * TK * 2;  // one BF16 half of A: 16 KB
 constexpr uint32_t TB_BYTES = TK * TK * 2;  // one BF16 half of B: 8 KB
@@ -297,34 +301,41 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
   extern __shared__ uint8_t tube_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(tube_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sAh = base;
+  uint8_t* sAh = base;  // A halves; between tiles, the FP32 staging of the next input tile
   uint8_t* sAl = base + TA_BYTES;
+  float* stg = reinterpret_cast<float*>(base);  // [TK][TP] FP32, 32 KB = both A halves
   uint8_t* sBh = base + 2 * TA_BYTES;
   uint8_t* sBl = sBh + TB_BYTES;
   uint64_t* done = reinterpret_cast<uint64_t*>(sBl + TB_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ float sh_coef[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const size_t p0 = (size_t)blockIdx.x * TP;
+  const size_t ntile = (P + TP - 1) / TP;
   const bool vec = P % 4 == 0 && (reinterpret_cast<uintptr_t>(in) & 15) == 0;
 
-  // input: unit u = tid + 128 i is slice l = u / 16, pixels p0 + 8 (u % 16) + 0..7
-  float x[8][8];
+  // Input tile t into the staging buffer: unit u = tid + 128 i is slice l =
+  // u / 16, pixels 8 (u % 16) + 0..7; each thread later reads its own units.
+  auto stage = [&](size_t t) {
+    const size_t p0 = t * TP;
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int u = tid + TNT * i, l = u >> 4;
-    const size_t p = p0 + 8 * (u & 15);
-    if (l < n3 && vec && p + 8 <= P) {
-      const float4 a = *reinterpret_cast<const float4*>(in + (size_t)l * P + p);
-      const float4 b = *reinterpret_cast<const float4*>(in + (size_t)l * P + p + 4);
-      x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
-      x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
-    } else {
+    for (int i = 0; i < 8; ++i) {
+      const int u = tid + TNT * i, l = u >> 4, px = 8 * (u & 15);
+      float* dst = stg + l * TP + px;
+      const size_t p = p0 + px;
+      if (vec) {
 #pragma unroll
-      for (int e = 0; e < 8; ++e)
-        x[i][e] = (l < n3 && p + e < P) ? in[(size_t)l * P + p + e] : 0.f;
+        for (int h = 0; h < 2; ++h) {
+          const bool ok = l < n3 && p + 4 * h + 4 <= P;
+          cp_async16(dst + 4 * h, ok ? in + (size_t)l * P + p + 4 * h : in, ok);
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) dst[e] = (l < n3 && p + e < P) ? in[(size_t)l * P + p + e] : 0.f;
+      }
     }
-  }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  if (blockIdx.x < ntile) stage(blockIdx.x);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tslot)),
@@ -337,7 +348,7 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (OUT == OUT_F32) coef_compute(ep.coef, sh_coef);
-  // B = T: unit u = tid + 128 j is row n = u / 8 (output k), slices 8 (u % 8) + 0..7
+  // B = T, once a CTA: unit u = tid + 128 j is row n = u / 8 (output k), slices 8 (u % 8) + 0..7
 #pragma unroll
   for (int j = 0; j < 4; ++j) {
     const int u = tid + TNT * j, n = u >> 3, c = u & 7;
@@ -353,55 +364,78 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
     *reinterpret_cast<uint4*>(sBh + off) = hi;
     *reinterpret_cast<uint4*>(sBl + off) = lo;
   }
-  // A = in^T, MN-major: pixel chunk c of slice l in atom column c / 8, row l
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int u = tid + TNT * i, l = u >> 4, c = u & 15;
-    uint4 hi, lo;
-    split8(x[i], hi, lo);
-    const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
-    *reinterpret_cast<uint4*>(sAh + off) = hi;
-    *reinterpret_cast<uint4*>(sAl + off) = lo;
-  }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tslot;
-  if (tid == 0) {
-#pragma unroll
-    for (int pass = 0; pass < 3; ++pass) {  // hi.hi, hi.lo, lo.hi
-      const uint32_t a0 = su32(pass == 2 ? sAl : sAh), b0 = su32(pass == 1 ? sBl : sBh);
-#pragma unroll
-      for (int kk = 0; kk < TK / 16; ++kk)
-        umma<0>(tmem, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
-                smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
-    }
-    umma_commit(done);
-  }
-
-  // epilogue: thread = pixel p0 + 32 warp + lane = tensor-memory lane 32 warp + lane
-  const size_t p = p0 + 32 * warp + lane;
-  const bool live = p < P;
-  float pv[32];
-  auto load_prev = [&](int k0) {
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      pv[j] = (OUT == OUT_F32 && ep.prev && live && k0 + j < n3)
-                  ? ep.prev[(size_t)(k0 + j) * P + p]
-                  : 0.f;
-  };
-  load_prev(0);  // does not depend on the MMAs
-  const bool ok = __all_sync(0xffffffffu, mbar_wait(done, 0));
+  const float ca = OUT == OUT_F32 ? sh_coef[0] : 1.f, cp = OUT == OUT_F32 ? sh_coef[1] : 0.f;
   float local = 0.f;
-  if (ok) {
+  bool ok = true;
+  uint32_t phase = 0;
+
+  for (size_t t = blockIdx.x; t < ntile && ok; t += gridDim.x, phase ^= 1u) {
+    const size_t p0 = t * TP;
+    // staged input -> registers -> split into the A halves (same bytes)
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    float x[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int u = tid + TNT * i, l = u >> 4, px = 8 * (u & 15);
+      const float4 a = *reinterpret_cast<const float4*>(stg + l * TP + px);
+      const float4 b = *reinterpret_cast<const float4*>(stg + l * TP + px + 4);
+      x[i][0] = a.x; x[i][1] = a.y; x[i][2] = a.z; x[i][3] = a.w;
+      x[i][4] = b.x; x[i][5] = b.y; x[i][6] = b.z; x[i][7] = b.w;
+    }
+    __syncthreads();  // every thread has its staged values
+    // A = in^T, MN-major: pixel chunk c of slice l in atom column c / 8, row l
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int u = tid + TNT * i, l = u >> 4, c = u & 15;
+      uint4 hi, lo;
+      split8(x[i], hi, lo);
+      const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
+      *reinterpret_cast<uint4*>(sAh + off) = hi;
+      *reinterpret_cast<uint4*>(sAl + off) = lo;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const float ca = OUT == OUT_F32 ? sh_coef[0] : 1.f, cp = OUT == OUT_F32 ? sh_coef[1] : 0.f;
+    if (tid == 0) {
+#pragma unroll
+      for (int pass = 0; pass < 3; ++pass) {  // hi.hi, hi.lo, lo.hi
+        const uint32_t a0 = su32(pass == 2 ? sAl : sAh), b0 = su32(pass == 1 ? sBl : sBh);
+#pragma unroll
+        for (int kk = 0; kk < TK / 16; ++kk)
+          umma<0>(tmem, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
+                  smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+      }
+      umma_commit(done);
+    }
+
+    // epilogue: thread = pixel p0 + 32 warp + lane = tensor-memory lane 32 warp + lane
+    const size_t p = p0 + 32 * warp + lane;
+    const bool live = p < P;
+    float pv[2][32];  // prev of outputs 32 h + j
+    auto load_prev = [&](int h) {
+#pragma unroll
+      for (int j = 0; j < 32; ++j)
+        pv[h][j] = (OUT == OUT_F32 && ep.prev && live && 32 * h + j < n3)
+                       ? ep.prev[(size_t)(32 * h + j) * P + p]
+                       : 0.f;
+    };
+    load_prev(0);  // does not depend on the MMAs
+    ok = __syncthreads_and(mbar_wait(done, phase));
+    if (!ok) break;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // the MMAs have read the A halves: stage the next tile there now
+    if (t + gridDim.x < ntile) stage(t + gridDim.x);
 #pragma unroll
     for (int h = 0; h < TK / 32; ++h) {
-      if (h > 0) load_prev(32 * h);
       float v[32];
       tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)(32 * h), v);
+      if (h + 1 < TK / 32) load_prev(h + 1);  // in flight while this half is stored
 #pragma unroll
       for (int j = 0; j < 32; ++j) {
         const int k = 32 * h + j;
@@ -413,15 +447,17 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
           static_cast<float*>(out_v)[idx] = round_tf32(v[j]);
         } else {
           float o = ca * v[j];
-          if (ep.prev) o = fmaf(cp, pv[j], o);
+          if (ep.prev) o = fmaf(cp, pv[h][j], o);
           static_cast<float*>(out_v)[idx] = o;
           if (ep.red.out) local = fmaf(o, ep.red.other ? ep.red.other[idx] : o, local);
         }
       }
     }
-  } else if (lane == 0) {
-    atomicExch(err, TC_ETIMEOUT);
+    // the next tile's MMAs overwrite the accumulator after the next barrier
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
+  if (!ok && tid == 0) atomicExch(err, TC_ETIMEOUT);
+  asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
   if (OUT == OUT_F32 && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -457,12 +493,20 @@ int init_kpw() {
 }
 }  // namespace
 
+namespace {
+int g_tube_sms = 152;  // SM count of the device (set by transform_init)
+
+// persistent grid: four CTAs a SM, no more than one a tile
+unsigned tube_grid(size_t P) {
+  const size_t tiles = (P + TP - 1) / TP, cap = 4 * (size_t)g_tube_sms;
+  return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
+}
+}  // namespace
+
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
                     const Epi& ep, int* err, cudaStream_t st) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
-  const size_t blocks = (P + TP - 1) / TP;
-  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
-  k_tube<OUT_F32><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  k_tube<OUT_F32><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -470,22 +514,27 @@ int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, siz
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                          int bf16, const int* skip, int* err, cudaStream_t st) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
-  const size_t blocks = (P + TP - 1) / TP;
-  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
   Epi ep;
   ep.skip = skip;
   if (bf16)
-    k_tube<OUT_BF16><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+    k_tube<OUT_BF16><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
   else
-    k_tube<OUT_TF32><<<(unsigned)blocks, TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+    k_tube<OUT_TF32><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 
 int transform_init() {
-  for (auto fn : {k_tube<OUT_F32>, k_tube<OUT_BF16>, k_tube<OUT_TF32>})
+  for (auto fn : {k_tube<OUT_F32>, k_tube<OUT_BF16>, k_tube<OUT_TF32>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tube_smem()));
+    // four CTAs of 50 KB a SM need the largest shared-memory carveout
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+  }
+  int dev = 0;
+  TC_CUDA(cudaGetDevice(&dev));
+  TC_CUDA(cudaDeviceGetAttribute(&g_tube_sms, cudaDevAttrMultiProcessorCount, dev));
   TC_TRY(init_kpw<1>());
   TC_TRY(init_kpw<2>());
   TC_TRY(init_kpw<4>());

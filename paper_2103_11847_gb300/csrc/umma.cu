@@ -341,9 +341,13 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 }  // namespace
 
 int umma_init() {
-  for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>})
+  for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes()));
+    // two CTAs of 105 KB a SM need the largest shared-memory carveout
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+  }
   int dev = 0;
   TC_CUDA(cudaGetDevice(&dev));
   TC_CUDA(cudaDeviceGetAttribute(&g_nsm, cudaDevAttrMultiProcessorCount, dev));
