@@ -61,7 +61,7 @@ def product_flops(n1, n2, s, n3, two_sided):
     return f
 
 
-def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32", s=0):
+def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32", s=0, n3=64):
     """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu).
     A fused product is one launch, except two-sided with s > 256 (two)."""
     if fused:
@@ -70,6 +70,8 @@ def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp
         per_product = 4 if two_sided else 3
     if precision != "fp32":  # transform, [transpose for TF32], tcgen05 GEMM, transform back
         per_product = 4 if precision == "tf32" else 3
+        if precision == "bf16x3" and n3 <= 32:  # FP32 transform pass, then the three planes
+            per_product = 4
     init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
     # product, adjoint, and the LSQR step: inside the next product on the
     # two-sided fused route (s <= 256), else its own launch; the last step
@@ -198,7 +200,8 @@ def precision_forms(dev, peaks, steps=3):
                        f"X {n2}x{s}x{n3}", "l2": "inputs (64-256 MB per tensor) exceed L2"}
     C = None
     st = torch.cuda.current_stream()
-    for name, code in (("fp32", tcprod.TC_FP32), ("tf32", tcprod.TC_TF32), ("bf16", tcprod.TC_BF16)):
+    for name, code in (("fp32", tcprod.TC_FP32), ("tf32", tcprod.TC_TF32), ("bf16", tcprod.TC_BF16),
+                       ("bf16x3", tcprod.TC_BF16X3)):
         plan = tcprod.Plan(A, s=s, precision=code)
         if C is None:
             Cc = plan.cprod(Xt)
@@ -217,8 +220,9 @@ def precision_forms(dev, peaks, steps=3):
         ms = e0.elapsed_time(e1) / steps
         inf = tcprod.read_info(info)
         # slice GEMM alone on a transform-domain operand of the plan's input type
-        dt = torch.bfloat16 if name == "bf16" else torch.float32
-        Xh = torch.randn((n3, n2, s), device=dev).to(dt)
+        dt = torch.bfloat16 if name in ("bf16", "bf16x3") else torch.float32
+        planes = 3 if name == "bf16x3" else 1
+        Xh = torch.randn((planes * n3, n2, s), device=dev).to(dt)
         Yh = torch.empty((n3, n1, s), device=dev)
         for _ in range(3):
             tcprod.tc_slice_gemm(plan.handle, Xh, Yh)
@@ -230,7 +234,7 @@ def precision_forms(dev, peaks, steps=3):
         g1.record(st)
         torch.cuda.synchronize()
         gms = g0.elapsed_time(g1) / reps
-        es = 2 if name == "bf16" else 4
+        es = 2 * planes if name in ("bf16", "bf16x3") else 4
         gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
         gflops = 2.0 * n1 * n2 * s * n3
         gbs = gbytes / (gms * 1e-3) / 1e9
@@ -238,14 +242,15 @@ def precision_forms(dev, peaks, steps=3):
                      "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
                      "rel_err_lsqr": float((X - Xt).norm() / Xt.norm()), "lambda": inf["lam"],
                      "status": inf["status"],
-                     "slice_gemm": {"kernel": "k_umma_gemm (tcgen05)" if name != "fp32"
-                                    else "k_slice_gemm (FFMA)", "ms": gms,
+                     "slice_gemm": {"kernel": ("k_umma_gemm (tcgen05, six split-BF16 products)"
+                                               if name == "bf16x3" else "k_umma_gemm (tcgen05)")
+                                    if name != "fp32" else "k_slice_gemm (FFMA)", "ms": gms,
                                     "GB_per_s": gbs, "TFLOP_per_s": gflops / (gms * 1e-3) / 1e12,
                                     "hbm_frac": gbs / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                                     "algorithmic_bytes": gbytes}}
         plan.close()
     base = out["fp32"]["rel_err_reg"]
-    for name in ("tf32", "bf16"):
+    for name in ("tf32", "bf16", "bf16x3"):
         out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
         out[name]["speedup_vs_fp32"] = out[name]["iters_per_s"] / out["fp32"]["iters_per_s"]
     # Algorithm 1's dct reading (ORTHODCT): off the fused route LSQR runs in the
@@ -493,7 +498,8 @@ def run_gpu(args):
     B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
     Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
     G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
-    prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16}[args.precision]
+    prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16,
+            "bf16x3": tcprod.TC_BF16X3}[args.precision]
     product = {"th": tcprod.TC_TH, "orthodct": tcprod.TC_ORTHODCT}[args.product]
     plan = tcprod.Plan(A, B, s=s, precision=prec, product=product)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
@@ -543,10 +549,12 @@ def run_gpu(args):
         src, dst = Xr, torch.empty(plan.yshape(), device=dev)
         call = lambda: tcprod.tc_cprod(plan.handle, src, dst)
     else:
-        lowp_dt = torch.bfloat16 if args.precision == "bf16" else torch.float32
-        roof_kernel = ("k_umma_gemm (tcgen05 slice GEMMs of one product)" if args.precision != "fp32"
-                       else "k_slice_gemm (FFMA slice GEMMs of one product)")
-        src = torch.randn((n3, n2, s), device=dev).to(lowp_dt)
+        lowp_dt = torch.bfloat16 if args.precision in ("bf16", "bf16x3") else torch.float32
+        planes = 3 if args.precision == "bf16x3" else 1
+        roof_kernel = ("k_umma_gemm (tcgen05 slice GEMMs of one product"
+                       + (", six split-BF16 products)" if planes == 3 else ")")
+                       if args.precision != "fp32" else "k_slice_gemm (FFMA slice GEMMs of one product)")
+        src = torch.randn((planes * n3, n2, s), device=dev).to(lowp_dt)
         dst = torch.empty((n3, n1, s), device=dev)
         call = lambda: tcprod.tc_slice_gemm(plan.handle, src, dst)
         reps = 50
@@ -591,7 +599,7 @@ def run_gpu(args):
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                    f"({src_peaks} max clock)", "launch_ms": prod_ms}
         else:  # tcgen05 GEMM: A~ and X~ in the input type read once, Y~ written in FP32
-            es = 2 if args.precision == "bf16" else 4
+            es = {"bf16": 2, "bf16x3": 6}.get(args.precision, 4)
             gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
             hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
             gbs = gbytes / (prod_ms * 1e-3) / 1e9
@@ -609,7 +617,7 @@ def run_gpu(args):
             "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
             "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else f"{args.precision} GEMM inputs, f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "f32-level: three BF16 planes an operand, six products, f32 accumulate"}.get(args.precision, f"{args.precision} GEMM inputs, f32"),
             "data": "synthetic (seeded image + Gaussian blur + 1e-3 noise)",
             "config": {"workload": f"{args.workload}: c-LSQR {iters} it + Tikhonov/GCV, "
                                    f"A {n1}x{n2}x{n3}" + (f", B {s}x{s}x{n3}" if two else "")
@@ -622,7 +630,8 @@ def run_gpu(args):
                     "h2d_bytes_per_step": int(C.numel() * 4),
                     "d2h_bytes_per_step": int(Xr.numel() * 4 + info.numel())},
             "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4,
-                                                              precision=args.precision, s=s),
+                                                              precision=args.precision, s=s,
+                                                              n3=n3),
             "clocks": clk,
             "solve": {"iters": inf["iters"], "status": inf["status"], "lambda": inf["lam"],
                       "resid": inf["resid"],
@@ -682,7 +691,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-forms", action="store_true")
     ap.add_argument("--iters", type=int, default=0, help="override the workload's iterations")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"],
                     help="slice-GEMM inputs of the main workload (tensor-core forms need "
                          "one-sided plans: video_512 or colour_64)")
     ap.add_argument("--product", default="th", choices=["th", "orthodct"],

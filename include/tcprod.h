@@ -59,7 +59,14 @@ typedef enum {
 typedef enum {
   TC_FP32 = 0, /* slice GEMMs in FP32 (FFMA)                         */
   TC_TF32 = 1, /* slice GEMMs on tensor cores, TF32 in, FP32 accumulate */
-  TC_BF16 = 2  /* slice GEMMs on tensor cores, BF16 in, FP32 accumulate */
+  TC_BF16 = 2, /* slice GEMMs on tensor cores, BF16 in, FP32 accumulate */
+  TC_BF16X3 = 3 /* FP32-level on the tensor cores: each operand of the slice
+                   GEMMs (and, for n3 > 32, of the tube transforms) is split into
+                   three BF16 planes, x = x0 + x1 + x2 (x0 = bf16(x), x1 =
+                   bf16(x - x0), x2 = bf16(x - x0 - x1)), and the six products
+                   x_i y_j with i + j <= 2 accumulate in FP32. Products are
+                   within the FP32 plans' 1e-5 bound (about 1e-6 relative, a few
+                   times the FFMA path's, set by the tensor cores' accumulation) */
 } tc_precision;
 
 typedef enum {
@@ -265,7 +272,8 @@ int tc_lsqr_c_learned(tc_plan* plan, const tc_mlp* mlp, const float* C, float* X
  * with A~ = A x_3 M held by the plan (eqs. (dft9), (dft8)). One-sided plans only.
  *   Xh: device, n3 slices of K x s (K = n2, or n1 for the adjoint), in the
  *       plan's GEMM input type: FP32 for TC_FP32 plans, BF16 for TC_BF16, FP32
- *       already rounded to TF32 for TC_TF32.
+ *       already rounded to TF32 for TC_TF32, and for TC_BF16X3 three BF16 planes
+ *       of n3 K s values each (x0, x1, x2 as above, plane q at Xh + q n3 K s).
  *   Yh: device FP32, n3 slices of M x s (M = n1, or n2 for the adjoint).
  * On the tensor-core forms this is one tcgen05 GEMM launch. */
 int tc_slice_gemm(tc_plan* plan, const void* Xh, float* Yh, int adjoint, tc_stream_t stream);

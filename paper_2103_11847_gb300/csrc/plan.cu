@@ -87,6 +87,13 @@ void dfree(void* p) {
 
 bool fused(const tc_plan* p) { return p->n3 <= TC_MAX_FUSED && p->opts.precision == TC_FP32; }
 bool lowp(const tc_plan* p) { return p->opts.precision != TC_FP32; }
+bool x3(const tc_plan* p) { return p->opts.precision == TC_BF16X3; }
+// operand type of the plan's tensor-core GEMMs (RoundKind)
+int rkind(const tc_plan* p) {
+  return x3(p) ? ROUND_BF16X3 : (p->opts.precision == TC_BF16 ? ROUND_BF16 : ROUND_TF32);
+}
+// where the rounded operand of the tensor-core GEMMs lives
+void* lowop(const tc_plan* p) { return x3(p) ? p->lowX : (void*)p->tmp1; }
 }  // namespace
 
 void tc_set_error(const char* what, cudaError_t e) {
@@ -127,13 +134,19 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
   }
   if (lowp(p)) {  // transform to the GEMM input type, tcgen05 slice GEMMs, transform back
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    const int bf16 = p->opts.precision == TC_BF16;
     const bool tct = n3 > TC_TUBE_MIN_N3;
-    TC_TRY(tct ? launch_mode3_tc_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s, bf16, ep.skip, err, st)
-               : launch_mode3_lowp(X, p->tmp1, p->dM, n3, (size_t)n2 * s, bf16, ep.skip, st));
+    const size_t P = (size_t)n2 * s;
+    if (tct) {
+      TC_TRY(launch_mode3_tc_lowp(X, lowop(p), p->dM, n3, P, rkind(p), ep.skip, err, st));
+    } else if (x3(p)) {  // the exact FP32 pass, then the three planes
+      TC_TRY(launch_mode3(X, p->tmp2, p->dM, n3, P, mid, st));
+      TC_TRY(launch_round(p->tmp2, p->lowX, P * n3, ROUND_BF16X3, st, ep.skip));
+    } else {
+      TC_TRY(launch_mode3_lowp(X, p->tmp1, p->dM, n3, P, rkind(p) == ROUND_BF16, ep.skip, st));
+    }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
-    return tct ? launch_mode3_tc(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st)
+    return tct ? launch_mode3_tc(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st, x3(p))
                : launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
   }
   TC_TRY(launch_mode3(X, p->tmp1, p->dM, n3, (size_t)n2 * s, mid, st));
@@ -160,8 +173,7 @@ int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t
   const float* src = p->tmp2;
   if (lowp(p)) {
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    TC_TRY(launch_round(Xt, p->tmp1, (size_t)n2 * s * n3, p->opts.precision == TC_BF16, st,
-                        ep.skip));
+    TC_TRY(launch_round(Xt, lowop(p), (size_t)n2 * s * n3, rkind(p), st, ep.skip));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
   } else {
@@ -194,8 +206,7 @@ int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream
   const float* src = p->tmp2;
   if (lowp(p)) {
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    TC_TRY(launch_round(Yt, p->tmp1, (size_t)n1 * s * n3, p->opts.precision == TC_BF16, st,
-                        ep.skip));
+    TC_TRY(launch_round(Yt, lowop(p), (size_t)n1 * s * n3, rkind(p), st, ep.skip));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
   } else {
@@ -224,14 +235,20 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
   }
   if (lowp(p)) {
     int* err = ep.red.status ? ep.red.status : p->dev_err;
-    const int bf16 = p->opts.precision == TC_BF16;
     const bool tct = n3 > TC_TUBE_MIN_N3;
-    TC_TRY(tct ? launch_mode3_tc_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, bf16, ep.skip,
-                                      err, st)
-               : launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, bf16, ep.skip, st));
+    const size_t P = (size_t)n1 * s;
+    if (tct) {
+      TC_TRY(launch_mode3_tc_lowp(Y, lowop(p), p->dMinvT, n3, P, rkind(p), ep.skip, err, st));
+    } else if (x3(p)) {
+      TC_TRY(launch_mode3(Y, p->tmp2, p->dMinvT, n3, P, mid, st));
+      TC_TRY(launch_round(p->tmp2, p->lowX, P * n3, ROUND_BF16X3, st, ep.skip));
+    } else {
+      TC_TRY(launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, P, rkind(p) == ROUND_BF16, ep.skip,
+                               st));
+    }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
-    return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st)
+    return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, x3(p))
                : launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
   TC_TRY(launch_mode3(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, mid, st));
@@ -318,21 +335,23 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
   TC_TRY(dalloc(&p->dev_err, 1));
   TC_CUDA(cudaMemsetAsync(p->dev_err, 0, sizeof(int), st));
   if (lowp(p)) {
-    const int bf16 = p->opts.precision == TC_BF16;
+    const int bf16 = p->opts.precision != TC_TF32;  // BF16 operands (one plane or three)
+    const int ns = x3(p) ? 3 : 1;
     const size_t es = bf16 ? 2 : 4;
-    TC_CUDA(cudaMalloc(&p->AhL, TA * es));
-    TC_CUDA(cudaMalloc(&p->AhTL, TA * es));
-    TC_TRY(launch_round(p->Ah, p->AhL, TA, bf16, st));
-    TC_TRY(launch_round(p->AhT, p->AhTL, TA, bf16, st));
+    TC_CUDA(cudaMalloc(&p->AhL, TA * es * ns));
+    TC_CUDA(cudaMalloc(&p->AhTL, TA * es * ns));
+    TC_TRY(launch_round(p->Ah, p->AhL, TA, rkind(p), st));
+    TC_TRY(launch_round(p->AhT, p->AhTL, TA, rkind(p), st));
+    if (ns == 3) TC_CUDA(cudaMalloc(&p->lowX, p->tmp_elems * 2 * 3));
     p->umf = new UmmaMaps();
     p->uma = new UmmaMaps();
     const int kind = bf16 ? 0 : 1;
     // TF32 reads B K-major: the transformed operand is transposed per slice into tmp3
     if (!bf16) TC_TRY(dalloc(&p->tmp3, p->tmp_elems));
-    const void* bop = bf16 ? (const void*)p->tmp1 : (const void*)p->tmp3;
-    TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3));
-    TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3));
-    if (bf16 && p->opts.product == TC_ORTHODCT) {
+    const void* bop = bf16 ? lowop(p) : (const void*)p->tmp3;
+    TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3, ns));
+    TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3, ns));
+    if (p->opts.precision == TC_BF16 && p->opts.product == TC_ORTHODCT) {
       // transform-domain LSQR with the epilogue in the GEMM: each product's
       // store also writes the BF16 operand of the next one, so the forward and
       // adjoint GEMMs read separate buffers (bV: V~, n2 x s; bU: U~, n1 x s)
@@ -377,6 +396,7 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   delete p->uma;
   delete p->umf_td;
   delete p->uma_td;
+  dfree(p->lowX);
   dfree(p->lowV);
   dfree(p->lowU);
   delete p;
@@ -398,7 +418,8 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
     o = *opts;
     for (int r : o.reserved)
       if (r != 0) return TC_EINVAL;
-    if (o.precision != TC_FP32 && o.precision != TC_TF32 && o.precision != TC_BF16)
+    if (o.precision != TC_FP32 && o.precision != TC_TF32 && o.precision != TC_BF16 &&
+        o.precision != TC_BF16X3)
       return TC_EINVAL;
     if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
     if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
@@ -463,7 +484,7 @@ extern "C" int tc_slice_gemm(tc_plan* p, const void* Xh, float* Yh, int adjoint,
     bop = p->tmp3;
   }
   UmmaMaps m;
-  TC_TRY(make_umma_maps(&m, p->opts.precision == TC_BF16 ? 0 : 1, adjoint ? p->AhTL : p->AhL, bop,
-                        M, p->s, K, p->n3));
+  TC_TRY(make_umma_maps(&m, p->opts.precision == TC_TF32 ? 1 : 0, adjoint ? p->AhTL : p->AhL, bop,
+                        M, p->s, K, p->n3, x3(p) ? 3 : 1));
   return launch_umma(m, Yh, p->dev_err, nullptr, st);
 }

@@ -172,7 +172,8 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   const bool tct = p->opts.precision != TC_FP32 && p->n3 > TC_TUBE_MIN_N3;
   auto mode3 = [&](const float* in, float* out, const float* T, size_t P) -> int {
     Epi none;
-    return tct ? launch_mode3_tc(in, out, T, p->n3, P, none, p->dev_err, st)
+    return tct ? launch_mode3_tc(in, out, T, p->n3, P, none, p->dev_err, st,
+                                 p->opts.precision == TC_BF16X3)
                : launch_mode3(in, out, T, p->n3, P, none, st);
   };
   if (td) {

@@ -123,6 +123,7 @@ struct tc_plan {
   void* AhTL = nullptr;           // its slice transposes
   UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
   UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
+  void* lowX = nullptr;           // TC_BF16X3 plans: the GEMM operand as three BF16 planes
   void* lowV = nullptr;           // BF16 ORTHODCT plans: bf16(V~) and bf16(U~), the operands
   void* lowU = nullptr;           // of the transform-domain GEMMs with fused epilogues
   UmmaMaps* umf_td = nullptr;     // A~ times lowV
@@ -182,17 +183,22 @@ int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t
 // rounded to TF32 (bf16 = 0). No epilogue.
 int launch_mode3_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                       int bf16, const int* skip, cudaStream_t st);
+// GEMM operand types of the tensor-core forms: TF32 (in FP32 storage), BF16,
+// and three BF16 planes (plane q of n values at out + q n) for the
+// FP32-level form.
+enum RoundKind { ROUND_TF32 = 0, ROUND_BF16 = 1, ROUND_BF16X3 = 2 };
 // Tensor-core forms of launch_mode3 / launch_mode3_lowp (tcgen05, operands
-// split into BF16 hi + lo pairs: relative error near 2^-16 a term), used by
-// the TF32 and BF16 precision forms; *err is set to TC_ETIMEOUT if the bounded
-// wait for the MMAs gives up.
+// split into BF16 planes: two, relative error near 2^-16 a term, for the TF32
+// and BF16 forms; three (split3 / ROUND_BF16X3), near 2^-27, for the
+// FP32-level form). *err is set to TC_ETIMEOUT if the bounded wait for the
+// MMAs gives up.
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
-                    const Epi& ep, int* err, cudaStream_t st);
+                    const Epi& ep, int* err, cudaStream_t st, int split3 = 0);
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
-                         int bf16, const int* skip, int* err, cudaStream_t st);
-// Elementwise rounding of n FP32 values to BF16 or to TF32 (in FP32 storage).
+                         int kind, const int* skip, int* err, cudaStream_t st);
+// Elementwise rounding of n FP32 values to the operand type `kind` (RoundKind).
 int transform_init();  // shared-memory limits of the transform passes
-int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
+int launch_round(const float* in, void* out, size_t n, int kind, cudaStream_t st,
                  const int* skip = nullptr);
 // vec.cu
 int vec_init();  // carveout preference of the vector passes; the SM count for their grids

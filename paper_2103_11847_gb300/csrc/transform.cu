@@ -18,7 +18,7 @@ namespace {
 // Output element of a transform pass: FP32 (with the Krylov epilogue), or the
 // low-precision operand of a tensor-core GEMM: BF16 (round to nearest even)
 // or FP32 holding a TF32 value (round to nearest, ties away, as cvt.rna).
-enum OutKind { OUT_F32 = 0, OUT_BF16 = 1, OUT_TF32 = 2 };
+enum OutKind { OUT_F32 = 0, OUT_BF16 = 1, OUT_TF32 = 2, OUT_BF16X3 = 3 };
 
 __device__ __forceinline__ float round_tf32(float x) {
   uint32_t r;
@@ -207,14 +207,18 @@ int pick(const float* in, void* out, const float* T, int n3, size_t P, const Epi
 
 // Elementwise rounding to the GEMM input type; four elements per thread and
 // iteration when in is 16-byte aligned (the output then is 8- or 16-byte
-// aligned too), with four such groups of loads in flight.
+// aligned too), with four such groups of loads in flight. OUT_BF16X3 writes
+// three BF16 planes of n values each: bf16(x), then bf16 of what each plane
+// leaves (the planes of the FP32-level form).
 __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int kind,
                         const int* skip) {
   if (skip && *skip) return;
   const size_t st = (size_t)gridDim.x * blockDim.x;
   const size_t gt = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   size_t done = 0;
-  if ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+  __nv_bfloat16* o16 = static_cast<__nv_bfloat16*>(out);
+  if ((reinterpret_cast<uintptr_t>(in) & 15) == 0 && (reinterpret_cast<uintptr_t>(out) & 15) == 0 &&
+      (kind != OUT_BF16X3 || n % 4 == 0)) {
     const size_t n4 = n / 4;
     for (size_t i0 = gt; i0 < n4; i0 += 4 * st) {
       float4 v[4];
@@ -227,13 +231,20 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
       for (int u = 0; u < 4; ++u) {
         const size_t i = i0 + u * st;
         if (i >= n4) break;
-        if (kind == OUT_BF16) {
-          __nv_bfloat162 lo = __floats2bfloat162_rn(v[u].x, v[u].y);
-          __nv_bfloat162 hi = __floats2bfloat162_rn(v[u].z, v[u].w);
-          uint2 pk;
-          pk.x = *reinterpret_cast<uint32_t*>(&lo);
-          pk.y = *reinterpret_cast<uint32_t*>(&hi);
-          reinterpret_cast<uint2*>(out)[i] = pk;
+        if (kind == OUT_BF16 || kind == OUT_BF16X3) {
+          float4 r = v[u];
+          for (int q = 0; q < (kind == OUT_BF16X3 ? 3 : 1); ++q) {
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
+            const __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
+            uint2 pk;
+            pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+            pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+            reinterpret_cast<uint2*>(o16 + q * n)[i] = pk;
+            r.x -= __low2float(lo);
+            r.y -= __high2float(lo);
+            r.z -= __low2float(hi);
+            r.w -= __high2float(hi);
+          }
         } else {
           reinterpret_cast<float4*>(out)[i] = make_float4(round_tf32(v[u].x), round_tf32(v[u].y),
                                                           round_tf32(v[u].z), round_tf32(v[u].w));
@@ -243,10 +254,16 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
     done = 4 * n4;
   }
   for (size_t i = done + gt; i < n; i += st) {
-    if (kind == OUT_BF16)
-      static_cast<__nv_bfloat16*>(out)[i] = __float2bfloat16_rn(in[i]);
-    else
+    if (kind == OUT_BF16 || kind == OUT_BF16X3) {
+      float r = in[i];
+      for (int q = 0; q < (kind == OUT_BF16X3 ? 3 : 1); ++q) {
+        const __nv_bfloat16 b = __float2bfloat16_rn(r);
+        o16[q * n + i] = b;
+        r -= __bfloat162float(b);
+      }
+    } else {
       static_cast<float*>(out)[i] = round_tf32(in[i]);
+    }
   }
 }
 
@@ -258,41 +275,56 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
 // slice layout; B = T (64 outputs x 64 slices), K-major; D = 128 pixels x 64
 // outputs in tensor memory, lane = pixel, so each store (and prev load) of a
 // warp is 32 consecutive pixels of one slice. n3 < 64 pads K and N with zeros.
-// Both operands are split into BF16 pairs, x = hi + lo with hi = bf16(x) and
-// lo = bf16(x - hi), and D accumulates hi.hi + hi.lo + lo.hi in FP32
-// (kind::f16). The dropped lo.lo term and the roundings of lo leave a
-// relative error near 2^-16 a term, where one BF16 product has 2^-8.
-// Shared memory holds the four operand halves in the 128-byte swizzled
-// layouts the descriptors name (16-byte chunk j of row r at chunk j ^ (r & 7)).
-// The kernel is persistent, four CTAs a SM, each looping over tiles. B is
-// split once a CTA. Once a tile's MMAs have completed, the next tile's FP32
-// input is copied (cp.async) into the 32 KB of the A halves while this tile's
-// epilogue runs. The reduction runs once a CTA.
+// Both operands are split into NS BF16 planes: x_0 = bf16(x), then each next
+// plane rounds what the ones before leave, x_s = bf16(x - x_0 - .. - x_{s-1})
+// (each difference is exact in FP32). D accumulates the products x_i y_j with
+// i + j < NS in FP32 (kind::f16):
+// * NS = 2 (TF32 and BF16 forms): 3 products, relative error near 2^-16 a term;
+// * NS = 3 (the FP32-level form): 6 products, near 2^-27 a term, below FP32
+//   rounding; the tensor cores' FP32 accumulation then sets the error.
+// Shared memory holds the operand planes in the 128-byte swizzled layouts the
+// descriptors name (16-byte chunk j of row r at chunk j ^ (r & 7)).
+// The kernel is persistent, 4 (NS = 2) or 3 (NS = 3) CTAs a SM, each looping
+// over tiles. B is split once a CTA. Once a tile's MMAs have completed, the
+// next tile's FP32 input is copied (cp.async) into the first 32 KB of the A
+// planes while this tile's epilogue runs. The reduction runs once a CTA.
 constexpr int TP = 128, TK = 64, TNT = 128;
-constexpr uint32_t TA_BYTES = TP * TK * 2;  // one BF16 half of A: 16 KB
-constexpr uint32_t TB_BYTES = TK * TK * 2;  // one BF16 half of B: 8 KB
+constexpr uint32_t TA_BYTES = TP * TK * 2;  // one BF16 plane of A: 16 KB
+constexpr uint32_t TB_BYTES = TK * TK * 2;  // one BF16 plane of B: 8 KB
 
-size_t tube_smem() { return 1024 + 2 * TA_BYTES + 2 * TB_BYTES + 16; }
+constexpr size_t tube_smem(int ns) { return 1024 + ns * (TA_BYTES + TB_BYTES) + 16; }
+constexpr int tube_ctas(int ns) { return ns == 2 ? 4 : 3; }  // resident CTAs a SM
 
-// hi and lo halves of eight values, packed as eight BF16 each
-__device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
-  uint32_t h[4], l[4];
+// product p of the split operands: planes (tube_pa(p), tube_pb(p)), the
+// products with i + j = 0, 1, 2 in that order
+__device__ __forceinline__ int tube_pa(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
+__device__ __forceinline__ int tube_pb(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
+
+// NS planes of eight values, packed as eight BF16 each
+template <int NS>
+__device__ __forceinline__ void split8(const float* x, uint4* pl) {
+  float r[8];
 #pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    const __nv_bfloat162 hb = __floats2bfloat162_rn(x[2 * j], x[2 * j + 1]);
-    const __nv_bfloat162 lb = __floats2bfloat162_rn(x[2 * j] - __low2float(hb),
-                                                     x[2 * j + 1] - __high2float(hb));
-    h[j] = *reinterpret_cast<const uint32_t*>(&hb);
-    l[j] = *reinterpret_cast<const uint32_t*>(&lb);
+  for (int e = 0; e < 8; ++e) r[e] = x[e];
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const __nv_bfloat162 b = __floats2bfloat162_rn(r[2 * j], r[2 * j + 1]);
+      w[j] = *reinterpret_cast<const uint32_t*>(&b);
+      r[2 * j] -= __low2float(b);
+      r[2 * j + 1] -= __high2float(b);
+    }
+    pl[s] = make_uint4(w[0], w[1], w[2], w[3]);
   }
-  hi = make_uint4(h[0], h[1], h[2], h[3]);
-  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-template <int OUT>
-__global__ void __launch_bounds__(TNT, 4)
+template <int OUT, int NS>
+__global__ void __launch_bounds__(TNT, tube_ctas(NS))
 k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, int n3, size_t P,
        Epi ep, int* err) {
+  constexpr int NPASS = NS == 2 ? 3 : 6;
   using namespace tc5;
   // D F32; A, B BF16; A MN-major, B K-major; N = 64, M = 128
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
@@ -301,12 +333,10 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
   extern __shared__ uint8_t tube_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(tube_raw) + 1023) & ~(uintptr_t)1023);
-  uint8_t* sAh = base;  // A halves; between tiles, the FP32 staging of the next input tile
-  uint8_t* sAl = base + TA_BYTES;
-  float* stg = reinterpret_cast<float*>(base);  // [TK][TP] FP32, 32 KB = both A halves
-  uint8_t* sBh = base + 2 * TA_BYTES;
-  uint8_t* sBl = sBh + TB_BYTES;
-  uint64_t* done = reinterpret_cast<uint64_t*>(sBl + TB_BYTES);
+  uint8_t* sA = base;  // NS A planes; between tiles, the FP32 staging of the next input tile
+  float* stg = reinterpret_cast<float*>(base);  // [TK][TP] FP32, 32 KB: the first two planes
+  uint8_t* sB = base + NS * TA_BYTES;           // NS B planes
+  uint64_t* done = reinterpret_cast<uint64_t*>(sB + NS * TB_BYTES);
   uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
   __shared__ float sh_coef[2];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -358,11 +388,11 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
       const int l = 8 * c + e;
       t[e] = (n < n3 && l < n3) ? __ldg(T + (size_t)n * n3 + l) : 0.f;
     }
-    uint4 hi, lo;
-    split8(t, hi, lo);
+    uint4 pl[NS];
+    split8<NS>(t, pl);
     const uint32_t off = n * 128 + ((c ^ (n & 7)) << 4);
-    *reinterpret_cast<uint4*>(sBh + off) = hi;
-    *reinterpret_cast<uint4*>(sBl + off) = lo;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(sB + q * TB_BYTES + off) = pl[q];
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -392,11 +422,11 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
       const int u = tid + TNT * i, l = u >> 4, c = u & 15;
-      uint4 hi, lo;
-      split8(x[i], hi, lo);
+      uint4 pl[NS];
+      split8<NS>(x[i], pl);
       const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
-      *reinterpret_cast<uint4*>(sAh + off) = hi;
-      *reinterpret_cast<uint4*>(sAl + off) = lo;
+#pragma unroll
+      for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(sA + q * TA_BYTES + off) = pl[q];
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -404,8 +434,9 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (tid == 0) {
 #pragma unroll
-      for (int pass = 0; pass < 3; ++pass) {  // hi.hi, hi.lo, lo.hi
-        const uint32_t a0 = su32(pass == 2 ? sAl : sAh), b0 = su32(pass == 1 ? sBl : sBh);
+      for (int pass = 0; pass < NPASS; ++pass) {
+        const uint32_t a0 = su32(sA + tube_pa(pass) * TA_BYTES);
+        const uint32_t b0 = su32(sB + tube_pb(pass) * TB_BYTES);
 #pragma unroll
         for (int kk = 0; kk < TK / 16; ++kk)
           umma<0>(tmem, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
@@ -443,6 +474,14 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
         const size_t idx = (size_t)k * P + p;
         if (OUT == OUT_BF16) {
           static_cast<__nv_bfloat16*>(out_v)[idx] = __float2bfloat16_rn(v[j]);
+        } else if (OUT == OUT_BF16X3) {  // three planes of n3 P values
+          __nv_bfloat16* o3 = static_cast<__nv_bfloat16*>(out_v);
+          const __nv_bfloat16 y0 = __float2bfloat16_rn(v[j]);
+          const float r1 = v[j] - __bfloat162float(y0);
+          const __nv_bfloat16 y1 = __float2bfloat16_rn(r1);
+          o3[idx] = y0;
+          o3[(size_t)n3 * P + idx] = y1;
+          o3[2 * (size_t)n3 * P + idx] = __float2bfloat16_rn(r1 - __bfloat162float(y1));
         } else if (OUT == OUT_TF32) {
           static_cast<float*>(out_v)[idx] = round_tf32(v[j]);
         } else {
@@ -496,39 +535,51 @@ int init_kpw() {
 namespace {
 int g_tube_sms = 152;  // SM count of the device (set by transform_init)
 
-// persistent grid: four CTAs a SM, no more than one a tile
-unsigned tube_grid(size_t P) {
-  const size_t tiles = (P + TP - 1) / TP, cap = 4 * (size_t)g_tube_sms;
+// persistent grid: tube_ctas(ns) CTAs a SM, no more than one a tile
+unsigned tube_grid(size_t P, int ns) {
+  const size_t tiles = (P + TP - 1) / TP, cap = (size_t)tube_ctas(ns) * g_tube_sms;
   return (unsigned)(tiles < 1 ? 1 : (tiles < cap ? tiles : cap));
 }
 }  // namespace
 
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
-                    const Epi& ep, int* err, cudaStream_t st) {
+                    const Epi& ep, int* err, cudaStream_t st, int split3) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
-  k_tube<OUT_F32><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  if (split3)
+    k_tube<OUT_F32, 3><<<tube_grid(P, 3), TNT, tube_smem(3), st>>>(in, out, T_dev, n3, P, ep, err);
+  else
+    k_tube<OUT_F32, 2><<<tube_grid(P, 2), TNT, tube_smem(2), st>>>(in, out, T_dev, n3, P, ep, err);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
-                         int bf16, const int* skip, int* err, cudaStream_t st) {
+                         int kind, const int* skip, int* err, cudaStream_t st) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
   Epi ep;
   ep.skip = skip;
-  if (bf16)
-    k_tube<OUT_BF16><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+  if (kind == ROUND_BF16X3)
+    k_tube<OUT_BF16X3, 3><<<tube_grid(P, 3), TNT, tube_smem(3), st>>>(in, out, T_dev, n3, P, ep,
+                                                                        err);
+  else if (kind == ROUND_BF16)
+    k_tube<OUT_BF16, 2><<<tube_grid(P, 2), TNT, tube_smem(2), st>>>(in, out, T_dev, n3, P, ep, err);
   else
-    k_tube<OUT_TF32><<<tube_grid(P), TNT, tube_smem(), st>>>(in, out, T_dev, n3, P, ep, err);
+    k_tube<OUT_TF32, 2><<<tube_grid(P, 2), TNT, tube_smem(2), st>>>(in, out, T_dev, n3, P, ep, err);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
 
 int transform_init() {
-  for (auto fn : {k_tube<OUT_F32>, k_tube<OUT_BF16>, k_tube<OUT_TF32>}) {
+  // several CTAs of 50 (NS = 2) or 73 KB (NS = 3) a SM need the largest carveout
+  for (auto fn : {k_tube<OUT_F32, 2>, k_tube<OUT_BF16, 2>, k_tube<OUT_TF32, 2>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)tube_smem()));
-    // four CTAs of 50 KB a SM need the largest shared-memory carveout
+                                 (int)tube_smem(2)));
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared));
+  }
+  for (auto fn : {k_tube<OUT_F32, 3>, k_tube<OUT_BF16X3, 3>}) {
+    TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)tube_smem(3)));
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
   }
@@ -542,9 +593,12 @@ int transform_init() {
   return TC_OK;
 }
 
-int launch_round(const float* in, void* out, size_t n, int bf16, cudaStream_t st,
+int launch_round(const float* in, void* out, size_t n, int kind, cudaStream_t st,
                  const int* skip) {
-  k_round<<<152 * 8, 256, 0, st>>>(in, out, n, bf16 ? OUT_BF16 : OUT_TF32, skip);
+  TC_CHECK(kind == ROUND_TF32 || kind == ROUND_BF16 || kind == ROUND_BF16X3);
+  k_round<<<152 * 8, 256, 0, st>>>(
+      in, out, n, kind == ROUND_BF16X3 ? OUT_BF16X3 : (kind == ROUND_BF16 ? OUT_BF16 : OUT_TF32),
+      skip);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

@@ -57,7 +57,16 @@ size_t smem_bytes() {
 }
 
 
-template <int KIND, int BKMAJ, bool EPI>
+// Split-operand products (NPAIR = 6): A and B are each given as three BF16
+// planes, x = x0 + x1 + x2 (x0 = bf16(x), x1 = bf16(x - x0), x2 = bf16(x - x0
+// - x1)), stacked as slices p Z + z of one map. D accumulates the six products
+// x_i y_j with i + j <= 2. The dropped terms and the residual of the split are
+// near 2^-27 relative; the FP32 accumulation in the tensor core then sets the
+// error (about 1e-6 relative at K = 64..512, a few times FFMA's).
+__device__ __forceinline__ int pair_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
+__device__ __forceinline__ int pair_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
+
+template <int KIND, int BKMAJ, bool EPI, int NPAIR = 1>
 __global__ void __launch_bounds__(NT, 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             float* D, int M, int N, int K, int Z, int* err, const int* skip, Epi ep,
@@ -148,7 +157,8 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x) {
         const int z = t / (tm * tn), r = t % (tm * tn);
         const int m0 = (r / tn) * BM, n0 = (r % tn) * BN;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int q = 0; q < NPAIR * nk; ++q, ++g) {  // (split pair, K block)
+          const int kb = q % nk, za = pair_a(q / nk) * Z + z, zb = pair_b(q / nk) * Z + z;
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
           if (!mbar_wait(empty + s, ph ^ 1)) {
@@ -156,13 +166,13 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             break;
           }
           mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-          tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, z, full + s);
+          tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, za, full + s);
           if (BKMAJ) {
-            tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, z, full + s);
+            tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, zb, full + s);
           } else {
 #pragma unroll
             for (int bx = 0; bx < NBOX; ++bx)
-              tma_load_3d(sB + s * B_BYTES + bx * B_COL, &tmB, n0 + bx * NATOM, kb * BKE, z,
+              tma_load_3d(sB + s * B_BYTES + bx * B_COL, &tmB, n0 + bx * NATOM, kb * BKE, zb,
                           full + s);
           }
           issued = g + 1;
@@ -181,7 +191,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)(b * BN);
         bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++g) {
+        for (int q = 0; q < NPAIR * nk; ++q, ++g) {
           const int s = g % STAGES;
           const uint32_t ph = (g / STAGES) & 1;
           if (!mbar_wait(full + s, ph)) {
@@ -196,7 +206,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
             const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);
             const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
                                       : smem_desc(b0 + kk * UK * 128, B_COL, 1024);
-            umma<KIND>(acc, ad, bd, IDESC, (kb | kk) != 0);
+            umma<KIND>(acc, ad, bd, IDESC, (q | kk) != 0);
           }
           umma_commit(empty + s);
         }
@@ -341,7 +351,8 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 }  // namespace
 
 int umma_init() {
-  for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>}) {
+  for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>,
+                  k_umma_gemm<0, 0, false, 6>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes()));
     // two CTAs of 105 KB a SM need the largest shared-memory carveout
@@ -384,19 +395,21 @@ int make_tmap(CUtensorMap* map, const void* base, int bf16, int inner, int rows,
 // A operand: M x K per slice, K contiguous. B operand: K x N with N contiguous
 // (BF16), or its transpose N x K with K contiguous (TF32).
 int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, int N, int K,
-                   int slices) {
+                   int slices, int nsplit) {
   const int bf16 = kind == 0;
   const int bke = bf16 ? 64 : 32;
-  TC_TRY(make_tmap(&m->a, A, bf16, K, M, slices, bke, BM));
+  TC_CHECK(nsplit == 1 || (nsplit == 3 && bf16));
+  TC_TRY(make_tmap(&m->a, A, bf16, K, M, slices * nsplit, bke, BM));
   if (bf16)
-    TC_TRY(make_tmap(&m->b, B, bf16, N, K, slices, 64, bke));
+    TC_TRY(make_tmap(&m->b, B, bf16, N, K, slices * nsplit, 64, bke));
   else
-    TC_TRY(make_tmap(&m->b, B, bf16, K, N, slices, bke, BN));
+    TC_TRY(make_tmap(&m->b, B, bf16, K, N, slices * nsplit, bke, BN));
   m->M = M;
   m->N = N;
   m->K = K;
   m->slices = slices;
   m->kind = kind;
+  m->nsplit = nsplit;
   return TC_OK;
 }
 
@@ -410,7 +423,10 @@ unsigned grid_size(const UmmaMaps& m) {
 
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
   Epi none;
-  if (m.kind == 0)
+  if (m.nsplit == 3)
+    k_umma_gemm<0, 0, false, 6><<<grid_size(m), NT, smem_bytes(), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
+  else if (m.kind == 0)
     k_umma_gemm<0, 0, false><<<grid_size(m), NT, smem_bytes(), st>>>(
         m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
   else
@@ -422,7 +438,7 @@ int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStre
 
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st) {
-  TC_CHECK(m.kind == 0);
+  TC_CHECK(m.kind == 0 && m.nsplit == 1);
   k_umma_gemm<0, 0, true><<<grid_size(m), NT, smem_bytes(), st>>>(
       m.a, m.b, D, m.M, m.N, m.K, m.slices, err, ep.skip, ep, dlow);
   TC_CUDA(cudaGetLastError());

@@ -10,13 +10,16 @@ struct UmmaMaps {
   CUtensorMap a;  // M x K per slice, K contiguous (K-major operand)
   CUtensorMap b;  // BF16: K x N per slice (MN-major); TF32: N x K per slice (K-major)
   int M = 0, N = 0, K = 0, slices = 0, kind = 0;  // kind 0: BF16, 1: TF32
+  int nsplit = 1;  // 3: each operand is three stacked BF16 planes (FP32-level products)
 };
 
 int umma_init();
+// nsplit 3 (BF16 only): A and B hold three planes each, plane p of slice z at
+// slice p * slices + z.
 int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, int N, int K,
-                   int slices);
-// D_z = A_z B_z in FP32 for every slice; *err is set to TC_ETIMEOUT if a
-// bounded wait gives up.
+                   int slices, int nsplit = 1);
+// D_z = A_z B_z in FP32 for every slice (nsplit 3: the six split products);
+// *err is set to TC_ETIMEOUT if a bounded wait gives up.
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st);
 // BF16 maps only: the same GEMM with the Krylov epilogue in its store
 // (D = ca * acc + cp * ep.prev, the reduction ep.red of D, ep.skip) and, when

@@ -15,7 +15,7 @@ c_int, c_double, c_void_p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 
 TC_OK, TC_EINVAL, TC_ECUDA, TC_EBREAKDOWN, TC_ENONFINITE, TC_ETIMEOUT, TC_ENOMEM, \
     TC_EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
-TC_FP32, TC_TF32, TC_BF16 = 0, 1, 2
+TC_FP32, TC_TF32, TC_BF16, TC_BF16X3 = 0, 1, 2, 3
 TC_GCV_PAPER, TC_GCV_FULL = 0, 1
 TC_TH, TC_ORTHODCT = 0, 1
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",

@@ -100,7 +100,7 @@ def test_orthodct_lsqr_matches_oracle(tc, two):
     plan.close()
 
 
-@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16"])
+@pytest.mark.parametrize("precision", ["fp32", "tf32", "bf16", "bf16x3"])
 def test_transform_domain_lsqr(tc, precision):
     # ORTHODCT plans off the fused route (n3 > 4, or a tensor-core form)
     # iterate on dct(C) with slice GEMMs only and transform X, X_reg back at
@@ -114,7 +114,8 @@ def test_transform_domain_lsqr(tc, precision):
     Xt = w["X_true"]
     C = f32(inputs.scale_noise(op(Xt), w["G"], 1e-2)).astype(np.float64)
     ref = kr.lsqr_gcv(op, adj, C, itermax=15)
-    prec = {"fp32": tc.TC_FP32, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16}[precision]
+    prec = {"fp32": tc.TC_FP32, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16,
+            "bf16x3": tc.TC_BF16X3}[precision]
     plan = tc.Plan(dev(A), s=64, precision=prec, product=tc.TC_ORTHODCT)
     for _ in range(2):  # the second call replays the captured graph
         X, Xr, _, info = plan.lsqr(dev(C), 15, regularize=True)
@@ -122,7 +123,7 @@ def test_transform_domain_lsqr(tc, precision):
         assert tc.read_info(info)["iters"] == 15
         e_ref = rel(ref["X_reg"], Xt)
         e_gpu = rel(Xr.cpu().numpy(), Xt)
-        if precision == "fp32":
+        if precision in ("fp32", "bf16x3"):  # bf16x3: FP32-accurate products
             assert rel(X.cpu().numpy(), ref["X"]) < 1e-3
             assert abs(e_gpu - e_ref) <= 0.01 * e_ref
         else:
