@@ -32,6 +32,7 @@ sys.path.insert(0, ROOT)
 METRIC = "LSQR-c iters/s & solves/s at matched rel. error (BF16/TF32 vs FP32); % roofline"
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6800.0
+FALLBACK_BF16_TFLOPS = 1900.0  # profiling recipe fallback (burst), used without MEASURED_PEAKS.json
 # FP32 FFMA peak: 152 SMs x 128 FP32 lanes x 2 flop x clock (GB300 unit counts).
 FP32_LANES = 152 * 128
 
@@ -598,6 +599,15 @@ def run_gpu(args):
                     "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
                     "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
                                    f"({src_peaks} max clock)", "launch_ms": prod_ms}
+        elif args.precision == "bf16x3":  # six BF16 products per FP32-level product
+            peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / 6.0
+            roof = {"kernel": roof_kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / 6: each "
+                                   "FP32-level product is six BF16 products",
+                    "launch_ms": prod_ms, "algorithmic_flops": fl,
+                    "note": "its 268 MB at the measured HBM rate take 40 us at 512x512x64, "
+                            "less than the six products at the tensor rate"}
         else:  # tcgen05 GEMM: A~ and X~ in the input type read once, Y~ written in FP32
             es = {"bf16": 2, "bf16x3": 6}.get(args.precision, 4)
             gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
