@@ -37,7 +37,7 @@ namespace {
 
 using namespace tc5;
 
-constexpr int BM = 128, BN = 128, STAGES = 3;  // 105 KB smem: 2 CTAs per SM
+constexpr int BM = 128, BN = 128, STAGES = 3;  // 105 KB smem: 2 CTAs per SM (NPAIR 1)
 constexpr uint32_t A_BYTES = BM * 128;   // 128 rows of one 128-byte K slab
 constexpr uint32_t B_BYTES = 128 * BN;   // (128 / elem) K rows x BN columns
 
@@ -52,8 +52,15 @@ int g_nsm = 0;  // SMs of the device (persistent grid size: 2 CTAs per SM)
 // Without EPI the accumulator is stored as is.
 constexpr int NT = 192;  // warps 0, 1: producer, MMA; warps 2..5: epilogue
 
-size_t smem_bytes() {
-  return 1024 + STAGES * (A_BYTES + B_BYTES) + 4 * 32 * 16 * 4 + (2 * STAGES + 5) * 8 + 16;
+// Stages: three of one (A, B) K block (two CTAs a SM); for the split
+// products (NPAIR = 6), two of all three planes of both operands (96 KB a
+// stage, one CTA a SM), so each plane is loaded once per K block.
+__host__ __device__ constexpr int stage_planes(int npair) { return npair == 6 ? 3 : 1; }
+__host__ __device__ constexpr int stage_count(int npair) { return npair == 6 ? 2 : STAGES; }
+
+size_t smem_bytes(int npair = 1) {
+  const int pl = stage_planes(npair), ns = stage_count(npair);
+  return 1024 + ns * pl * (A_BYTES + B_BYTES) + 4 * 32 * 16 * 4 + (2 * ns + 5) * 8 + 16;
 }
 
 
@@ -67,7 +74,7 @@ __device__ __forceinline__ int pair_a(int p) { return p == 2 || p == 4 ? 1 : (p 
 __device__ __forceinline__ int pair_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
 
 template <int KIND, int BKMAJ, bool EPI, int NPAIR = 1>
-__global__ void __launch_bounds__(NT, 2)
+__global__ void __launch_bounds__(NT, NPAIR == 6 ? 1 : 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             float* D, int M, int N, int K, int Z, int* err, const int* skip, Epi ep,
             __nv_bfloat16* dlow) {
@@ -81,16 +88,18 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t BMAJ = BKMAJ ? 0u : 1u;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | (0u << 15) | (BMAJ << 16) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  constexpr int PL = stage_planes(NPAIR), NST = stage_count(NPAIR);
+  constexpr uint32_t SA = PL * A_BYTES, SB = PL * B_BYTES;  // one stage's A, B bytes
   if (skip && *skip) return;
   extern __shared__ uint8_t dsm_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sA = base;
-  uint8_t* sB = base + STAGES * A_BYTES;
-  float* sE = reinterpret_cast<float*>(sB + STAGES * B_BYTES);  // 4 warps x 32 x 16 floats
+  uint8_t* sB = base + NST * SA;
+  float* sE = reinterpret_cast<float*>(sB + NST * SB);  // 4 warps x 32 x 16 floats
   uint64_t* full = reinterpret_cast<uint64_t*>(sE + 4 * 32 * 16);
-  uint64_t* empty = full + STAGES;
-  uint64_t* accf = empty + STAGES;  // [2]: accumulator buffer ready for the epilogue
+  uint64_t* empty = full + NST;
+  uint64_t* accf = empty + NST;  // [2]: accumulator buffer ready for the epilogue
   uint64_t* acce = accf + 2;        // [2]: accumulator buffer drained by the epilogue
   uint64_t* fin = acce + 2;         // every MMA of this CTA completed
   uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
@@ -103,7 +112,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const int nk = (K + BKE - 1) / BKE;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < NST; ++s) {
       mbar_init(full + s, 1);
       mbar_init(empty + s, 1);
     }
@@ -157,23 +166,26 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
       for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x) {
         const int z = t / (tm * tn), r = t % (tm * tn);
         const int m0 = (r / tn) * BM, n0 = (r % tn) * BN;
-        for (int q = 0; q < NPAIR * nk; ++q, ++g) {  // (split pair, K block)
-          const int kb = q % nk, za = pair_a(q / nk) * Z + z, zb = pair_b(q / nk) * Z + z;
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % NST;
+          const uint32_t ph = (g / NST) & 1;
           if (!mbar_wait(empty + s, ph ^ 1)) {
             *vfail = 1;
             break;
           }
-          mbar_expect_tx(full + s, A_BYTES + B_BYTES);
-          tma_load_3d(sA + s * A_BYTES, &tmA, kb * BKE, m0, za, full + s);
-          if (BKMAJ) {
-            tma_load_3d(sB + s * B_BYTES, &tmB, kb * BKE, n0, zb, full + s);
-          } else {
+          mbar_expect_tx(full + s, SA + SB);
 #pragma unroll
-            for (int bx = 0; bx < NBOX; ++bx)
-              tma_load_3d(sB + s * B_BYTES + bx * B_COL, &tmB, n0 + bx * NATOM, kb * BKE, zb,
-                          full + s);
+          for (int pl = 0; pl < PL; ++pl) {  // operand plane pl: slice pl Z + z
+            const int zp = pl * Z + z;
+            tma_load_3d(sA + s * SA + pl * A_BYTES, &tmA, kb * BKE, m0, zp, full + s);
+            uint8_t* sb = sB + s * SB + pl * B_BYTES;
+            if (BKMAJ) {
+              tma_load_3d(sb, &tmB, kb * BKE, n0, zp, full + s);
+            } else {
+#pragma unroll
+              for (int bx = 0; bx < NBOX; ++bx)
+                tma_load_3d(sb + bx * B_COL, &tmB, n0 + bx * NATOM, kb * BKE, zp, full + s);
+            }
           }
           issued = g + 1;
         }
@@ -191,22 +203,26 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)(b * BN);
         bool ok = true;
-        for (int q = 0; q < NPAIR * nk; ++q, ++g) {
-          const int s = g % STAGES;
-          const uint32_t ph = (g / STAGES) & 1;
+        for (int kb = 0; kb < nk; ++kb, ++g) {
+          const int s = g % NST;
+          const uint32_t ph = (g / NST) & 1;
           if (!mbar_wait(full + s, ph)) {
             *vfail = 1;
             ok = false;
             break;
           }
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t a0 = su32(sA + s * A_BYTES), b0 = su32(sB + s * B_BYTES);
 #pragma unroll
-          for (int kk = 0; kk < BKE / UK; ++kk) {
-            const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);
-            const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
-                                      : smem_desc(b0 + kk * UK * 128, B_COL, 1024);
-            umma<KIND>(acc, ad, bd, IDESC, (q | kk) != 0);
+          for (int pr = 0; pr < NPAIR; ++pr) {  // product of planes (pair_a, pair_b)
+            const uint32_t a0 = su32(sA + s * SA + pair_a(pr) * A_BYTES);
+            const uint32_t b0 = su32(sB + s * SB + pair_b(pr) * B_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < BKE / UK; ++kk) {
+              const uint64_t ad = smem_desc(a0 + kk * UK * ES, 16, 1024);
+              const uint64_t bd = BKMAJ ? smem_desc(b0 + kk * UK * ES, 16, 1024)
+                                        : smem_desc(b0 + kk * UK * 128, B_COL, 1024);
+              umma<KIND>(acc, ad, bd, IDESC, (kb | pr | kk) != 0);
+            }
           }
           umma_commit(empty + s);
         }
@@ -336,8 +352,8 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   const bool failed = *vfail != 0;
   if (warp == 1 && lane == 0) mbar_wait(fin, 0);  // the MMAs have finished with TMEM
   if (failed && warp == 0 && lane == 0) {          // let the copies this CTA issued land
-    for (int g = (issued > STAGES ? issued - STAGES : 0); g < issued; ++g)
-      mbar_wait(full + g % STAGES, (g / STAGES) & 1);
+    for (int g = (issued > NST ? issued - NST : 0); g < issued; ++g)
+      mbar_wait(full + g % NST, (g / NST) & 1);
     atomicExch(err, TC_ETIMEOUT);
   }
   if (EPI && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
@@ -353,9 +369,10 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 int umma_init() {
   for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>,
                   k_umma_gemm<0, 0, false, 6>}) {
+    const int npair = fn == k_umma_gemm<0, 0, false, 6> ? 6 : 1;
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem_bytes()));
-    // two CTAs of 105 KB a SM need the largest shared-memory carveout
+                                 (int)smem_bytes(npair)));
+    // two CTAs of 105 KB (or one of 201 KB) a SM need the largest carveout
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
   }
@@ -416,7 +433,7 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
 namespace {
 unsigned grid_size(const UmmaMaps& m) {
   const long tiles = (long)((m.N + BN - 1) / BN) * ((m.M + BM - 1) / BM) * m.slices;
-  const long cap = 2L * (g_nsm > 0 ? g_nsm : 152);
+  const long cap = (m.nsplit == 3 ? 1L : 2L) * (g_nsm > 0 ? g_nsm : 152);  // CTAs a SM
   return (unsigned)(tiles < cap ? tiles : cap);
 }
 }  // namespace
@@ -424,7 +441,7 @@ unsigned grid_size(const UmmaMaps& m) {
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
   Epi none;
   if (m.nsplit == 3)
-    k_umma_gemm<0, 0, false, 6><<<grid_size(m), NT, smem_bytes(), st>>>(
+    k_umma_gemm<0, 0, false, 6><<<grid_size(m), NT, smem_bytes(6), st>>>(
         m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
   else if (m.kind == 0)
     k_umma_gemm<0, 0, false><<<grid_size(m), NT, smem_bytes(), st>>>(
