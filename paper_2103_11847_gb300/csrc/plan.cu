@@ -351,16 +351,16 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
     const void* bop = bf16 ? lowop(p) : (const void*)p->tmp3;
     TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3, ns));
     TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3, ns));
-    if (p->opts.precision == TC_BF16 && p->opts.product == TC_ORTHODCT) {
+    if (bf16 && p->opts.product == TC_ORTHODCT) {
       // transform-domain LSQR with the epilogue in the GEMM: each product's
       // store also writes the BF16 operand of the next one, so the forward and
       // adjoint GEMMs read separate buffers (bV: V~, n2 x s; bU: U~, n1 x s)
-      TC_CUDA(cudaMalloc(&p->lowV, (size_t)n2 * s * n3 * 2));
-      TC_CUDA(cudaMalloc(&p->lowU, (size_t)n1 * s * n3 * 2));
+      TC_CUDA(cudaMalloc(&p->lowV, (size_t)n2 * s * n3 * 2 * ns));
+      TC_CUDA(cudaMalloc(&p->lowU, (size_t)n1 * s * n3 * 2 * ns));
       p->umf_td = new UmmaMaps();
       p->uma_td = new UmmaMaps();
-      TC_TRY(make_umma_maps(p->umf_td, 0, p->AhL, p->lowV, n1, s, n2, n3));
-      TC_TRY(make_umma_maps(p->uma_td, 0, p->AhTL, p->lowU, n2, s, n1, n3));
+      TC_TRY(make_umma_maps(p->umf_td, 0, p->AhL, p->lowV, n1, s, n2, n3, ns));
+      TC_TRY(make_umma_maps(p->uma_td, 0, p->AhTL, p->lowU, n2, s, n1, n3, ns));
     }
   }
   TC_TRY(dalloc(&p->scratch.partials, np));

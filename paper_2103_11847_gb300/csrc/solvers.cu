@@ -184,7 +184,9 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   // BF16 plans with fused epilogues keep the GEMM operands as BF16 copies that
   // each product's store writes for the next one; the first is bf16(C~).
   const bool tdf = td && p->umf_td != nullptr;
-  if (tdf) TC_TRY(launch_round(Cin, p->lowU, p->Ty, 1, st));
+  if (tdf)
+    TC_TRY(launch_round(Cin, p->lowU, p->Ty,
+                        p->opts.precision == TC_BF16X3 ? ROUND_BF16X3 : ROUND_BF16, st));
   auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
     if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
     if (step) TC_TRY(launch_lsqr_update(*step, st));

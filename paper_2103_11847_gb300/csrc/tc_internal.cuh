@@ -124,7 +124,7 @@ struct tc_plan {
   UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
   UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
   void* lowX = nullptr;           // TC_BF16X3 plans: the GEMM operand as three BF16 planes
-  void* lowV = nullptr;           // BF16 ORTHODCT plans: bf16(V~) and bf16(U~), the operands
+  void* lowV = nullptr;           // BF16/BF16X3 ORTHODCT plans: bf16(V~) and bf16(U~) (three planes for BF16X3), the operands
   void* lowU = nullptr;           // of the transform-domain GEMMs with fused epilogues
   UmmaMaps* umf_td = nullptr;     // A~ times lowV
   UmmaMaps* uma_td = nullptr;     // A~^T times lowU

@@ -91,6 +91,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr int PL = stage_planes(NPAIR), NST = stage_count(NPAIR);
   constexpr uint32_t SA = PL * A_BYTES, SB = PL * B_BYTES;  // one stage's A, B bytes
   if (skip && *skip) return;
+  const size_t zmn = (size_t)Z * M * N;  // values of one output plane
   extern __shared__ uint8_t dsm_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(dsm_raw) + 1023) & ~(uintptr_t)1023);
@@ -312,13 +313,21 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
               }
             }
             *reinterpret_cast<float4*>(D + o) = y;
-            if (EPI && dlow) {
-              __nv_bfloat162 lo = __floats2bfloat162_rn(y.x, y.y);
-              __nv_bfloat162 hi = __floats2bfloat162_rn(y.z, y.w);
-              uint2 pk;
-              pk.x = *reinterpret_cast<uint32_t*>(&lo);
-              pk.y = *reinterpret_cast<uint32_t*>(&hi);
-              *reinterpret_cast<uint2*>(dlow + o) = pk;
+            if (EPI && dlow) {  // PL planes of the next operand, Z M N values apart
+              float4 r = y;
+#pragma unroll
+              for (int pl = 0; pl < PL; ++pl) {
+                const __nv_bfloat162 lo = __floats2bfloat162_rn(r.x, r.y);
+                const __nv_bfloat162 hi = __floats2bfloat162_rn(r.z, r.w);
+                uint2 pk;
+                pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+                pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+                *reinterpret_cast<uint2*>(dlow + pl * zmn + o) = pk;
+                r.x -= __low2float(lo);
+                r.y -= __high2float(lo);
+                r.z -= __low2float(hi);
+                r.w -= __high2float(hi);
+              }
             }
           } else {  // ragged row length: element by element
             const float ys[4] = {y.x, y.y, y.z, y.w};
@@ -330,7 +339,15 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (ep.red.out) local = fmaf(w, ep.red.other ? ep.red.other[o + e] : w, local);
               }
               D[o + e] = w;
-              if (EPI && dlow) dlow[o + e] = __float2bfloat16_rn(w);
+              if (EPI && dlow) {
+                float r = w;
+#pragma unroll
+                for (int pl = 0; pl < PL; ++pl) {
+                  const __nv_bfloat16 b = __float2bfloat16_rn(r);
+                  dlow[pl * zmn + o + e] = b;
+                  r -= __bfloat162float(b);
+                }
+              }
             }
           }
         }
@@ -368,8 +385,9 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
 int umma_init() {
   for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>,
-                  k_umma_gemm<0, 0, false, 6>}) {
-    const int npair = fn == k_umma_gemm<0, 0, false, 6> ? 6 : 1;
+                  k_umma_gemm<0, 0, false, 6>, k_umma_gemm<0, 0, true, 6>}) {
+    const int npair =
+        (fn == k_umma_gemm<0, 0, false, 6> || fn == k_umma_gemm<0, 0, true, 6>) ? 6 : 1;
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem_bytes(npair)));
     // two CTAs of 105 KB (or one of 201 KB) a SM need the largest carveout
@@ -455,9 +473,13 @@ int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStre
 
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st) {
-  TC_CHECK(m.kind == 0 && m.nsplit == 1);
-  k_umma_gemm<0, 0, true><<<grid_size(m), NT, smem_bytes(), st>>>(
-      m.a, m.b, D, m.M, m.N, m.K, m.slices, err, ep.skip, ep, dlow);
+  TC_CHECK(m.kind == 0);
+  if (m.nsplit == 3)
+    k_umma_gemm<0, 0, true, 6><<<grid_size(m), NT, smem_bytes(6), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, ep.skip, ep, dlow);
+  else
+    k_umma_gemm<0, 0, true><<<grid_size(m), NT, smem_bytes(), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, ep.skip, ep, dlow);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

@@ -23,6 +23,7 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
 int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st);
 // BF16 maps only: the same GEMM with the Krylov epilogue in its store
 // (D = ca * acc + cp * ep.prev, the reduction ep.red of D, ep.skip) and, when
-// dlow is non-null, a BF16 copy of D written beside it.
+// dlow is non-null, a BF16 copy of D written beside it (nsplit 3: its three
+// planes, plane q at dlow + q slices M N).
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st);
