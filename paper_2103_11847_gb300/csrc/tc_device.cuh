@@ -4,6 +4,29 @@
 
 #include "tc_internal.cuh"
 
+// FP64 reciprocal and inverse square root by Newton's method from the
+// hardware estimates: y <- y (2 - x y) and y <- y (3/2 - x y^2 / 2), each step
+// doubling the correct bits. A few dependent FMAs, where the IEEE division
+// and square root are long sequences on this part's scarce FP64 units.
+// Results are within a few ulp of the correctly rounded ones.
+__device__ __forceinline__ double rcp_newton(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
+__device__ __forceinline__ double rsqrt_newton(double x) {  // x > 0, finite
+  double y;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  const double h = 0.5 * x;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) y = y * fma(-h * y, y, 1.5);
+  return y;
+}
+
 // (ca, cp) of the epilogue rule, computed by thread 0 in FP64 and broadcast.
 // A zero denominator gives a zero coefficient: that is how a Golub-Kahan
 // breakdown (beta or alpha = 0) produces a zero tensor instead of Inf/NaN.
@@ -14,13 +37,13 @@ __device__ __forceinline__ void coef_compute(const Coef& c, float* sh2) {
       case COEF_RESID: ca = -1.0; cp = 1.0; break;
       case COEF_GK: {
         double s0 = *c.s0, s1 = *c.s1;
-        ca = (s0 != 0.0) ? 1.0 / s0 : 0.0;
-        cp = (s1 != 0.0) ? -s0 / s1 : 0.0;
+        ca = (s0 != 0.0) ? rcp_newton(s0) : 0.0;
+        cp = (s1 != 0.0) ? -s0 * rcp_newton(s1) : 0.0;
         break;
       }
       case COEF_INV: {
         double s0 = *c.s0;
-        ca = (s0 != 0.0) ? 1.0 / s0 : 0.0;
+        ca = (s0 != 0.0) ? rcp_newton(s0) : 0.0;
         break;
       }
       case COEF_NEG: ca = -1.0; break;
@@ -114,8 +137,10 @@ __device__ __forceinline__ bool lsqr_step_scalars(const LsqrStep& u, float* sh, 
   const int j = u.j;
   const double b = u.beta[j + 1], a = u.alpha[j + 1];
   const double rb = u.rhobar[j], pb = u.phibar[j];
-  const double rho = hypot(rb, b);
-  const double irho = 1.0 / rho;
+  const double r2 = fma(rb, rb, b * b);
+  const bool plain = r2 > 0.0 && r2 < 1e300;  // else the IEEE path: zeros, Inf, NaN
+  const double irho = plain ? rsqrt_newton(r2) : 1.0 / hypot(rb, b);
+  const double rho = plain ? r2 * irho : hypot(rb, b);
   const double c = rb * irho, s = b * irho;
   const double theta = s * a;
   const double phi = c * pb;
@@ -124,7 +149,7 @@ __device__ __forceinline__ bool lsqr_step_scalars(const LsqrStep& u, float* sh, 
   const bool brk = (a == 0.0);
   const bool conv = fabs(pbn) < u.tol || (u.stop_at && *u.stop_at > 0 && j + 1 >= *u.stop_at);
   sh[0] = (float)(phi * irho);
-  sh[1] = brk ? 0.f : (float)(1.0 / a);
+  sh[1] = brk ? 0.f : (float)rcp_newton(a);
   sh[2] = (float)(theta * irho);
   const bool stop = brk || conv || !finite;
   if (writer) {
