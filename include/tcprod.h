@@ -308,6 +308,16 @@ int tc_tikhonov_gcv(const double* H, int k, const double* beta, int variant,
  * Each call clears the array's arrival counter on `stream` before its kernel. */
 int tc_fro_norm_noalloc(const float* X, size_t n, double* out, tc_stream_t stream);
 
+/* Self-check of the bounded-wait path. Every wait in the tensor-core kernels
+ * polls an mbarrier a bounded number of times and, if the copies or MMAs it
+ * waits for never arrive, reports TC_ETIMEOUT (in the plan's error status or
+ * tc_solve_info) instead of hanging the GPU. This call runs one such wait on a
+ * barrier that nothing arrives on and writes the outcome to *status.
+ *   spins: 1 .. 2^20 polls.  status: device int, written with TC_ETIMEOUT
+ *   (TC_OK would mean the wait completed, which it cannot).
+ * No fault or trap is involved; the context stays usable. */
+int tc_check_bounded_wait(int spins, int* status, tc_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,10 +35,16 @@ __device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-  for (int i = 0; i < kSpin; ++i)
+// Polls the phase of parity `parity` at most `spins` times; false if it has
+// not completed by then (the caller reports TC_ETIMEOUT instead of hanging).
+__device__ __forceinline__ bool mbar_wait_n(uint64_t* bar, uint32_t parity, int spins) {
+  for (int i = 0; i < spins; ++i)
     if (mbar_try(bar, parity)) return true;
   return false;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  return mbar_wait_n(bar, parity, kSpin);
 }
 
 __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int c0, int c1,

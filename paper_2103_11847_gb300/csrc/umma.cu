@@ -383,6 +383,30 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
 
 }  // namespace
 
+namespace {
+// One bounded wait on an mbarrier that nothing arrives on: the phase of
+// parity 0 never completes, so the wait gives up after `spins` polls and the
+// status is TC_ETIMEOUT. This is the path every wait of the tcgen05 kernels
+// takes when its copies or MMAs do not arrive.
+__global__ void k_wait_check(int spins, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const bool done = mbar_wait_n(&bar, 0, spins);
+  if (threadIdx.x == 0) *status = done ? TC_OK : TC_ETIMEOUT;
+}
+}  // namespace
+
+extern "C" int tc_check_bounded_wait(int spins, int* status, tc_stream_t stream) {
+  if (!status || spins < 1 || spins > (1 << 20)) return TC_EINVAL;
+  k_wait_check<<<1, 32, 0, (cudaStream_t)stream>>>(spins, status);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 int umma_init() {
   for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>,
                   k_umma_gemm<0, 0, false, 6>, k_umma_gemm<0, 0, true, 6>}) {

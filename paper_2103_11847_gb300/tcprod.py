@@ -54,6 +54,7 @@ _SIGS = {
     "tc_tikhonov_gcv": ([c_void_p, c_int, c_void_p, c_int, c_double, c_void_p, c_void_p,
                          c_void_p, c_void_p], c_int),
     "tc_fro_norm_noalloc": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p], c_int),
+    "tc_check_bounded_wait": ([c_int, c_void_p, c_void_p], c_int),
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
     "tc_batch_create": ([ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int),
                          ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
@@ -220,6 +221,13 @@ def tc_fro_norm_noalloc(X, out, stream=None):
     """||X||_F into the device double `out`, using no device allocation."""
     _check("tc_fro_norm_noalloc", lib().tc_fro_norm_noalloc(
         _ptr(X, name="X"), X.numel(), _ptr(out, torch.float64, name="out"), _stream(stream)))
+
+
+def tc_check_bounded_wait(spins, status, stream=None):
+    """One bounded mbarrier wait that cannot complete; writes TC_ETIMEOUT to
+    the device int32 `status`."""
+    _check("tc_check_bounded_wait", lib().tc_check_bounded_wait(
+        int(spins), _ptr(status, torch.int32, name="status"), _stream(stream)))
 
 
 def _ptr_array(ts, name):
