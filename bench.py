@@ -366,17 +366,24 @@ def learned_form(train_count=20000):
     return out
 
 
+def source_digest(paths):
+    """sha256 over the concatenated bytes of the given repository files."""
+    import hashlib
+    h = hashlib.sha256()
+    for rel in paths:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def captured_traffic(kernel):
     """DRAM bytes per launch of `kernel` from the committed ncu capture
-    (profiles/traffic.json), or None once the kernel's source no longer
-    hashes to the captured version."""
-    import hashlib
+    (profiles/traffic.json), or None once any source the kernel is built from
+    no longer hashes to the captured version."""
     try:
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "profiles",
-                               "traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
-        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), rec["source"]), "rb") as f:
-            digest = hashlib.sha256(f.read()).hexdigest()
+        digest = source_digest(rec["sources"])
     except (OSError, ValueError, TypeError, KeyError):
         return None
     return rec["dram_bytes_per_launch"] if digest == rec["sha256"] else None
