@@ -148,19 +148,13 @@ k_tikhonov_gcv(const double* __restrict__ H, int ld, int kmax, const int* kdev,
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    double smax = 0.0, smin = 1e308, gs = 0.0;
-    for (int i = 0; i < k; ++i) {
-      smax = fmax(smax, sig[i]);
-      smin = fmin(smin, sig[i]);
-      gs += g[i] * g[i];
-    }
-    sh_misc[0] = smax;
-    sh_misc[1] = smin;
+  if (tid == 0) {  // the part of beta e1 outside the range of H
+    double gs = 0.0;
+    for (int i = 0; i < k; ++i) gs += g[i] * g[i];
     sh_misc[2] = fmax(beta * beta - gs, 0.0);
   }
   __syncthreads();
-  const double smax = sh_misc[0], smin = sh_misc[1], gnull2 = sh_misc[2];
+  const double gnull2 = sh_misc[2];
 
   // ---- 2. lambda -------------------------------------------------------------
   double lam = lambda_in;
