@@ -486,6 +486,19 @@ def dist_env():
     return rank, local, world
 
 
+def replica_throughput(total_ms, steps, iters, world, device):
+    """The slowest rank's timed region (max over ranks) and the whole-job value:
+    the LSQR iterations every rank ran, over that time. Each rank solves its
+    own problem (replicas), so this max is the only collective."""
+    import torch
+    t_max = float(total_ms)
+    if world > 1:
+        t = torch.tensor([t_max], device=device, dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(t.item())
+    return t_max, world * steps * iters / (t_max / 1000.0)
+
+
 def run_gpu(args):
     import torch
     from paper_2103_11847_gb300 import tcprod
@@ -588,12 +601,7 @@ def run_gpu(args):
     e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
     inf = tcprod.read_info(info)
 
-    t_max = total_ms
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * args.steps * iters / (t_max / 1000.0)
+    t_max, value = replica_throughput(total_ms, args.steps, iters, world, dev)
     if rank == 0:
         peaks, src_peaks = load_peaks()
         sm_max = peaks.get("sm_max_mhz", 2070.0)
