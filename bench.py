@@ -4,11 +4,14 @@ A step is one whole solve: itermax c-LSQR iterations (Algorithm 6) on one
 observed tensor, then GCV on the projected bidiagonal and X_reg = V_k (*) y
 (Algorithm 5's projection), all on the GPU, replayed as one CUDA graph.
 
-Default workload: two-sided A *c X *c B, 256 x 256 x 3, Gaussian blurs
-(sigma 3 and 2, half-band 8), noise 1e-3, 50 iterations.
+Default workload (the precision form): a 512 x 512 x 64 video, frame k blurred
+by its own Gaussian Toeplitz matrix (sigma 1.5 -> 3.5), noise 1e-3, 50
+iterations, slice GEMMs in BF16 with FP32 accumulation; the FP32, TF32 and
+FP32-level (BF16X3) forms run beside it, and the reported form must match the
+FP32 form's reconstruction error within 2 %.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tcprod|reference]
-                  [--workload two_sided_256|colour_64|video_512]
+                  [--workload video_512|two_sided_256|colour_64] [--precision ...]
 
 Prints one JSON line (rank 0). Under torchrun each rank solves its own
 replica (independent problems, no collective on the data path): "weak"
@@ -43,6 +46,10 @@ WORKLOADS = {
 }
 
 
+# Iterations in one bounded oracle sample (about 10-30 s of host work).
+CPU_SAMPLE = {"video_512": 2, "two_sided_256": 10, "colour_64": 30}
+
+
 def make_problem(name):
     from paper_2103_11847_gb300 import inputs
     w = WORKLOADS[name]
@@ -60,27 +67,6 @@ def product_flops(n1, n2, s, n3, two_sided):
     if two_sided:
         f += 2.0 * n1 * s * s * n3
     return f
-
-
-def lsqr_kernel_launches(iters, two_sided, fused, keep_basis=True, precision="fp32", s=0, n3=64):
-    """Kernels one solve launches (mirrors the schedule in csrc/solvers.cu).
-    A fused product is one launch, except two-sided with s > 256 (two)."""
-    if fused:
-        per_product = 2 if (two_sided and s > 256) else 1
-    else:
-        per_product = 4 if two_sided else 3
-    if precision != "fp32":  # transform, [transpose for TF32], tcgen05 GEMM, transform back
-        per_product = 4 if precision == "tf32" else 3
-        if precision == "bf16x3" and n3 <= 32:  # FP32 transform pass, then the three planes
-            per_product = 4
-    init = 1 + per_product + 1 + (1 if keep_basis else 0) + 1
-    # product, adjoint, and the LSQR step: inside the next product on the
-    # two-sided fused route (s <= 256), else its own launch; the last step
-    # always has its own launch
-    inside = fused and two_sided and s <= 256 and precision == "fp32"
-    per_iter = 2 * per_product + (0 if inside else 1)
-    tail = (1 if inside else 0) + (5 if keep_basis else 0) + 1  # GCV levels, final, combine; info
-    return init + iters * per_iter + tail
 
 
 class ClockSampler:
@@ -141,10 +127,10 @@ def load_peaks():
 
 # ------------------------------------------------------------- CPU oracle ----
 
-def cpu_worker(workload, budget_s):
-    """Time the FP64 oracle's c-LSQR on this host (run in a child process)."""
+def oracle_problem(workload):
+    """The workload's FP32 inputs as FP64 arrays and the oracle's operator:
+    (op, adj, C) with C = op(X_true) + N formed by the oracle."""
     from oracle import cproduct as cp
-    from oracle import krylov as kr
     from paper_2103_11847_gb300 import inputs
     w = make_problem(workload)
     A = w["A"].astype(np.float32).astype(np.float64)
@@ -152,31 +138,66 @@ def cpu_worker(workload, budget_s):
     op = lambda X: cp.cprod(A, X, B)
     adj = lambda Y: cp.cprod_adjoint(A, Y, B)
     C = inputs.scale_noise(op(w["X_true"]), w["G"], w["nu"]).astype(np.float32).astype(np.float64)
-    iters = WORKLOADS[workload]["iters"]
-    sample = max(2, min(iters, 10))
-    kr.lsqr(op, adj, C, itermax=2)  # warm-up
-    done, t0 = 0, time.perf_counter()
-    while True:
+    return op, adj, C
+
+
+def cpu_worker(workload, sample, steps, budget_s):
+    """Time the FP64 oracle's c-LSQR on this host (run in a child process):
+    `steps` runs of `sample` iterations from X_0 = 0 (each run includes the
+    start-up product and norms, as a GPU solve does), stopping early once
+    `budget_s` seconds have gone. Prints the per-run times and the CPU time
+    the process used over them (its threads' user + system time)."""
+    import resource
+    from oracle import krylov as kr
+    op, adj, C = oracle_problem(workload)
+    times = []
+    r0 = resource.getrusage(resource.RUSAGE_SELF)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        t = time.perf_counter()
         kr.lsqr(op, adj, C, itermax=sample)
-        done += sample
-        el = time.perf_counter() - t0
-        if el > budget_s:
+        times.append(time.perf_counter() - t)
+        if time.perf_counter() - t0 > budget_s:
             break
-    print(json.dumps({"iters": done, "seconds": el, "sample_iters": sample}))
+    wall = time.perf_counter() - t0
+    r1 = resource.getrusage(resource.RUSAGE_SELF)
+    cpu = (r1.ru_utime - r0.ru_utime) + (r1.ru_stime - r0.ru_stime)
+    print(json.dumps({"times": times, "sample_iters": sample, "wall": wall, "cpu": cpu}))
 
 
-def cpu_baseline(workload, budget_s=12.0):
-    cores = len(os.sched_getaffinity(0))
-    env = dict(os.environ, OMP_NUM_THREADS=str(cores), OPENBLAS_NUM_THREADS=str(cores),
-               MKL_NUM_THREADS=str(cores), CUDA_VISIBLE_DEVICES="")
+def cpu_run(workload, sample, steps, budget_s, threads=None):
+    """Run cpu_worker in a child process with `threads` BLAS/OpenMP threads
+    (default: every core this process may run on)."""
+    avail = len(os.sched_getaffinity(0))
+    n = threads or avail
+    env = dict(os.environ, OMP_NUM_THREADS=str(n), OPENBLAS_NUM_THREADS=str(n),
+               MKL_NUM_THREADS=str(n), CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-worker", workload,
+                        "--cpu-sample", str(sample), "--cpu-steps", str(steps),
                         "--cpu-budget", str(budget_s)], capture_output=True, text=True, env=env,
-                       timeout=600)
+                       timeout=1800)
+    if r.returncode != 0:
+        raise RuntimeError(f"oracle worker failed: {r.stderr[-2000:]}")
     out = json.loads(r.stdout.strip().splitlines()[-1])
-    value = out["iters"] / out["seconds"]
-    return {"value": value, "unit": "LSQR iterations/s", "cores": cores, "kind": "oracle",
-            "sample": (f"{out['iters']} c-LSQR iterations of the {workload} workload in runs of "
-                       f"{out['sample_iters']} (FP64 NumPy oracle, {out['seconds']:.1f} s)")}
+    out["threads_allowed"] = n
+    out["cores_available"] = avail
+    # cores the oracle kept busy: its CPU time over the wall time of the runs
+    out["cores_used"] = max(1, int(round(out["cpu"] / max(out["wall"], 1e-9))))
+    return out
+
+
+def cpu_baseline(workload, sample=None):
+    """The FP64 oracle as it stands on this host's cores: one run of `sample`
+    c-LSQR iterations of the workload (the bounded sample), iterations/s."""
+    sample = sample or CPU_SAMPLE.get(workload, 2)
+    out = cpu_run(workload, sample, 1, 0.0)
+    t = out["times"][0]
+    return {"value": sample / t, "unit": "LSQR iterations/s", "cores": out["cores_used"],
+            "cores_available": out["cores_available"], "kind": "oracle",
+            "sample": (f"one c-LSQR run of {sample} iterations from X_0 = 0 on the {workload} "
+                       f"workload, start-up product and norms included (FP64 NumPy oracle, "
+                       f"{t:.1f} s, {out['cpu']:.1f} s of CPU time on {out['cores_available']} "
+                       f"available cores)")}
 
 
 # ---------------------------------------------------------------- GPU arm ----
@@ -499,6 +520,110 @@ def replica_throughput(total_ms, steps, iters, world, device):
     return t_max, world * steps * iters / (t_max / 1000.0)
 
 
+def lsqr_floor_bytes(n1, n2, s, n3, precision, two_sided):
+    """Algorithmic HBM bytes of one c-LSQR iteration on the fused schedule,
+    2 T_A + 11 T: each product reads A~ (T_A, in the GEMM input type) and two
+    tensors and writes one; the update reads X, W, V~ and writes X, W. T is
+    one FP32 tensor of the larger of the two shapes."""
+    T = 4.0 * max(n1, n2) * s * n3
+    ea = {"fp32": 4, "tf32": 4, "bf16": 2, "bf16x3": 6}[precision]
+    TA = ea * n1 * n2 * n3 + (ea * s * s * n3 if two_sided else 0)
+    return 2 * TA + 11 * T
+
+
+def dominant_kernel(plan, args, dims, dev):
+    """The kernel that takes the largest share of the workload's solve, as a
+    callable that launches it once on the current stream with the operands
+    it has inside the solve, and its algorithmic work per launch.
+
+    * TF32/BF16/BF16X3 plans with n3 > 32: the tcgen05 transform pass back to
+      the spatial domain with the Krylov epilogue (k_tube, FP32 out): it reads
+      the slice-GEMM result and prev and writes the output (3 T bytes) and
+      reduces its norm. Two launches an iteration.
+    * FP32 plans with n3 <= 4: the fused product (k_cprod2 for the two-sided
+      product with s <= 256, else k_fused_gemm), FFMA-bound.
+    * Otherwise: the slice GEMMs of one product (tc_slice_gemm)."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    n1, n2, s, n3, two = dims
+    prec = args.precision
+    if prec != "fp32" and n3 > 32:
+        P = n1 * s
+        Yh = torch.randn((n3, n1, s), device=dev)
+        prev = torch.randn((n3, n1, s), device=dev)
+        out = torch.empty((n3, n1, s), device=dev)
+        ss = torch.zeros(1, dtype=torch.float64, device=dev)
+        name = ("k_tube<OUT_F32, 3> (tcgen05 mode-3 transform M^-1, three-plane split, with the "
+                "Krylov epilogue and norm)" if prec == "bf16x3" else
+                "k_tube<OUT_F32, 2> (tcgen05 mode-3 transform M^-1 with the Krylov epilogue "
+                "and norm)")
+        call = lambda: tcprod.tc_transform(plan.handle, tcprod.TC_MINV, Yh, out, prev, ss)
+        return dict(kernel=name, call=call, bound="hbm", work=3 * 4.0 * n3 * P,
+                    traffic_key="k_tube_f32", reps=50)
+    fl = product_flops(n1, n2, s, n3, two)
+    if n3 <= 4 and prec == "fp32":
+        src = torch.randn((n3, n2, s), device=dev)
+        dst = torch.empty((n3, n1, s), device=dev)
+        name = ("k_cprod2 (the whole two-sided product, one launch)" if two and s <= 256
+                else "k_fused_gemm (the GEMM stages of one c-product)")
+        return dict(kernel=name, call=lambda: tcprod.tc_cprod(plan.handle, src, dst), bound="alu",
+                    work=fl, traffic_key="k_cprod2" if two and s <= 256 else None, reps=200)
+    lowp_dt = torch.bfloat16 if prec in ("bf16", "bf16x3") else torch.float32
+    planes = 3 if prec == "bf16x3" else 1
+    src = torch.randn((planes * n3, n2, s), device=dev).to(lowp_dt)
+    dst = torch.empty((n3, n1, s), device=dev)
+    name = ("k_umma_gemm (tcgen05 slice GEMMs of one product"
+            + (", six split-BF16 products)" if planes == 3 else ")")
+            if prec != "fp32" else "k_slice_gemm (FFMA slice GEMMs of one product)")
+    es = {"bf16": 2, "bf16x3": 6}.get(prec, 4)
+    return dict(kernel=name, call=lambda: tcprod.tc_slice_gemm(plan.handle, src, dst),
+                bound="tensor" if prec == "bf16x3" else "hbm", flops=fl,
+                work=fl if prec == "bf16x3" else (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4,
+                traffic_key=None, reps=50)
+
+
+def roofline_line(dk, ms, peaks, src_peaks):
+    """roofline object of the JSON line for the dominant kernel `dk` whose
+    average launch took `ms` milliseconds."""
+    if dk["bound"] == "hbm":
+        peak = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+        ach = dk["work"] / (ms * 1e-3) / 1e9
+        unit, psrc = "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({src_peaks}, burst copy)"
+        extra = {"algorithmic_bytes": dk["work"]}
+    elif dk["bound"] == "tensor":  # six BF16 products per FP32-level product
+        peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / 6.0
+        ach = dk["work"] / (ms * 1e-3) / 1e12
+        unit = "TFLOP/s"
+        psrc = f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / 6: six BF16 products each"
+        extra = {"algorithmic_flops": dk["work"]}
+    else:
+        fp = measured_peak("fp32_ffma_tflops")
+        if fp is not None:
+            peak, psrc = fp, "profiles/peaks.json fp32_ffma_tflops (measured FFMA loop)"
+        else:
+            sm_max = peaks.get("sm_max_mhz", 2070.0)
+            peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12
+            psrc = f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz (unit count x max clock)"
+        ach = dk["work"] / (ms * 1e-3) / 1e12
+        unit = "TFLOP/s"
+        extra = {"algorithmic_flops": dk["work"]}
+    traffic = captured_traffic(dk["traffic_key"]) if dk.get("traffic_key") else None
+    r = {"kernel": dk["kernel"], "bound": dk["bound"], "achieved": ach, "peak": peak,
+         "unit": unit, "frac": ach / peak, "traffic": traffic, "peak_source": psrc,
+         "launch_ms": ms}
+    r.update(extra)
+    return r
+
+
+def measured_peak(key):
+    """A peak this repository measured (profiles/peaks.json), or None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "peaks.json")) as f:
+            return float(json.load(f)[key])
+    except (OSError, ValueError, KeyError, TypeError):
+        return None
+
+
 def run_gpu(args):
     import torch
     from paper_2103_11847_gb300 import tcprod
@@ -538,6 +663,7 @@ def run_gpu(args):
     for _ in range(max(args.warmup, 3)):
         solve()
     torch.cuda.synchronize()
+    kernels_per_solve = tcprod.tc_lsqr_graph_kernels(plan.handle)
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -558,28 +684,10 @@ def run_gpu(args):
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = sum(step_ms)
 
-    # dominant kernel, timed alone on the stream. n3 <= 4 (FP32): the fused
-    # product launches (one for the two-sided product with s <= 256), timed
-    # through tc_cprod. Otherwise: the slice GEMMs of one product (tc_slice_gemm).
-    fl = product_flops(n1, n2, s, n3, two)
-    reps = 200
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    if n3 <= 4 and args.precision == "fp32":
-        roof_kernel = ("k_cprod2 (the whole two-sided product, one launch)" if two and s <= 256
-                       else "k_fused_gemm (the GEMM stages of one c-product)")
-        src, dst = Xr, torch.empty(plan.yshape(), device=dev)
-        call = lambda: tcprod.tc_cprod(plan.handle, src, dst)
-    else:
-        lowp_dt = torch.bfloat16 if args.precision in ("bf16", "bf16x3") else torch.float32
-        planes = 3 if args.precision == "bf16x3" else 1
-        roof_kernel = ("k_umma_gemm (tcgen05 slice GEMMs of one product"
-                       + (", six split-BF16 products)" if planes == 3 else ")")
-                       if args.precision != "fp32" else "k_slice_gemm (FFMA slice GEMMs of one product)")
-        src = torch.randn((planes * n3, n2, s), device=dev).to(lowp_dt)
-        dst = torch.empty((n3, n1, s), device=dev)
-        call = lambda: tcprod.tc_slice_gemm(plan.handle, src, dst)
-        reps = 50
-    prod_ms = graph_time(call, reps)
+    # the dominant kernel alone, on the stream it is launched on, with the
+    # operands it has inside the solve (back-to-back launches, CUDA events)
+    dk = dominant_kernel(plan, args, (n1, n2, s, n3, two), dev)
+    dk_ms = graph_time(dk["call"], dk["reps"])
     clk = clocks.stop()
 
     # end to end through the public API: pinned host C in, X_reg out, every step
@@ -599,107 +707,160 @@ def run_gpu(args):
     ee1.record(st)
     torch.cuda.synchronize()
     e2e_ms = ee0.elapsed_time(ee1) / e2e_steps
+    tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)  # the solve reported
     inf = tcprod.read_info(info)
+    if tcprod.tc_plan_status(plan.handle) != tcprod.TC_OK:
+        raise RuntimeError("a bounded wait of a tensor-core kernel gave up during the bench")
 
     t_max, value = replica_throughput(total_ms, args.steps, iters, world, dev)
     if rank == 0:
         peaks, src_peaks = load_peaks()
-        sm_max = peaks.get("sm_max_mhz", 2070.0)
-        fp32_peak = FP32_LANES * 2 * sm_max * 1e6 / 1e12
-        achieved = fl / (prod_ms * 1e-3) / 1e12
-        if args.precision == "fp32":
-            traffic = captured_traffic("k_cprod2") if roof_kernel.startswith("k_cprod2") and \
-                args.workload == "two_sided_256" else None
-            roof = {"kernel": roof_kernel, "bound": "alu", "achieved": achieved, "peak": fp32_peak,
-                    "unit": "TFLOP/s", "frac": achieved / fp32_peak, "traffic": traffic,
-                    "peak_source": f"152 SMs x 128 FP32 lanes x 2 x {sm_max:.0f} MHz "
-                                   f"({src_peaks} max clock)", "launch_ms": prod_ms}
-        elif args.precision == "bf16x3":  # six BF16 products per FP32-level product
-            peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / 6.0
-            roof = {"kernel": roof_kernel, "bound": "tensor", "achieved": achieved, "peak": peak,
-                    "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                    "peak_source": f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / 6: each "
-                                   "FP32-level product is six BF16 products",
-                    "launch_ms": prod_ms, "algorithmic_flops": fl,
-                    "note": "its 268 MB at the measured HBM rate take 40 us at 512x512x64, "
-                            "less than the six products at the tensor rate"}
-        else:  # tcgen05 GEMM: A~ and X~ in the input type read once, Y~ written in FP32
-            es = {"bf16": 2, "bf16x3": 6}.get(args.precision, 4)
-            gbytes = (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4
-            hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
-            gbs = gbytes / (prod_ms * 1e-3) / 1e9
-            roof = {"kernel": roof_kernel, "bound": "hbm", "achieved": gbs, "peak": hbm,
-                    "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
-                    "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src_peaks})",
-                    "launch_ms": prod_ms, "algorithmic_bytes": gbytes,
-                    "note": ("the mode-3 transform passes take most of this solve; see profiles"
-                             if args.product == "th" else
-                             "transform-domain iteration: the solve runs the fused form of "
-                             "this GEMM (Krylov epilogue and BF16 copy in the store, 235 MB a "
-                             "product at 512x512x64); timed here is the plain form; see "
-                             "profiles")}
+        hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+        ms_iter = t_max / args.steps / iters
+        floor_b = lsqr_floor_bytes(n1, n2, s, n3, args.precision, two)
         line = {
             "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
             "solves_per_s": value / iters, "n_gpus": world, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": t_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp32": "f32", "bf16x3": "f32-level: three BF16 planes an operand, six products, f32 accumulate"}.get(args.precision, f"{args.precision} GEMM inputs, f32"),
-            "data": "synthetic (seeded image + Gaussian blur + 1e-3 noise)",
-            "config": {"workload": f"{args.workload}: c-LSQR {iters} it + Tikhonov/GCV, "
-                                   f"A {n1}x{n2}x{n3}" + (f", B {s}x{s}x{n3}" if two else "")
-                                   + f", X {n2}x{s}x{n3}",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "bf16x3": "f32-level: three BF16 planes an operand, six "
+                      "products, f32 accumulate"}.get(args.precision,
+                                                       f"{args.precision} GEMM inputs, f32"),
+            "data": "synthetic (seeded video/image + Gaussian Toeplitz blurs + 1e-3 noise)",
+            "config": {"workload": WORKLOAD_NAMES[args.workload].format(
+                           iters=iters, n1=n1, n2=n2, n3=n3, s=s),
                        "precision": args.precision, "product": args.product,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof,
+            "roofline": roofline_line(dk, dk_ms, peaks, src_peaks),
+            "solve_roofline": {
+                "bytes_per_iteration": floor_b,
+                "floor_us_per_iteration": floor_b / (hbm * 1e9) * 1e6,
+                "measured_us_per_iteration": ms_iter * 1e3,
+                "solve_frac": floor_b / (hbm * 1e9) / (ms_iter * 1e-3),
+                "definition": "algorithmic bytes 2 T_A + 11 T per c-LSQR iteration at the "
+                              "measured HBM copy rate, over the measured time per iteration "
+                              "of the whole solve (start-up, GCV and X_reg included)"},
             "e2e": {"value": iters / (e2e_ms / 1000.0) * world, "unit": "LSQR iterations/s",
                     "h2d_bytes_per_step": int(C.numel() * 4),
                     "d2h_bytes_per_step": int(Xr.numel() * 4 + info.numel())},
-            "gpu_launches": args.steps * lsqr_kernel_launches(iters, two, n3 <= 4,
-                                                              precision=args.precision, s=s,
-                                                              n3=n3),
+            "gpu_launches": args.steps * kernels_per_solve,
+            "gpu_launches_per_solve": kernels_per_solve,
             "clocks": clk,
             "solve": {"iters": inf["iters"], "status": inf["status"], "lambda": inf["lam"],
                       "resid": inf["resid"],
                       "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
                       "rel_err_lsqr": float((X - Xt).norm() / Xt.norm())},
         }
+        plan.close()
         if not args.no_precision_forms and world == 1:
-            line["precision_forms"] = precision_forms(dev, peaks)
+            if args.workload == "video_512":
+                pf = precision_forms(dev, peaks)
+                line["precision_forms"] = pf
+                if args.precision in pf:
+                    line["matched_error"] = {
+                        "form": args.precision, "rel_err_reg": pf[args.precision]["rel_err_reg"],
+                        "fp32_rel_err_reg": pf["fp32"]["rel_err_reg"],
+                        "matched": pf[args.precision].get("matched_error", True),
+                        "rule": "|e - e_fp32| <= 0.02 e_fp32 on X_reg vs the clean video",
+                        "speedup_vs_fp32": value / pf["fp32"]["iters_per_s"]}
+            line["two_sided_256"] = two_sided_form(dev, peaks, src_peaks)
             line["batched_form"] = batched_form(dev)
             line["learned_form"] = learned_form()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
-    plan.close()
+    else:
+        plan.close()
     if world > 1:
         torch.distributed.destroy_process_group()
 
 
+def two_sided_form(dev, peaks, src_peaks, steps=10):
+    """The two-sided 256 x 256 x 3 workload (A *c X *c B, 50 c-LSQR iterations
+    + Tikhonov/GCV, FP32): iterations/s and the fused product's roofline."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    w = make_problem("two_sided_256")
+    n3, n1, n2 = w["A"].shape
+    s = w["B"].shape[1]
+    iters = WORKLOADS["two_sided_256"]["iters"]
+    A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+    B = torch.from_numpy(w["B"].astype(np.float32)).to(dev)
+    Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
+    G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
+    plan = tcprod.Plan(A, B, s=s)
+    Cc = plan.cprod(Xt)
+    C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
+    X = torch.empty(plan.xshape(), device=dev)
+    Xr = torch.empty(plan.xshape(), device=dev)
+    info = tcprod.new_info()
+    st = torch.cuda.current_stream()
+    for _ in range(3):
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+
+    class _A:
+        precision = "fp32"
+    dk = dominant_kernel(plan, _A, (n1, n2, s, n3, True), dev)
+    dk_ms = graph_time(dk["call"], dk["reps"])
+    out = {"workload": WORKLOAD_NAMES["two_sided_256"].format(iters=iters, n1=n1, n2=n2, n3=n3,
+                                                               s=s),
+           "iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+           "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+           "roofline": roofline_line(dk, dk_ms, peaks, src_peaks)}
+    plan.close()
+    return out
+
+
+WORKLOAD_NAMES = {
+    "video_512": ("video_512: c-LSQR {iters} it + Tikhonov/GCV on a {n1}x{n2}x{n3} video "
+                  "(A {n1}x{n2}x{n3}, frame k blurred by G(sigma_k), sigma 1.5 -> 3.5; "
+                  "X {n2}x{s}x{n3})"),
+    "two_sided_256": ("two_sided_256: c-LSQR {iters} it + Tikhonov/GCV, A *c X *c B with "
+                      "A {n1}x{n2}x{n3}, B {s}x{s}x{n3}, X {n2}x{s}x{n3}"),
+    "colour_64": ("colour_64: c-LSQR {iters} it + Tikhonov/GCV, A {n1}x{n2}x{n3}, "
+                  "X {n2}x{s}x{n3}"),
+}
+
+
 def run_reference(args):
+    """The oracle as the reference arm: each step one bounded sample of the
+    workload (CPU_SAMPLE iterations from X_0 = 0) on the host cores; the run
+    stops early, after at least two steps, once about two minutes have gone."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
-    cb_steps = []
-    cores = len(os.sched_getaffinity(0))
-    budget = 4.0  # seconds of oracle work per step (the worker warms up first)
+    sample = CPU_SAMPLE.get(args.workload, 2)
     t0 = time.perf_counter()
-    total_iters = 0
-    for _ in range(args.steps):
-        cb = cpu_baseline(args.workload, budget_s=budget)
-        cb_steps.append(cb)
-        total_iters += 1
+    out = cpu_run(args.workload, sample, max(args.steps, 1), args.ref_budget)
     el = time.perf_counter() - t0
-    value = statistics.median(c["value"] for c in cb_steps)
+    times = out["times"]
+    value = sample * len(times) / sum(times)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
-        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
-        "ms_per_step": el * 1000.0 / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded image + Gaussian blur)",
-        "config": {"workload": f"{args.workload}: c-LSQR {wl['iters']} it (FP64 NumPy oracle "
-                               "on the host cores; each step a bounded sample)"},
-        "cpu_baseline": {"kind": "oracle", "cores": cores, "value": value,
-                         "unit": "LSQR iterations/s", "sample": cb_steps[0]["sample"]},
+        "n_gpus": world, "steps": len(times), "steps_requested": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded video/image + Gaussian Toeplitz blurs + 1e-3 noise)",
+        "config": {"workload": f"{args.workload}: c-LSQR (FP64 NumPy oracle on the host cores); "
+                               f"each step a bounded sample of {sample} iterations of the "
+                               f"{wl['iters']}-iteration solve",
+                   "wall_s": el},
+        "cpu_baseline": {"kind": "oracle", "cores": out["cores_used"],
+                         "cores_available": out["cores_available"], "value": value,
+                         "unit": "LSQR iterations/s",
+                         "sample": f"{len(times)} runs of {sample} c-LSQR iterations from X_0 = 0 "
+                                   f"(start-up product and norms included), "
+                                   f"{sum(times):.1f} s"},
         "e2e": {"value": value, "unit": "LSQR iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -712,32 +873,71 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tcprod", choices=["tcprod", "reference"])
-    ap.add_argument("--workload", default="two_sided_256", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="video_512", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-precision-forms", action="store_true")
+    ap.add_argument("--no-precision-forms", action="store_true",
+                    help="only the main workload (no other forms, batch, learned, two-sided)")
     ap.add_argument("--iters", type=int, default=0, help="override the workload's iterations")
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16", "bf16x3"],
-                    help="slice-GEMM inputs of the main workload (tensor-core forms need "
-                         "one-sided plans: video_512 or colour_64)")
+    ap.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16", "bf16x3"],
+                    help="slice-GEMM inputs of the main workload (default: bf16 for video_512, "
+                         "fp32 otherwise)")
     ap.add_argument("--product", default="th", choices=["th", "orthodct"],
                     help="c-product reading: Definition 2.1 (th) or Algorithm 1's dct "
                          "(orthodct; off the fused route LSQR then runs in the transform domain)")
     ap.add_argument("--paper-shaped", action="store_true",
                     help="time the paper's three methods on the shapes of its Tables 1-4")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="launch only the workload's dominant kernel (3 warm-up + 5 launches), "
+                         "for profiling captures")
+    ap.add_argument("--ref-budget", type=float, default=120.0,
+                    help="seconds after which the reference arm stops taking steps")
     ap.add_argument("--cpu-worker", default=None)
-    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--cpu-sample", type=int, default=2)
+    ap.add_argument("--cpu-steps", type=int, default=1)
+    ap.add_argument("--cpu-budget", type=float, default=0.0)
     args = ap.parse_args()
+    if args.precision is None:
+        args.precision = "bf16" if args.workload == "video_512" else "fp32"
     if args.cpu_worker:
-        cpu_worker(args.cpu_worker, args.cpu_budget)
+        cpu_worker(args.cpu_worker, args.cpu_sample, args.cpu_steps, args.cpu_budget)
         return
     if args.paper_shaped:
         for row in paper_shaped():
             print(json.dumps(row))
         return
+    if args.kernel_only:
+        kernel_only(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)
+
+
+def kernel_only(args):
+    """Plan the workload and launch its dominant kernel 3 + 5 times (the
+    command profiling captures run)."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    w = make_problem(args.workload)
+    n3, n1, n2 = w["A"].shape
+    two = w["B"] is not None
+    s = w["B"].shape[1] if two else w["X_true"].shape[2]
+    dev = torch.device("cuda", 0)
+    A = torch.from_numpy(w["A"].astype(np.float32)).to(dev)
+    B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
+    prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16,
+            "bf16x3": tcprod.TC_BF16X3}[args.precision]
+    plan = tcprod.Plan(A, B, s=s, precision=prec)
+    dk = dominant_kernel(plan, args, (n1, n2, s, n3, two), dev)
+    for _ in range(8):
+        dk["call"]()
+    torch.cuda.synchronize()
+    status = tcprod.tc_plan_status(plan.handle)
+    plan.close()
+    print(json.dumps({"kernel": dk["kernel"], "launches": 8, "status": status}))
+    if status != tcprod.TC_OK:
+        sys.exit(1)
 
 
 if __name__ == "__main__":

@@ -278,6 +278,40 @@ int tc_lsqr_c_learned(tc_plan* plan, const tc_mlp* mlp, const float* C, float* X
  * On the tensor-core forms this is one tcgen05 GEMM launch. */
 int tc_slice_gemm(tc_plan* plan, const void* Xh, float* Yh, int adjoint, tc_stream_t stream);
 
+/* Steps 1 and 3 of Algorithm 1 alone: the mode-3 transform of Remark 2.1,
+ * out = in x_3 T (+ prev), on the plan's transform matrices:
+ *   which: TC_M (M, forward), TC_MINV (M^{-1}, inverse), TC_MINVT (M^{-T}, the
+ *   adjoint's forward transform) or TC_MT (M^T, the adjoint's inverse).
+ *   in, out: device FP32, n3 slices of P values each (slice k at k P).
+ *   P: 1 .. max(n1, n2) s. prev: device, same layout, or NULL; when given,
+ *   out = in x_3 T + prev. sumsq: device double or NULL: ||out||_F^2 by the
+ *   library's deterministic reduction.
+ * It runs the pass the plan's products run: the tcgen05 form (operands split
+ * into BF16 planes) for TF32/BF16/BF16X3 plans with n3 > 32, the FP32 pass
+ * otherwise. A bounded wait that gives up sets the plan's status to
+ * TC_ETIMEOUT (tc_plan_status). `in` must not alias out or prev. */
+typedef enum { TC_M = 0, TC_MINV = 1, TC_MINVT = 2, TC_MT = 3 } tc_transform_kind;
+int tc_transform(tc_plan* plan, int which, const float* in, float* out, size_t P,
+                 const float* prev, double* sumsq, tc_stream_t stream);
+
+/* The plan's device status word (TC_OK, or TC_ETIMEOUT once a bounded wait of
+ * its tensor-core kernels gave up), copied to the host *status. Synchronous. */
+int tc_plan_status(tc_plan* plan, int* status);
+
+/* Kernel launches in the plan's captured c-LSQR graph (tc_lsqr_c and
+ * tc_lsqr_c_lcurve with opts.use_graphs): every replay launches all of them,
+ * including those that return at once after an early stop. *count = 0 when no
+ * graph is cached. Host int. */
+int tc_lsqr_graph_kernels(tc_plan* plan, int* count);
+
+/* Self-check of the FP64 reciprocal and inverse square root that the solvers
+ * use for their step scalars and epilogue coefficients (Newton's method from
+ * the hardware estimates inside [DBL_MIN, 2^1000], IEEE division and square
+ * root outside it): rcp[i] = 1/x[i], rsqrt[i] = 1/sqrt(x[i]) for x[i] > 0
+ * (0 otherwise). x, rcp, rsqrt: device double[n], 1 <= n <= 2^28. */
+int tc_check_recip(const double* x, size_t n, double* rcp, double* rsqrt,
+                   tc_stream_t stream);
+
 /* Tikhonov solution of a projected problem with GCV (§3.1, eqs. (leastsq),
  * (tikho2), (gcv2)): y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
  *   H: device double, (k+1) x k row-major (Hessenberg or lower bidiagonal).
@@ -315,6 +349,9 @@ int tc_fro_norm_noalloc(const float* X, size_t n, double* out, tc_stream_t strea
  * barrier that nothing arrives on and writes the outcome to *status.
  *   spins: 1 .. 2^20 polls.  status: device int, written with TC_ETIMEOUT
  *   (TC_OK would mean the wait completed, which it cannot).
+ * When a wait gives up, the kernel waits once more (bounded) for the copies
+ * and MMAs it has already issued before it frees its tensor memory and returns
+ * (the slice GEMM and the tensor-core transform pass alike).
  * No fault or trap is involved; the context stays usable. */
 int tc_check_bounded_wait(int spins, int* status, tc_stream_t stream);
 

@@ -488,3 +488,32 @@ extern "C" int tc_slice_gemm(tc_plan* p, const void* Xh, float* Yh, int adjoint,
                         M, p->s, K, p->n3, x3(p) ? 3 : 1));
   return launch_umma(m, Yh, p->dev_err, nullptr, st);
 }
+
+extern "C" int tc_transform(tc_plan* p, int which, const float* in, float* out, size_t P,
+                            const float* prev, double* sumsq, tc_stream_t stream) {
+  if (!p || !in || !out || (const void*)in == (const void*)out) return TC_EINVAL;
+  if (which < TC_M || which > TC_MT || P < 1 || P * (size_t)p->n3 > p->tmp_elems)
+    return TC_EINVAL;
+  if (prev && (prev == out || prev == in)) return TC_EINVAL;
+  cudaStream_t st = (cudaStream_t)stream;
+  const float* T = which == TC_M ? p->dM : which == TC_MINV ? p->dMinv
+                   : which == TC_MINVT ? p->dMinvT : p->dMT;
+  Epi ep;
+  if (prev) {
+    ep.coef.rule = COEF_ADD;
+    ep.prev = prev;
+  }
+  if (sumsq) ep.red = make_red(p, sumsq, 0, nullptr, nullptr);
+  // the pass the plan's products run: tcgen05 for tensor-core plans above
+  // TC_TUBE_MIN_N3 (three BF16 planes for TC_BF16X3), the FP32 pass otherwise
+  if (lowp(p) && p->n3 > TC_TUBE_MIN_N3)
+    return launch_mode3_tc(in, out, T, p->n3, P, ep, p->dev_err, st, x3(p));
+  return launch_mode3(in, out, T, p->n3, P, ep, st);
+}
+
+extern "C" int tc_plan_status(tc_plan* p, int* status) {
+  if (!p || !status) return TC_EINVAL;
+  TC_CUDA(cudaMemcpy(status, p->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+  return TC_OK;
+}
+

@@ -8,6 +8,7 @@
 // that makes the remaining launches of the solve return at once.
 #include <cmath>
 #include <cstring>
+#include <vector>
 
 #include "mlp.cuh"
 #include "tc_device.cuh"
@@ -323,6 +324,17 @@ int run_lsqr(tc_plan* p, const LsqrArgs& a, const uintptr_t (&key)[10], cudaStre
       tc_set_error("cudaStreamEndCapture", e);
       return TC_ECUDA;
     }
+    size_t nn = 0;
+    p->lsqr_kernels = 0;
+    if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+      std::vector<cudaGraphNode_t> nodes(nn);
+      if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+        for (size_t i = 0; i < nn; ++i) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel)
+            ++p->lsqr_kernels;
+        }
+    }
     const cudaError_t e2 = cudaGraphInstantiate(&p->lsqr_graph, g, 0);
     cudaGraphDestroy(g);
     if (e2 != cudaSuccess) {
@@ -354,6 +366,12 @@ extern "C" int tc_lsqr_c(tc_plan* p, const float* C, float* X, float* X_reg, int
                              (uintptr_t)tb, (uintptr_t)lb, (uintptr_t)phibar_hist,
                              (uintptr_t)info, 0, 0};
   return run_lsqr(p, a, key, (cudaStream_t)stream);
+}
+
+extern "C" int tc_lsqr_graph_kernels(tc_plan* p, int* count) {
+  if (!p || !count) return TC_EINVAL;
+  *count = p->lsqr_graph ? p->lsqr_kernels : 0;
+  return TC_OK;
 }
 
 extern "C" int tc_lsqr_c_lcurve(tc_plan* p, const float* C, float* X, float* X_opt, int kmax,

@@ -8,8 +8,18 @@
 // hardware estimates: y <- y (2 - x y) and y <- y (3/2 - x y^2 / 2), each step
 // doubling the correct bits. A few dependent FMAs, where the IEEE division
 // and square root are long sequences on this part's scarce FP64 units.
-// Results are within a few ulp of the correctly rounded ones.
+// The estimates flush subnormal inputs and results to zero, so the Newton
+// form serves |x| in [DBL_MIN, 2^1000] only (where x, 1/x and 1/sqrt(x) are
+// all normal); everything else (zero, subnormals, huge values, Inf, NaN)
+// takes the IEEE operations. Within that range the results are within a few
+// ulp of the correctly rounded ones (checked against host FP64 and long double
+// references by tc_check_recip).
+constexpr double kNewtonLo = 2.2250738585072014e-308;  // DBL_MIN
+constexpr double kNewtonHi = 1.0715086071862673e301;   // 2^1000
+
 __device__ __forceinline__ double rcp_newton(double x) {
+  const double ax = fabs(x);
+  if (!(ax >= kNewtonLo && ax <= kNewtonHi)) return 1.0 / x;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   double e = fma(-x, y, 1.0);
@@ -18,7 +28,8 @@ __device__ __forceinline__ double rcp_newton(double x) {
   return fma(y, e, y);
 }
 
-__device__ __forceinline__ double rsqrt_newton(double x) {  // x > 0, finite
+__device__ __forceinline__ double rsqrt_newton(double x) {
+  if (!(x >= kNewtonLo && x <= kNewtonHi)) return 1.0 / sqrt(x);
   double y;
   asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
   const double h = 0.5 * x;
@@ -48,6 +59,7 @@ __device__ __forceinline__ void coef_compute(const Coef& c, float* sh2) {
       }
       case COEF_NEG: ca = -1.0; break;
       case COEF_AXPY: cp = -*c.s0; break;
+      case COEF_ADD: cp = 1.0; break;
       default: break;
     }
     sh2[0] = (float)ca;
@@ -138,7 +150,9 @@ __device__ __forceinline__ bool lsqr_step_scalars(const LsqrStep& u, float* sh, 
   const double b = u.beta[j + 1], a = u.alpha[j + 1];
   const double rb = u.rhobar[j], pb = u.phibar[j];
   const double r2 = fma(rb, rb, b * b);
-  const bool plain = r2 > 0.0 && r2 < 1e300;  // else the IEEE path: zeros, Inf, NaN
+  // Newton's range (normal r2 up to 2^1000); else the IEEE path: zeros,
+  // subnormals, Inf, NaN, and squares that would overflow
+  const bool plain = r2 >= kNewtonLo && r2 <= kNewtonHi;
   const double irho = plain ? rsqrt_newton(r2) : 1.0 / hypot(rb, b);
   const double rho = plain ? r2 * irho : hypot(rb, b);
   const double c = rb * irho, s = b * irho;

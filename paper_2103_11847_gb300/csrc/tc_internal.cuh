@@ -33,7 +33,8 @@ enum CoefRule : int {
   COEF_GK = 2,     // ca = 1/s0,    cp = -s0/s1  (Golub-Kahan with deferred normalisation)
   COEF_INV = 3,    // ca = 1/s0,    cp = 0
   COEF_NEG = 4,    // ca = -1,      cp = 0
-  COEF_AXPY = 5    // ca = 1,       cp = -s0
+  COEF_AXPY = 5,   // ca = 1,       cp = -s0
+  COEF_ADD = 6     // ca = 1,       cp = 1
 };
 
 struct Coef {
@@ -135,6 +136,7 @@ struct tc_plan {
   // graph cache for tc_lsqr_c
   cudaGraphExec_t lsqr_graph = nullptr;
   uintptr_t lsqr_key[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  int lsqr_kernels = 0;           // kernel nodes of the captured solve (each replay launches them all)
 };
 
 // ----------------------------------------------------------- error helpers --

@@ -495,7 +495,13 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
     // the next tile's MMAs overwrite the accumulator after the next barrier
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   }
-  if (!ok && tid == 0) atomicExch(err, TC_ETIMEOUT);
+  if (!ok && tid == 0) {
+    // The MMAs of the tile whose wait gave up may still read sA/sB and write
+    // the accumulator: wait (bounded) once more for their commit before the
+    // tensor memory is freed and the CTA's shared memory is released.
+    mbar_wait(done, phase);
+    atomicExch(err, TC_ETIMEOUT);
+  }
   asm volatile("cp.async.wait_all;" ::: "memory");  // no copy outlives the CTA
   if (OUT == OUT_F32 && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

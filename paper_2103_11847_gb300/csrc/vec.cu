@@ -344,3 +344,28 @@ int launch_mgs_pass(float* W, const float* Vi, const double* h, const float* Vne
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
+
+namespace {
+// The FP64 reciprocal and inverse square root of the step and coefficient
+// scalars (rcp_newton, rsqrt_newton), evaluated elementwise for their test.
+__global__ void k_check_recip(const double* __restrict__ x, size_t n, double* rcp,
+                              double* rsq) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    rcp[i] = rcp_newton(v);
+    rsq[i] = v > 0.0 ? rsqrt_newton(v) : 0.0;
+  }
+}
+}  // namespace
+
+extern "C" int tc_check_recip(const double* x, size_t n, double* rcp, double* rsqrt_out,
+                              tc_stream_t stream) {
+  if (!x || !rcp || !rsqrt_out || n < 1 || n > ((size_t)1 << 28)) return TC_EINVAL;
+  const size_t blocks = (n + 255) / 256;
+  k_check_recip<<<(unsigned)(blocks < 4096 ? blocks : 4096), 256, 0, (cudaStream_t)stream>>>(
+      x, n, rcp, rsqrt_out);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+

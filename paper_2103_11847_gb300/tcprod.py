@@ -18,6 +18,7 @@ TC_OK, TC_EINVAL, TC_ECUDA, TC_EBREAKDOWN, TC_ENONFINITE, TC_ETIMEOUT, TC_ENOMEM
 TC_FP32, TC_TF32, TC_BF16, TC_BF16X3 = 0, 1, 2, 3
 TC_GCV_PAPER, TC_GCV_FULL = 0, 1
 TC_TH, TC_ORTHODCT = 0, 1
+TC_M, TC_MINV, TC_MINVT, TC_MT = 0, 1, 2, 3
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
                 TC_ENONFINITE: "nonfinite"}
 
@@ -56,6 +57,11 @@ _SIGS = {
     "tc_fro_norm_noalloc": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p], c_int),
     "tc_check_bounded_wait": ([c_int, c_void_p, c_void_p], c_int),
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
+    "tc_transform": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p, c_void_p,
+                      c_void_p], c_int),
+    "tc_plan_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
+    "tc_lsqr_graph_kernels": ([c_void_p, ctypes.POINTER(c_int)], c_int),
+    "tc_check_recip": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p, c_void_p], c_int),
     "tc_batch_create": ([ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int),
                          ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
                          ctypes.POINTER(c_void_p), ctypes.POINTER(tc_opts), c_void_p], c_int),
@@ -215,6 +221,39 @@ def tc_slice_gemm(h, Xh, Yh, adjoint=False, stream=None):
     dt = torch.bfloat16 if Xh.dtype == torch.bfloat16 else torch.float32
     _check("tc_slice_gemm", lib().tc_slice_gemm(h, _ptr(Xh, dt, name="Xh"), _ptr(Yh, name="Yh"),
                                                 int(bool(adjoint)), _stream(stream)))
+
+
+def tc_transform(h, which, X, Y, prev=None, sumsq=None, stream=None):
+    """Y = X x_3 T (+ prev) with T = M, M^-1, M^-T or M^T (which = TC_M ..
+    TC_MT); X, Y of shape (n3, ...); sumsq: device double for ||Y||^2 or None."""
+    P = X[0].numel()
+    if Y.shape != X.shape or (prev is not None and prev.shape != X.shape):
+        raise ValueError("X, Y (and prev) must have the same shape")
+    _check("tc_transform", lib().tc_transform(h, int(which), _ptr(X, name="X"), _ptr(Y, name="Y"),
+                                              P, _ptr(prev, name="prev"),
+                                              _ptr(sumsq, torch.float64, name="sumsq"),
+                                              _stream(stream)))
+
+
+def tc_plan_status(h):
+    """The plan's device status word (synchronous): TC_OK or TC_ETIMEOUT."""
+    v = c_int(0)
+    _check("tc_plan_status", lib().tc_plan_status(h, ctypes.byref(v)))
+    return v.value
+
+
+def tc_lsqr_graph_kernels(h):
+    """Kernel launches in the plan's captured c-LSQR graph (0 if none)."""
+    v = c_int(0)
+    _check("tc_lsqr_graph_kernels", lib().tc_lsqr_graph_kernels(h, ctypes.byref(v)))
+    return v.value
+
+
+def tc_check_recip(x, rcp, rsq, stream=None):
+    """rcp = 1/x, rsq = 1/sqrt(x) by the library's FP64 helpers (float64 tensors)."""
+    _check("tc_check_recip", lib().tc_check_recip(
+        _ptr(x, torch.float64, name="x"), x.numel(), _ptr(rcp, torch.float64, name="rcp"),
+        _ptr(rsq, torch.float64, name="rsq"), _stream(stream)))
 
 
 def tc_fro_norm_noalloc(X, out, stream=None):
