@@ -576,9 +576,10 @@ def dominant_kernel(plan, args, dims, dev):
             + (", six split-BF16 products)" if planes == 3 else ")")
             if prec != "fp32" else "k_slice_gemm (FFMA slice GEMMs of one product)")
     es = {"bf16": 2, "bf16x3": 6}.get(prec, 4)
+    bound = {"bf16x3": "tensor", "fp32": "alu"}.get(prec, "hbm")
     return dict(kernel=name, call=lambda: tcprod.tc_slice_gemm(plan.handle, src, dst),
-                bound="tensor" if prec == "bf16x3" else "hbm", flops=fl,
-                work=fl if prec == "bf16x3" else (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4,
+                bound=bound, flops=fl,
+                work=fl if bound != "hbm" else (n3 * n1 * n2 + n3 * n2 * s) * es + n3 * n1 * s * 4,
                 traffic_key=None, reps=50)
 
 

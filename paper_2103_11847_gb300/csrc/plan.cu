@@ -123,7 +123,7 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
   if (fused(p) && p->two_sided && cprod2_fits(s))  // the step runs inside the product
     return launch_cprod2(p->AhT, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep,
                          step ? *step : LsqrStep{}, st);
-  if (step) TC_TRY(launch_lsqr_update(*step, st));
+  if (step) TC_TRY(step->X ? launch_lsqr_update(*step, st) : launch_lsqr_scalars(*step, st));
   Epi mid;
   mid.skip = ep.skip;
   if (fused(p)) {

@@ -158,6 +158,15 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   int* done = p->lsqr_done;
   float *U = p->lsqr_U, *V = p->lsqr_V, *W = p->lsqr_W;
   const bool keep = a.X_reg != nullptr;
+  // With the basis kept, the iterate is formed from it once at the end,
+  // X_k = V_k R_k^{-1} f_k (§3.3), instead of by the per-step X, W updates:
+  // the basis holds the unnormalised V~_1..V~_k that the adjoint products
+  // write (slot j is both the forward product's operand and the next
+  // adjoint's prev), each step runs its scalars alone, and the final pass
+  // forms X and X_reg together with coefficients y_i / alpha_i. tc_lsqr_label
+  // reads the basis as normalised vectors and keeps the per-step updates.
+  const bool defer = keep && !a.spatial_basis;
+  auto slot = [&](int i) { return p->basis + (size_t)i * p->Tx; };
 
   TC_CUDA(cudaMemsetAsync(flags, 0, 16 * sizeof(int), st));
   TC_CUDA(cudaMemsetAsync(done, 0, L * sizeof(int), st));
@@ -190,7 +199,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
                         p->opts.precision == TC_BF16X3 ? ROUND_BF16X3 : ROUND_BF16, st));
   auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
     if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
-    if (step) TC_TRY(launch_lsqr_update(*step, st));
+    if (step) TC_TRY(step->X ? launch_lsqr_update(*step, st) : launch_lsqr_scalars(*step, st));
     return tdf ? cprod_tdf(p, Yv, ep, st) : cprod_td(p, Xv, Yv, ep, st);
   };
   auto adj = [&](const float* Yv, float* Xv, const Epi& ep) -> int {
@@ -205,17 +214,16 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     ep.coef.rule = COEF_INV;
     ep.coef.s0 = beta;
     ep.red = make_red(p, alpha, 1, nullptr, flags + 2);
-    TC_TRY(adj(Cin, V, ep));
+    TC_TRY(adj(Cin, defer ? slot(0) : V, ep));
   }
-  // W_1 = V_1 = V~_1 / alpha_1; X_0 = 0
-  {
+  if (!defer) {  // W_1 = V_1 = V~_1 / alpha_1; X_0 = 0
     Coef c;
     c.rule = COEF_INV;
     c.s0 = alpha;
     TC_TRY(launch_scale(V, W, p->Tx, c, nullptr, nullptr, st));
     if (keep) TC_TRY(launch_scale(V, p->basis, p->Tx, c, nullptr, nullptr, st));
+    TC_CUDA(cudaMemsetAsync(Xw, 0, p->Tx * sizeof(float), st));
   }
-  TC_CUDA(cudaMemsetAsync(Xw, 0, p->Tx * sizeof(float), st));
   k_lsqr_init<<<1, 1, 0, st>>>(alpha, beta, rhobar, phibar, flags, done);
   TC_CUDA(cudaGetLastError());
 
@@ -226,10 +234,10 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   // the loop.
   auto make_step = [&](int j) {
     LsqrStep u;
-    u.X = Xw;
-    u.W = W;
-    u.V = V;
-    u.basis_slot = (keep && j + 1 < a.itermax) ? p->basis + (size_t)(j + 1) * p->Tx : nullptr;
+    u.X = defer ? nullptr : Xw;  // deferred: the step's scalars alone
+    u.W = defer ? nullptr : W;
+    u.V = defer ? nullptr : V;
+    u.basis_slot = (!defer && keep && j + 1 < a.itermax) ? slot(j + 1) : nullptr;
     u.n = p->Tx;
     u.alpha = alpha;
     u.beta = beta;
@@ -257,7 +265,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
       const LsqrStep prev = j > 0 ? make_step(j - 1) : LsqrStep{};
-      TC_TRY(fwd(V, U, ep, j > 0 ? &prev : nullptr));
+      TC_TRY(fwd(defer ? slot(j) : V, U, ep, j > 0 ? &prev : nullptr));
     }
     // the learned predictor reads the first MLP_FEAT_STEPS steps
     if (a.mlp && j == MLP_FEAT_STEPS)
@@ -268,13 +276,18 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.coef.rule = COEF_GK;
       ep.coef.s0 = beta + j + 1;
       ep.coef.s1 = alpha + j;
-      ep.prev = V;
+      ep.prev = defer ? slot(j) : V;
       ep.red = make_red(p, alpha + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
-      TC_TRY(adj(U, V, ep));
+      // deferred: V~_{j+1} into basis slot j + 1 (the last one, never part of
+      // the basis, into the workspace)
+      TC_TRY(adj(U, defer ? (j + 1 < a.itermax ? slot(j + 1) : V) : V, ep));
     }
   }
-  TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));
+  if (defer)
+    TC_TRY(launch_lsqr_scalars(make_step(a.itermax - 1), st));
+  else
+    TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));
   if (a.mlp && a.itermax == MLP_FEAT_STEPS)
     TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   const bool gcv_on = keep && !a.lcurve;
@@ -282,14 +295,22 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   float* Xr_w = td ? p->tmp2 : a.X_reg;
   if (keep && a.lcurve) {  // X_reg = X_{k_opt} at the L-curve corner (flags[8] = k_opt)
     TC_TRY(launch_lcurve(rgiv, phibar, flags + 1, kp, a.curve, y, flags + 8, st));
-    TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, flags + 8, y, p->Tx, nullptr,
-                          st));
   } else if (keep) {
     TC_TRY(launch_gcv_bidiag(rgiv, phibar, alpha, beta, flags + 1, kp, p->opts.gcv_variant,
                              a.mlp ? -1.0 : a.lambda, gwork, lam, y, gcv, st,
                              a.mlp ? lam_pred : nullptr, a.factor, flags + 7));
-    TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, flags + 1, y, p->Tx, nullptr,
-                          st));
+  }
+  if (defer) {
+    // X_k = V_k R_k^{-1} f_k and X_reg = V_k y (y of k_opt's iterate for the
+    // L-curve, zero beyond it) in one pass over the unnormalised basis:
+    // coefficients divided by alpha_i
+    double* ylsqr = gwork;  // the GCV search's work space is free again
+    TC_TRY(launch_lsqr_coeffs(rgiv, flags + 1, kp, ylsqr, st));
+    TC_TRY(launch_combine2(Xw, ylsqr, Xr_w, y, alpha, p->basis, p->Tx, kp, flags + 1, p->Tx,
+                           st));
+  } else if (keep) {
+    TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, a.lcurve ? flags + 8 : flags + 1,
+                          y, p->Tx, nullptr, st));
   }
   if (td) {  // back to the spatial domain: X = idct(X~), X_reg likewise
     TC_TRY(mode3(Xw, a.X, p->dMinv, p->Tx / p->n3));

@@ -185,10 +185,13 @@ __device__ __forceinline__ bool lsqr_step_scalars(const LsqrStep& u, float* sh, 
 }
 
 // The vector part of an LSQR step on elements [beg, end), by the threads of
-// one CTA (nt threads), four loads in flight per thread.
+// one CTA (nt threads), four loads in flight per thread. A step without
+// vectors (X null: the iterate is formed from the kept basis at the end of
+// the solve) does nothing here.
 __device__ __forceinline__ void lsqr_step_vectors(const LsqrStep& u, size_t beg, size_t end,
                                                   float cx, float cv, float cw, bool stop,
                                                   int nt) {
+  if (!u.X) return;
   for (size_t i0 = beg + threadIdx.x; i0 < end; i0 += 4 * (size_t)nt) {
     float w[4], x[4], v[4];
 #pragma unroll

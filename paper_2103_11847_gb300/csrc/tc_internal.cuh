@@ -63,7 +63,9 @@ struct Epi {
 // recurrences on the device scalars and the X, W (and basis) updates. Run by
 // its own kernel, or by the CTAs of the next forward product before their
 // GEMM (n == 0: no step). done_in = done[j] gates it; done_out = done[j+1] is
-// written by CTA 0. flags: [1] iterations, [2] status.
+// written by CTA 0. flags: [1] iterations, [2] status. With X null the step
+// is its scalars alone: the solve keeps the basis and forms X_k = V_k y_k
+// from it once at the end (launch_lsqr_scalars, launch_lsqr_coeffs).
 struct LsqrStep {
   float* X = nullptr;
   float* W = nullptr;
@@ -211,9 +213,21 @@ int launch_reduce(const float* x, const float* other, size_t n, const Red& red,
 int launch_scale(const float* in, float* out, size_t n, const Coef& c, const float* prev,
                  const int* skip, cudaStream_t st);
 int launch_lsqr_update(const LsqrStep& step, cudaStream_t st);
+// The scalars of an LSQR step alone (one thread): the Givens recurrences,
+// the state, the flags and done_out.
+int launch_lsqr_scalars(const LsqrStep& step, cudaStream_t st);
+// y = R_k^{-1} f_k, the LSQR iterate's coordinates in the basis (§3.3: X_k =
+// V_k y_k), from the rotations rg (rho, theta, phi interleaved) with k =
+// min(*kdev, kmax); zero beyond k.
+int launch_lsqr_coeffs(const double* rg, const int* kdev, int kmax, double* y, cudaStream_t st);
 int launch_combine(float* X, const float* X0, const float* basis, size_t stride, int kmax,
                    const int* kdev, const double* y, size_t n, const int* skip,
                    cudaStream_t st);
+// Two combinations of one basis in one pass: X = sum_i (y_i / d_i) B_i and
+// X2 = sum_i (y2_i / d_i) B_i (d null: 1), B_i at basis + i * stride.
+int launch_combine2(float* X, const double* y, float* X2, const double* y2, const double* d,
+                    const float* basis, size_t stride, int kmax, const int* kdev, size_t n,
+                    cudaStream_t st);
 int launch_mgs_pass(float* W, const float* Vi, const double* h, const float* Vnext,
                     size_t n, const Red& red, const int* skip, cudaStream_t st);
 // small.cu (FP64, one CTA)

@@ -127,6 +127,86 @@ __global__ void __launch_bounds__(NT) k_lsqr_update(LsqrStep u) {
   }
 }
 
+// The scalars of one LSQR step (lsqr_step_scalars), one thread.
+__global__ void k_lsqr_scalars(LsqrStep u) {
+  if (*u.done_in) {
+    *u.done_out = 1;
+    return;
+  }
+  float sh[3];
+  lsqr_step_scalars(u, sh, true);
+}
+
+// y = R^{-1} f by back substitution: R upper bidiagonal with diagonal
+// rho_1..rho_k and superdiagonal theta_2..theta_k, f = (phi_1..phi_k), from
+// rg = (rho_j, theta_{j+1}, phi_j) interleaved; zero beyond k. One thread.
+__global__ void k_lsqr_coeffs(const double* __restrict__ rg, const int* kdev, int kmax,
+                              double* y) {
+  const int k = kdev ? max(0, min(*kdev, kmax)) : kmax;
+  for (int i = kmax - 1; i >= k; --i) y[i] = 0.0;
+  double yi = 0.0;
+  for (int i = k - 1; i >= 0; --i) {
+    const double num = rg[3 * i + 2] - (i + 1 < k ? rg[3 * i + 1] * yi : 0.0);
+    yi = num / rg[3 * i];
+    y[i] = yi;
+  }
+}
+
+// X = sum_i (y_i / d_i) B_i and X2 = sum_i (y2_i / d_i) B_i over i < k in one
+// pass over the basis (same order and loads as k_combine).
+template <bool VEC>
+__global__ void __launch_bounds__(NT)
+k_combine2(float* X, float* X2, const float* __restrict__ basis, size_t stride, int kmax,
+           const int* kdev, const double* __restrict__ y, const double* __restrict__ y2,
+           const double* __restrict__ d, size_t n) {
+  __shared__ float ys[TC_MAX_PROJ], ys2[TC_MAX_PROJ];
+  const int k = kdev ? max(0, min(*kdev, kmax)) : kmax;
+  for (int i = threadIdx.x; i < k; i += NT) {
+    const double dv = d ? d[i] : 1.0;
+    ys[i] = (float)(y[i] / dv);
+    ys2[i] = (float)(y2[i] / dv);
+  }
+  __syncthreads();
+  const size_t e = 4 * ((size_t)blockIdx.x * NT + threadIdx.x);
+  if (e >= n) return;
+  if (VEC && e + 3 < n) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+    for (int q0 = 0; q0 < k; q0 += 8) {
+      float4 v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        v[u] = q0 + u < k ? __ldg(reinterpret_cast<const float4*>(basis + (size_t)(q0 + u) * stride + e))
+                          : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (q0 + u >= k) break;
+        const float c = ys[q0 + u], c2 = ys2[q0 + u];
+        a.x = fmaf(c, v[u].x, a.x);
+        a.y = fmaf(c, v[u].y, a.y);
+        a.z = fmaf(c, v[u].z, a.z);
+        a.w = fmaf(c, v[u].w, a.w);
+        b.x = fmaf(c2, v[u].x, b.x);
+        b.y = fmaf(c2, v[u].y, b.y);
+        b.z = fmaf(c2, v[u].z, b.z);
+        b.w = fmaf(c2, v[u].w, b.w);
+      }
+    }
+    *reinterpret_cast<float4*>(X + e) = a;
+    *reinterpret_cast<float4*>(X2 + e) = b;
+    return;
+  }
+  for (size_t i = e; i < e + 4 && i < n; ++i) {
+    float a = 0.f, b = 0.f;
+    for (int q = 0; q < k; ++q) {
+      const float v = __ldg(basis + (size_t)q * stride + i);
+      a = fmaf(ys[q], v, a);
+      b = fmaf(ys2[q], v, b);
+    }
+    X[i] = a;
+    X2[i] = b;
+  }
+}
+
 // X = X0 + sum_{i<k} y_i V_i (V_i at basis + i*stride); k read from the device.
 // Thread t owns elements 4t..4t+3 and keeps eight basis loads in flight; the
 // sum runs in the order i = 0, 1, .., k-1 for every element. VEC: 16-byte
@@ -269,6 +349,8 @@ int vec_init() {
                                                         NT, 0));
   TC_CUDA(cudaFuncSetAttribute(k_combine<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_combine<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_combine2<true>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
+  TC_CUDA(cudaFuncSetAttribute(k_combine2<false>, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_mgs_pass, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   TC_CUDA(cudaFuncSetAttribute(k_epi, cudaFuncAttributePreferredSharedMemoryCarveout, c));
   return TC_OK;
@@ -334,6 +416,35 @@ int launch_combine(float* X, const float* X0, const float* basis, size_t stride,
     k_combine<true><<<(unsigned)blocks, NT, 0, st>>>(X, X0, basis, stride, kmax, kdev, y, n, skip);
   else
     k_combine<false><<<(unsigned)blocks, NT, 0, st>>>(X, X0, basis, stride, kmax, kdev, y, n, skip);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_lsqr_scalars(const LsqrStep& step, cudaStream_t st) {
+  k_lsqr_scalars<<<1, 1, 0, st>>>(step);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_lsqr_coeffs(const double* rg, const int* kdev, int kmax, double* y, cudaStream_t st) {
+  TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ);
+  k_lsqr_coeffs<<<1, 1, 0, st>>>(rg, kdev, kmax, y);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_combine2(float* X, const double* y, float* X2, const double* y2, const double* d,
+                    const float* basis, size_t stride, int kmax, const int* kdev, size_t n,
+                    cudaStream_t st) {
+  TC_CHECK(kmax <= TC_MAX_PROJ);
+  auto al = [](const void* q) { return (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  const bool vec = stride % 4 == 0 && al(X) && al(X2) && al(basis);
+  const size_t blocks = (n + 4 * (size_t)NT - 1) / (4 * (size_t)NT);
+  TC_CHECK(blocks >= 1 && blocks <= 0x7fffffffULL);
+  if (vec)
+    k_combine2<true><<<(unsigned)blocks, NT, 0, st>>>(X, X2, basis, stride, kmax, kdev, y, y2, d, n);
+  else
+    k_combine2<false><<<(unsigned)blocks, NT, 0, st>>>(X, X2, basis, stride, kmax, kdev, y, y2, d, n);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
