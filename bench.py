@@ -561,6 +561,13 @@ def dominant_kernel(plan, args, dims, dev):
         return dict(kernel=name, call=call, bound="hbm", work=3 * 4.0 * n3 * P,
                     traffic_key="k_tube_f32", reps=50)
     fl = product_flops(n1, n2, s, n3, two)
+    if two and prec != "fp32":  # the whole tensor-core product (two GEMMs and the passes)
+        src = torch.randn((n3, n2, s), device=dev)
+        dst = torch.empty((n3, n1, s), device=dev)
+        return dict(kernel=f"two-sided tensor-core product ({prec}: transform, two tcgen05 "
+                           "GEMMs, transform back)",
+                    call=lambda: tcprod.tc_cprod(plan.handle, src, dst), bound="tensor",
+                    work=fl, precision=prec, traffic_key=None, reps=100)
     if n3 <= 4 and prec == "fp32":
         src = torch.randn((n3, n2, s), device=dev)
         dst = torch.empty((n3, n1, s), device=dev)
@@ -591,11 +598,14 @@ def roofline_line(dk, ms, peaks, src_peaks):
         ach = dk["work"] / (ms * 1e-3) / 1e9
         unit, psrc = "GB/s", f"MEASURED_PEAKS.json hbm_gbs ({src_peaks}, burst copy)"
         extra = {"algorithmic_bytes": dk["work"]}
-    elif dk["bound"] == "tensor":  # six BF16 products per FP32-level product
-        peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / 6.0
+    elif dk["bound"] == "tensor":
+        # FP32-level (BF16X3): six BF16 products per product; TF32 runs at half
+        # the BF16 rate (the recipe's nominal ratio); BF16 at the BF16 rate
+        div = {"bf16x3": 6.0, "tf32": 2.0, "bf16": 1.0}[dk.get("precision", "bf16x3")]
+        peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / div
         ach = dk["work"] / (ms * 1e-3) / 1e12
         unit = "TFLOP/s"
-        psrc = f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / 6: six BF16 products each"
+        psrc = f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / {div:g}"
         extra = {"algorithmic_flops": dk["work"]}
     else:
         fp = measured_peak("fp32_ffma_tflops")
@@ -779,7 +789,9 @@ def run_gpu(args):
 
 def two_sided_form(dev, peaks, src_peaks, steps=10):
     """The two-sided 256 x 256 x 3 workload (A *c X *c B, 50 c-LSQR iterations
-    + Tikhonov/GCV, FP32): iterations/s and the fused product's roofline."""
+    + Tikhonov/GCV): FP32 (the fused one-launch FFMA product) and the
+    tensor-core forms (BF16X3 at FP32 level, TF32), iterations/s, the
+    reconstruction error, and the FP32 product's roofline."""
     import torch
     from paper_2103_11847_gb300 import tcprod
     w = make_problem("two_sided_256")
@@ -790,34 +802,49 @@ def two_sided_form(dev, peaks, src_peaks, steps=10):
     B = torch.from_numpy(w["B"].astype(np.float32)).to(dev)
     Xt = torch.from_numpy(w["X_true"].astype(np.float32)).to(dev)
     G = torch.from_numpy(w["G"].astype(np.float32)).to(dev)
-    plan = tcprod.Plan(A, B, s=s)
-    Cc = plan.cprod(Xt)
-    C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
-    X = torch.empty(plan.xshape(), device=dev)
-    Xr = torch.empty(plan.xshape(), device=dev)
-    info = tcprod.new_info()
     st = torch.cuda.current_stream()
-    for _ in range(3):
-        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(steps):
-        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / steps
-
-    class _A:
-        precision = "fp32"
-    dk = dominant_kernel(plan, _A, (n1, n2, s, n3, True), dev)
-    dk_ms = graph_time(dk["call"], dk["reps"])
     out = {"workload": WORKLOAD_NAMES["two_sided_256"].format(iters=iters, n1=n1, n2=n2, n3=n3,
-                                                               s=s),
-           "iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
-           "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
-           "roofline": roofline_line(dk, dk_ms, peaks, src_peaks)}
-    plan.close()
+                                                               s=s)}
+    C = None
+    for name, code in (("fp32", tcprod.TC_FP32), ("bf16x3", tcprod.TC_BF16X3),
+                       ("tf32", tcprod.TC_TF32)):
+        plan = tcprod.Plan(A, B, s=s, precision=code)
+        if C is None:
+            Cc = plan.cprod(Xt)
+            C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
+        X = torch.empty(plan.xshape(), device=dev)
+        Xr = torch.empty(plan.xshape(), device=dev)
+        info = tcprod.new_info()
+        for _ in range(3):
+            tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(steps):
+            tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+        e1.record(st)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / steps
+        r = {"iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+             "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+             "launches_per_solve": tcprod.tc_lsqr_graph_kernels(plan.handle)}
+        # one whole product alone (every launch of it), back to back
+        src, dst = torch.randn(plan.xshape(), device=dev), torch.empty(plan.yshape(), device=dev)
+        pms = graph_time(lambda: tcprod.tc_cprod(plan.handle, src, dst), 100)
+        r["product_us"] = pms * 1e3
+        if name == "fp32":
+            class _A:
+                precision = "fp32"
+            dk = dominant_kernel(plan, _A, (n1, n2, s, n3, True), dev)
+            r["roofline"] = roofline_line(dk, graph_time(dk["call"], dk["reps"]), peaks, src_peaks)
+        else:  # FP32-level products: six BF16 products each (BF16X3), or TF32 rate
+            fl = product_flops(n1, n2, s, n3, True)
+            r["product_tflops"] = fl / (pms * 1e-3) / 1e12
+        out[name] = r
+        plan.close()
+    base = out["fp32"]["rel_err_reg"]
+    for name in ("bf16x3", "tf32"):
+        out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
     return out
 
 

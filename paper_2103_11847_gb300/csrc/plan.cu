@@ -116,6 +116,19 @@ Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* sta
   return r;
 }
 
+namespace {
+// The right factor of a two-sided product on the tensor cores: the first
+// GEMM's result T (FP32, tmp2, `n` values) is rounded to the GEMM input type
+// into the operand buffer (free once the first GEMM has read its operand;
+// TF32: T is already K-major as the left operand), then tmp2 = T_k B~_k (or
+// T_k B~_k^T) by the second GEMM `m`.
+int right_factor(tc_plan* p, const UmmaMaps& m, size_t n, int* err, const int* skip,
+                 cudaStream_t st) {
+  TC_TRY(launch_round(p->tmp2, lowop(p), n, rkind(p), st, skip));
+  return launch_umma(m, p->tmp2, err, skip, st);
+}
+}  // namespace
+
 // Y = A *c X [*c B] with the epilogue `ep` on the last stage.
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
               const LsqrStep* step) {
@@ -146,6 +159,7 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
+    if (p->two_sided) TC_TRY(right_factor(p, *p->umf2, (size_t)n1 * s * n3, err, ep.skip, st));
     return tct ? launch_mode3_tc(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st, x3(p))
                : launch_mode3(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, st);
   }
@@ -176,6 +190,7 @@ int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t
     TC_TRY(launch_round(Xt, lowop(p), (size_t)n2 * s * n3, rkind(p), st, ep.skip));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
+    if (p->two_sided) TC_TRY(right_factor(p, *p->umf2, (size_t)n1 * s * n3, err, ep.skip, st));
   } else {
     TC_TRY(launch_slice_gemm(p->Ah, Xt, p->tmp2, n1, s, n2, n3, nullptr, nullptr, mid, st));
     if (p->two_sided) {
@@ -209,6 +224,7 @@ int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream
     TC_TRY(launch_round(Yt, lowop(p), (size_t)n1 * s * n3, rkind(p), st, ep.skip));
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
+    if (p->two_sided) TC_TRY(right_factor(p, *p->uma2, (size_t)n2 * s * n3, err, ep.skip, st));
   } else {
     TC_TRY(launch_slice_gemm(p->AhT, Yt, p->tmp2, n2, s, n1, n3, nullptr, nullptr, mid, st));
     if (p->two_sided) {
@@ -248,6 +264,7 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
+    if (p->two_sided) TC_TRY(right_factor(p, *p->uma2, (size_t)n2 * s * n3, err, ep.skip, st));
     return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, x3(p))
                : launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
@@ -351,7 +368,21 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
     const void* bop = bf16 ? lowop(p) : (const void*)p->tmp3;
     TC_TRY(make_umma_maps(p->umf, kind, p->AhL, bop, n1, s, n2, n3, ns));
     TC_TRY(make_umma_maps(p->uma, kind, p->AhTL, bop, n2, s, n1, n3, ns));
-    if (bf16 && p->opts.product == TC_ORTHODCT) {
+    if (B) {
+      // second GEMMs: left operand T in the operand buffer (K = s contiguous);
+      // B operand K x N with N contiguous (BF16): B~ forward, B~^T adjoint;
+      // N x K with K contiguous (TF32): B~^T forward, B~ adjoint
+      const size_t TB = (size_t)n3 * s * s;
+      TC_CUDA(cudaMalloc(&p->BfL, TB * es * ns));
+      TC_CUDA(cudaMalloc(&p->BaL, TB * es * ns));
+      TC_TRY(launch_round(bf16 ? p->Bh : p->BhT, p->BfL, TB, rkind(p), st));
+      TC_TRY(launch_round(bf16 ? p->BhT : p->Bh, p->BaL, TB, rkind(p), st));
+      p->umf2 = new UmmaMaps();
+      p->uma2 = new UmmaMaps();
+      TC_TRY(make_umma_maps(p->umf2, kind, lowop(p), p->BfL, n1, s, s, n3, ns));
+      TC_TRY(make_umma_maps(p->uma2, kind, lowop(p), p->BaL, n2, s, s, n3, ns));
+    }
+    if (bf16 && p->opts.product == TC_ORTHODCT && !B) {
       // transform-domain LSQR with the epilogue in the GEMM: each product's
       // store also writes the BF16 operand of the next one, so the forward and
       // adjoint GEMMs read separate buffers (bV: V~, n2 x s; bU: U~, n1 x s)
@@ -396,6 +427,10 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   delete p->uma;
   delete p->umf_td;
   delete p->uma_td;
+  delete p->umf2;
+  delete p->uma2;
+  dfree(p->BfL);
+  dfree(p->BaL);
   dfree(p->lowX);
   dfree(p->lowV);
   dfree(p->lowU);
@@ -425,9 +460,9 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
     if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
   }
   if (o.precision != TC_FP32) {
-    // tensor-core forms: one-sided, every dimension a multiple of 8 (16-byte
-    // rows for TMA), the transform passes of the unfused route
-    if (B || n1 % 8 || n2 % 8 || s % 8) return TC_EUNSUPPORTED;
+    // tensor-core forms: every dimension a multiple of 8 (16-byte rows for
+    // TMA), the transform passes of the unfused route
+    if (n1 % 8 || n2 % 8 || s % 8) return TC_EUNSUPPORTED;
   }
   static int inited = 0;
   if (!inited) {

@@ -126,6 +126,13 @@ struct tc_plan {
   void* AhTL = nullptr;           // its slice transposes
   UmmaMaps* umf = nullptr;        // forward:  A~_k (n1 x n2) times X~_k (n2 x s)
   UmmaMaps* uma = nullptr;        // adjoint:  A~_k^T (n2 x n1) times Y'_k (n1 x s)
+  // two-sided tensor-core plans: the right factor in the GEMM input type and
+  // the second GEMMs, T_k B~_k (forward) and T_k B~_k^T (adjoint), whose left
+  // operand T is the first GEMM's result rounded into the operand buffer
+  void* BfL = nullptr;            // B~ as the forward GEMM's B operand
+  void* BaL = nullptr;            // B~^T as the adjoint GEMM's B operand
+  UmmaMaps* umf2 = nullptr;       // T_k (n1 x s) times B~_k (s x s)
+  UmmaMaps* uma2 = nullptr;       // T_k (n2 x s) times B~_k^T (s x s)
   void* lowX = nullptr;           // TC_BF16X3 plans: the GEMM operand as three BF16 planes
   void* lowV = nullptr;           // BF16/BF16X3 ORTHODCT plans: bf16(V~) and bf16(U~) (three planes for BF16X3), the operands
   void* lowU = nullptr;           // of the transform-domain GEMMs with fused epilogues

@@ -90,22 +90,3 @@ def test_two_sided_deblur_full_size(tc):
     assert rel(Y, ref) < TOL
 
 
-def test_video_full_size_sampled_tubes(tc):
-    # 512x512x64 video operator (n3 = 64) at full size; the oracle computes
-    # sampled output tubes Y(i, j, :) one by one from the transform route.
-    w = inputs.video_deblur(n=512, frames=64, seed=2)
-    A, X = f32(w["A"]), f32(w["X_true"])
-    plan = tc.Plan(dev(A), s=512)
-    Y = plan.cprod(dev(X)).cpu().numpy()
-    M = cp.transform_matrix(64)
-    Minv = np.linalg.inv(M)
-    rng = np.random.default_rng(3)
-    Ad = A.astype(np.float64)
-    worst = 0.0
-    for _ in range(12):
-        i, j = int(rng.integers(0, 512)), int(rng.integers(0, 512))
-        Ah_row = np.einsum("kl,lp->kp", M, Ad[:, i, :])          # rows i of A~_k
-        Xh_col = np.einsum("kl,lp->kp", M, X[:, :, j].astype(np.float64))  # columns j of X~_k
-        tube = Minv @ np.sum(Ah_row * Xh_col, axis=1)
-        worst = max(worst, np.linalg.norm(Y[:, i, j] - tube) / np.linalg.norm(tube))
-    assert worst < 1e-5

@@ -114,6 +114,34 @@ def test_lsqr_gcv_full_variant_interior_minimum(tc):
     plan.close()
 
 
+@pytest.mark.parametrize("variant", ["paper", "full"])
+def test_colour_64_thirty_iterations_gcv_reconstruction(tc, variant):
+    # The 64x64x3 colour workload as stated: 30 c-LSQR iterations, then
+    # Tikhonov/GCV on the projected bidiagonal (reading R14). FP32 loses the
+    # basis's orthogonality after about 15 steps on this blur (no
+    # reorthogonalisation, as in the paper), so at 30 steps the regularised
+    # reconstructions differ by a few percent, in either direction: measured
+    # 0.309 (GPU) vs 0.335 (oracle) with the printed GCV, whose flat minimum
+    # leaves lambda to rounding, and 0.337 vs 0.331 with the full GCV. The
+    # check is that the FP32 form loses no more than 2% of reconstruction
+    # quality, and stays within 10% either way; the 1% parity holds at 15
+    # steps (test_lsqr_gcv_colour_64).
+    w = inputs.colour_deblur(n=64, seed=0)
+    A, B, C = observe(w)
+    ref = kr.lsqr_gcv(*oracle_ops(A, B), C, itermax=30, variant=variant)
+    plan = tc.Plan(dev(A), s=64, gcv_variant=tc.TC_GCV_FULL if variant == "full" else tc.TC_GCV_PAPER)
+    X, Xr, _, info = plan.lsqr(dev(C), 30, regularize=True)
+    torch.cuda.synchronize()
+    inf = tc.read_info(info)
+    assert inf["iters"] == 30
+    e_gpu = mt.relative_error(w["X_true"], Xr.cpu().numpy())
+    e_ref = mt.relative_error(w["X_true"], ref["X_reg"])
+    print(variant, e_gpu, e_ref, inf["lam"], ref["lam"])
+    assert e_gpu <= 1.02 * e_ref
+    assert abs(e_gpu - e_ref) <= 0.1 * e_ref
+    plan.close()
+
+
 def test_lsqr_colour_64_full_length_envelope(tc):
     # 30 iterations: the FP32 envelope above (0.106 for a CPU FP32 run); the
     # GPU's residual |phibar| must equal ||C - A X|| recomputed by the oracle.
@@ -219,10 +247,35 @@ def test_gkb_steps_match_oracle(tc):
     assert np.allclose(al.cpu().numpy(), g["alpha"], rtol=1e-4)
     assert np.allclose(be.cpu().numpy(), g["beta"], rtol=1e-4)
     Vg = V.cpu().numpy().astype(np.float64)
-    for j in range(4):
-        assert rel(Vg[j], g["V"][j]) < 1e-3
-    G = np.array([[np.sum(Vg[i] * Vg[j]) for j in range(m)] for i in range(m)])
-    assert np.abs(G - np.eye(m)).max() < 1e-2
+    Ug = U.cpu().numpy().astype(np.float64)
+    a, b = al.cpu().numpy(), be.cpu().numpy()
+    op, adj = oracle_ops(A, B)
+    # Proposition 3.2's relations hold to FP32 rounding whatever the loss of
+    # orthogonality, checked column by column with the oracle's operator on
+    # the GPU's vectors: A V_j = alpha_j U_j + beta_{j+1} U_{j+1} and
+    # A^T U_{j+1} = beta_{j+1} V_j + alpha_{j+1} V_{j+1}
+    for j in range(m):
+        AV = op(Vg[j])
+        r1 = AV - a[j] * Ug[j] - b[j + 1] * Ug[j + 1]
+        assert np.linalg.norm(r1) <= 1e-5 * np.linalg.norm(AV), j
+        ATU = adj(Ug[j + 1])
+        r2 = ATU - b[j + 1] * Vg[j] - a[j + 1] * Vg[j + 1]
+        assert np.linalg.norm(r2) <= 1e-5 * np.linalg.norm(ATU), j
+    # every basis tensor against the oracle's: FP32 rounding accumulates
+    # step by step (measured 7.5e-8 for V_1 growing to 4.8e-6 for V_9 on a
+    # GB300), bounded by 2e-6 (j + 1)
+    dv = [rel(Vg[j], g["V"][j]) for j in range(m + 1)]
+    print("basis differences", dv)
+    for j in range(m + 1):
+        assert dv[j] < 2e-6 * (j + 1), (j, dv[j])
+    # orthonormality of U_1..U_9 and V_1..V_9 (Proposition 3.2) to FP32
+    # rounding over these 8 steps: measured at most 1.2e-6
+    for W in (Vg, Ug):
+        G = np.array([[np.sum(W[i] * W[j]) for j in range(m + 1)] for i in range(m + 1)])
+        dev_ = np.abs(G - np.eye(m + 1))
+        print("orthogonality", [float(dev_[:k, :k].max()) for k in range(2, m + 2)])
+        assert dev_[:4, :4].max() < 1e-6
+        assert dev_.max() < 1e-5
 
 
 def test_gmres_two_sided_256(tc):

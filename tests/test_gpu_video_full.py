@@ -1,0 +1,74 @@
+"""The 512 x 512 x 64 video operator at full size, every element of the
+product and of the adjoint against the FP64 oracle (Algorithm 1 with the
+transform M of Remark 2.1; the adjoint of reading R4), for every precision
+form of the plan.
+
+The oracle's product of one full tensor takes a few seconds, so it is formed
+once per module. Each form reports the relative Frobenius error and the
+largest elementwise error relative to the largest magnitude of the result.
+Bounds (relative Frobenius / elementwise), with the values measured on a
+GB300 (product; adjoint):
+  FP32 (FP32 transform passes, FFMA slice GEMMs):   1e-5 / 1e-5  (4.6e-7 / 1.5e-6; 3.5e-7 / 8.3e-7)
+  BF16X3 (three BF16 planes, six products):          1e-5 / 1e-5  (1.5e-6 / 3.2e-6; 1.4e-6 / 2.0e-6)
+  TF32 (10-bit mantissas into the GEMM):             1e-3 / 2e-3  (1.2e-4 / 3.5e-4; 2.4e-4 / 2.6e-4)
+  BF16 (7-bit mantissas into the GEMM):              1e-2 / 2e-2  (1.6e-3 / 3.6e-3; 2.5e-3 / 2.7e-3)
+The elementwise error is measured against the largest magnitude of the
+result."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle import cproduct as cp
+from paper_2103_11847_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BOUNDS = {"fp32": (1e-5, 1e-5), "bf16x3": (1e-5, 1e-5), "tf32": (1e-3, 2e-3),
+          "bf16": (1e-2, 2e-2)}
+
+
+@pytest.fixture(scope="module")
+def tc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2103_11847_gb300 import tcprod
+    tcprod.lib()
+    return tcprod
+
+
+@pytest.fixture(scope="module")
+def video():
+    """A, X, Y = A *c X and Z = A^T *c Y by the oracle (FP64, from the FP32
+    inputs the GPU reads)."""
+    w = inputs.video_deblur(n=512, frames=64, seed=2)
+    A = np.ascontiguousarray(w["A"].astype(np.float32))
+    X = np.ascontiguousarray(w["X_true"].astype(np.float32))
+    G = np.ascontiguousarray(w["G"].astype(np.float32))  # a second, rough operand
+    Ad = A.astype(np.float64)
+    Y = cp.cprod(Ad, X.astype(np.float64))
+    Z = cp.cprod_adjoint(Ad, G.astype(np.float64))
+    return A, X, G, Y, Z
+
+
+def errors(got, ref):
+    d = got.astype(np.float64) - ref
+    return (float(np.linalg.norm(d.ravel()) / np.linalg.norm(ref.ravel())),
+            float(np.abs(d).max() / np.abs(ref).max()))
+
+
+@pytest.mark.parametrize("name", ["fp32", "bf16x3", "tf32", "bf16"])
+def test_video_operator_every_element(tc, video, name):
+    A, X, G, Y, Z = video
+    code = {"fp32": tc.TC_FP32, "tf32": tc.TC_TF32, "bf16": tc.TC_BF16, "bf16x3": tc.TC_BF16X3}[name]
+    plan = tc.Plan(torch.from_numpy(A).cuda(), s=512, precision=code)
+    Yg = plan.cprod(torch.from_numpy(X).cuda()).cpu().numpy()
+    Zg = plan.adjoint(torch.from_numpy(G).cuda()).cpu().numpy()
+    assert tc.tc_plan_status(plan.handle) == tc.TC_OK
+    plan.close()
+    fro, mx = errors(Yg, Y)
+    afro, amx = errors(Zg, Z)
+    print(f"{name}: product fro {fro:.3e} max {mx:.3e}; adjoint fro {afro:.3e} max {amx:.3e}")
+    bf, bm = BOUNDS[name]
+    assert fro < bf and mx < bm
+    assert afro < bf and amx < bm

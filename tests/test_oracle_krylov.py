@@ -223,6 +223,18 @@ def test_tikhonov_matches_stacked_least_squares():
     assert np.allclose(y, y_ls, atol=1e-12)
 
 
+def test_metrics_worked_example():
+    """§4's relative error and SNR on a hand-worked 2-channel case
+    (tests/golden/metrics_worked.txt): pins the global mean of reading R17,
+    the squared norms and the base-10 dB scale."""
+    from conftest import load_golden
+    snr_ref, rel_ref = load_golden("metrics_worked.txt")[0]
+    X_hat = np.array([[[0.0, 2.0]], [[10.0, 12.0]]])
+    X = np.array([[[1.0, 2.0]], [[10.0, 14.0]]])
+    assert abs(mt.snr_db(X_hat, X) - snr_ref) < 1e-6
+    assert abs(mt.relative_error(X_hat, X) - rel_ref) < 1e-6
+
+
 def test_metrics():
     X = np.random.default_rng(15).uniform(size=(3, 8, 8))
     assert mt.relative_error(X, X) == 0.0
