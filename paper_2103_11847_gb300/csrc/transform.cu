@@ -12,6 +12,7 @@
 
 #include "tc_device.cuh"
 #include "tcgen05.cuh"
+#include "umma.cuh"
 
 namespace {
 
@@ -289,6 +290,7 @@ __global__ void k_round(const float* __restrict__ in, void* out, size_t n, int k
 // next tile's FP32 input is copied (cp.async) into the first 32 KB of the A
 // planes while this tile's epilogue runs. The reduction runs once a CTA.
 constexpr int TP = 128, TK = 64, TNT = 128;
+int g_tube_sms = 152;  // SM count of the device (set by transform_init)
 constexpr uint32_t TA_BYTES = TP * TK * 2;  // one BF16 plane of A: 16 KB
 constexpr uint32_t TB_BYTES = TK * TK * 2;  // one BF16 plane of B: 8 KB
 
@@ -511,6 +513,384 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
                  : "memory");
 }
 
+// ------------------------------------------- TMA-streamed tensor-core pass --
+// The same transform (D = in^T T^T per tile of TP = 128 pixels, operands
+// split into NS BF16 planes, FP32 accumulation) as a warp-specialised
+// persistent kernel, one CTA per SM, every tile moved by TMA through two
+// rings of 32 KB slots:
+//   warp 0 (one lane): input producer; loads tile t's input box [n3 slices x
+//     128 pixels] into input slot t % NI;
+//   warp 2 (one lane): prev producer; loads tile t's prev box into output
+//     slot t % 2 once that slot's previous store has read it (without prev
+//     it only hands the slot on);
+//   warps 3..10: split the staged input into the NS BF16 planes of A (same
+//     swizzled MN-major layout as k_tube; zero for slices >= n3). With two
+//     planes (32 KB, the slot's size) the split is written over the slot
+//     itself once all eight warps have read it, so A is as deep as the input
+//     ring and the split of the next tile does not wait for these MMAs; the
+//     three planes of the FP32-level form go to a separate A buffer;
+//   warp 1 (one lane): tcgen05.mma into accumulator buffer t % 2 (2 x 64
+//     tensor-memory columns); one commit frees the input slot (or the A
+//     buffer), another hands the accumulator to the epilogue;
+//   warps 11..18: epilogue; thread = pixel = tensor-memory lane, two warps a
+//     lane quadrant, each taking 32 of the 64 outputs. It writes ca v + cp
+//     prev over prev in the output slot (or the GEMM operand's BF16 or TF32
+//     tile), and one thread stores the slot by TMA and frees it once the
+//     store has read it.
+// Eight warps split and eight write back, so that the ALU work of both stays
+// behind the loads (with four each, the split alone took about a tile period).
+// (The three-plane BF16 operand of the FP32-level form, 48 KB a tile, does
+// not fit a slot; k_tube writes it.)
+// So input loads run up to NI tiles ahead and prev loads and stores overlap
+// the split and the MMAs of the next tiles. Requirements (checked by the
+// launcher, else k_tube runs): P % 8 == 0 (16-byte rows of the FP32 and BF16
+// boxes), 16-byte aligned tensors, no dot-product reduction.
+constexpr int TT_NT = 608;
+constexpr uint32_t TT_SLOT = TK * TP * 4;  // one FP32 box of 64 x 128: 32 KB
+// Slots: two planes (A in the input slot) 3 input + 3 output, or 4 + 4
+// half-size output slots for a BF16 output (16 KB a tile); three planes (a
+// separate A buffer, larger B) 2 + 2.
+constexpr int tube_tma_in(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
+constexpr int tube_tma_out(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
+constexpr uint32_t tube_tma_oslot(int out) { return out == OUT_BF16 ? TT_SLOT / 2 : TT_SLOT; }
+constexpr size_t tube_tma_smem(int ns, int out) {
+  return 1024 + tube_tma_in(ns, out) * TT_SLOT + tube_tma_out(ns, out) * tube_tma_oslot(out) +
+         (ns == 3 ? ns * TA_BYTES : 0) + ns * TB_BYTES +
+         (3 * tube_tma_in(ns, out) + 3 * tube_tma_out(ns, out) + 7) * 8 + 16;
+}
+
+template <int OUT, int NS>
+__global__ void __launch_bounds__(TT_NT, 1)
+k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
+           const __grid_constant__ CUtensorMap tmOut, const float* __restrict__ T, int n3,
+           size_t P, int has_prev, Epi ep, int* err) {
+  constexpr int NPASS = NS == 2 ? 3 : 6;
+  constexpr int NI = tube_tma_in(NS, OUT), NO = tube_tma_out(NS, OUT);
+  constexpr uint32_t OSLOT = tube_tma_oslot(OUT);
+  constexpr bool INPLACE = NS == 2;  // A planes over the input slot
+  using namespace tc5;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
+                             ((uint32_t)(TK >> 3) << 17) | ((uint32_t)(TP >> 4) << 24);
+  if (ep.skip && *ep.skip) return;
+  extern __shared__ uint8_t tt_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(tt_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sin = base;                    // NI input slots
+  uint8_t* sout = base + NI * TT_SLOT;    // NO prev / output slots
+  uint8_t* sAx = sout + NO * OSLOT;       // three planes: the A buffer
+  uint8_t* sB = sAx + (INPLACE ? 0 : NS * TA_BYTES);  // NS B planes
+  uint64_t* ifull = reinterpret_cast<uint64_t*>(sB + NS * TB_BYTES);  // [NI] input loaded
+  uint64_t* iempty = ifull + NI;          // [NI] input split (8 converter warps)
+  // A planes written (8 converter warps), one barrier an input slot: the
+  // converters may run up to NI tiles ahead of the MMAs when A is in place,
+  // more than one barrier's phase parity can tell apart
+  uint64_t* afull = iempty + NI;          // [NI]
+  uint64_t* ofull = afull + NI;           // [NO] output slot holds prev (or is free)
+  uint64_t* oempty = ofull + NO;          // [NO] output slot stored (read by the TMA store)
+  uint64_t* owrit = oempty + NO;          // [NO] output tile written (8 epilogue warps)
+  uint64_t* aempty = owrit + NO;          // the A buffer read by the MMAs (three planes)
+  uint64_t* dfull = aempty + 1;           // [2] accumulator ready
+  uint64_t* dempty = aempty + 3;          // [2] accumulator drained (8 epilogue warps)
+  uint64_t* fin = aempty + 5;             // every MMA of this CTA completed
+  uint64_t* cread = aempty + 6;           // the input slot read (8 converter warps)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(aempty + 7);
+  __shared__ int sh_fail;
+  __shared__ float sh_coef[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntile = (int)((P + TP - 1) / TP);
+  const uint32_t box = (uint32_t)n3 * TP * 4;  // bytes of one FP32 box
+  static_assert(OUT != OUT_BF16X3, "the three-plane operand is k_tube's");
+
+  if (tid == 0) {
+    for (int b = 0; b < NI; ++b) {
+      mbar_init(ifull + b, 1);
+      mbar_init(iempty + b, INPLACE ? 1 : 8);
+      mbar_init(afull + b, 8);
+    }
+    for (int b = 0; b < NO; ++b) {
+      mbar_init(ofull + b, 1);
+      mbar_init(oempty + b, 1);
+      mbar_init(owrit + b, 8);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(dfull + b, 1);
+      mbar_init(dempty + b, 8);
+    }
+    mbar_init(aempty, 1);
+    mbar_init(fin, 1);
+    mbar_init(cread, 8);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh_fail = 0;
+  }
+  if (OUT == OUT_F32) coef_compute(ep.coef, sh_coef);
+  if (warp >= 3 && warp < 11) {  // B = T once: unit u is row n = u / 8, slices 8 (u % 8) + 0..7
+    const int ct = tid - 96;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int u = ct + 256 * j, n = u >> 3, c = u & 7;
+      float t[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int l = 8 * c + e;
+        t[e] = (n < n3 && l < n3) ? __ldg(T + (size_t)n * n3 + l) : 0.f;
+      }
+      uint4 pl[NS];
+      split8<NS>(t, pl);
+      const uint32_t off = n * 128 + ((c ^ (n & 7)) << 4);
+#pragma unroll
+      for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(sB + q * TB_BYTES + off) = pl[q];
+    }
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tslot)),
+                 "r"(2 * TK)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  volatile int* vfail = &sh_fail;
+  float local = 0.f;
+  int issued = 0, issued_p = 0;  // tiles whose input (prev) loads were issued
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int s = i % NI;
+        const uint32_t u = (uint32_t)(i / NI) & 1u;
+        if (!mbar_wait(iempty + s, u ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        mbar_expect_tx(ifull + s, box);
+        tma_load_2d(sin + s * TT_SLOT, &tmIn, t * TP, 0, ifull + s);
+        issued = i + 1;
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int s = i % NO;
+        const uint32_t u = (uint32_t)(i / NO) & 1u;
+        if (!mbar_wait(oempty + s, u ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        if (has_prev) {
+          mbar_expect_tx(ofull + s, box);
+          tma_load_2d(sout + s * OSLOT, &tmPrev, t * TP, 0, ofull + s);
+          issued_p = i + 1;
+        } else {
+          mbar_arrive(ofull + s);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int d = i & 1;
+        const uint32_t u = (uint32_t)(i >> 1) & 1u;
+        if (!mbar_wait(afull + i % NI, (uint32_t)(i / NI) & 1u) ||
+            !mbar_wait(dempty + d, u ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(d * TK);
+        uint8_t* sA = INPLACE ? sin + (i % NI) * TT_SLOT : sAx;
+#pragma unroll
+        for (int pass = 0; pass < NPASS; ++pass) {
+          const uint32_t a0 = su32(sA + tube_pa(pass) * TA_BYTES);
+          const uint32_t b0 = su32(sB + tube_pb(pass) * TB_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk)
+            umma<0>(acc, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
+                    smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+        }
+        umma_commit(INPLACE ? iempty + (i % NI) : aempty);  // the A planes are read
+        umma_commit(dfull + d);
+      }
+      umma_commit(fin);
+    }
+  } else if (warp < 11) {  // converters
+    const int ct = tid - 96;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+      if (__any_sync(0xffffffffu, *vfail)) break;
+      const int s = i % NI;
+      const uint32_t u = (uint32_t)(i / NI) & 1u;
+      bool ok = mbar_wait(ifull + s, u);
+      if (!INPLACE) ok = ok && mbar_wait(aempty, ((uint32_t)i & 1u) ^ 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        *vfail = 1;
+        break;
+      }
+      uint8_t* slot = sin + s * TT_SLOT;
+      const float* stg = reinterpret_cast<const float*>(slot);
+      float x[4][8];  // four units: slice l, pixels 8 c .. 8 c + 7
+#pragma unroll
+      for (int i8 = 0; i8 < 4; ++i8) {
+        const int uu = ct + 256 * i8, l = uu >> 4, c = uu & 15;
+        if (l < n3) {
+          const float4 a = *reinterpret_cast<const float4*>(stg + l * TP + 8 * c);
+          const float4 b = *reinterpret_cast<const float4*>(stg + l * TP + 8 * c + 4);
+          x[i8][0] = a.x; x[i8][1] = a.y; x[i8][2] = a.z; x[i8][3] = a.w;
+          x[i8][4] = b.x; x[i8][5] = b.y; x[i8][6] = b.z; x[i8][7] = b.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[i8][e] = 0.f;
+        }
+      }
+      if (INPLACE) {  // every warp has read the slot before any writes over it
+        __syncwarp();
+        if (lane == 0) mbar_arrive(cread);
+        if (!__all_sync(0xffffffffu, mbar_wait(cread, (uint32_t)i & 1u))) {
+          *vfail = 1;
+          break;
+        }
+      }
+      uint8_t* sA = INPLACE ? slot : sAx;
+#pragma unroll
+      for (int i8 = 0; i8 < 4; ++i8) {
+        const int uu = ct + 256 * i8, l = uu >> 4, c = uu & 15;
+        uint4 pl[NS];
+        split8<NS>(x[i8], pl);
+        const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
+#pragma unroll
+        for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(sA + q * TA_BYTES + off) = pl[q];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(afull + s);
+        if (!INPLACE) mbar_arrive(iempty + s);  // this warp has read the input slot
+      }
+    }
+  } else {  // epilogue warps 11..18: tensor-memory lanes 32 (warp % 4) .., columns 32 hh ..
+    const int qd = warp & 3, hh = (warp - 11) >> 2, px = 32 * qd + lane, et = tid - 352;
+    const float ca = OUT == OUT_F32 ? sh_coef[0] : 1.f, cp = OUT == OUT_F32 ? sh_coef[1] : 0.f;
+    int i = 0;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+      if (__any_sync(0xffffffffu, *vfail)) break;
+      const int s = i % NO, d = i & 1;
+      const uint32_t u = (uint32_t)(i / NO) & 1u, ud = (uint32_t)(i >> 1) & 1u;
+      bool ok = mbar_wait(dfull + d, ud);
+      ok = ok && mbar_wait(ofull + s, u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        *vfail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      uint8_t* so = sout + s * OSLOT;  // prev in, output out (same element, same thread)
+      const size_t p = (size_t)t * TP + px;
+      const bool live = p < P;
+      {
+        const int h = hh;
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(d * TK + 32 * h), v);
+        // this warp's part of the accumulator is read: hand it back
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(dempty + d);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int k = 32 * h + j;
+          if (k >= n3) continue;
+          const int o = k * TP + px;
+          if (OUT == OUT_BF16) {
+            reinterpret_cast<__nv_bfloat16*>(so)[o] = __float2bfloat16_rn(v[j]);
+          } else if (OUT == OUT_TF32) {
+            reinterpret_cast<float*>(so)[o] = round_tf32(v[j]);
+          } else {
+            float* f = reinterpret_cast<float*>(so);
+            float y = ca * v[j];
+            if (has_prev) y = fmaf(cp, f[o], y);
+            f[o] = y;
+            if (live) local = fmaf(y, y, local);
+          }
+        }
+      }
+      // every thread's writes to the async proxy, one arrival a warp; the
+      // storing thread waits (bounded) for all eight warps (a failed wait
+      // only raises the flag: each warp leaves the loop at its next check)
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(owrit + s);
+      // One store stays in flight: once this tile's store is issued, the
+      // previous one has read its slot, which goes back to the prev producer.
+      if (et == 0) {
+        if (mbar_wait(owrit + s, u)) {
+          tma_store_2d(&tmOut, t * TP, 0, so);
+          bulk_commit();
+          if (i > 0) {
+            bulk_wait_read1();
+            mbar_arrive(oempty + (i - 1) % NO);
+          }
+        } else {
+          *vfail = 1;
+        }
+      }
+    }
+    if (et == 0) {  // the last store's slot (and every store) done
+      bulk_wait_all();
+      if (i > 0 && !*vfail) mbar_arrive(oempty + (i - 1) % NO);
+    }
+  }
+
+  // wind down: every thread of the CTA
+  __syncthreads();
+  const bool failed = *vfail != 0;
+  if (warp == 1 && lane == 0) mbar_wait(fin, 0);  // the MMAs have finished with TMEM
+  if (failed && warp == 0 && lane == 0) {          // let the input loads this CTA issued land
+    for (int g = (issued > NI ? issued - NI : 0); g < issued; ++g)
+      mbar_wait(ifull + g % NI, (uint32_t)(g / NI) & 1u);
+    atomicExch(err, TC_ETIMEOUT);
+  }
+  if (failed && warp == 2 && lane == 0) {  // and the prev loads
+    for (int g = (issued_p > NO ? issued_p - NO : 0); g < issued_p; ++g)
+      mbar_wait(ofull + g % NO, (uint32_t)(g / NO) & 1u);
+  }
+  if (OUT == OUT_F32 && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TK)
+                 : "memory");
+}
+
+// The TMA form when its requirements hold: P % 8 == 0 (16-byte rows of the
+// FP32 and BF16 boxes), 16-byte aligned tensors, no dot-product reduction.
+bool tube_tma_ok(const float* in, const void* out, size_t P, const Epi& ep) {
+  auto al = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  return P % 8 == 0 && P / TP < (1u << 30) && al(in) && al(out) && al(ep.prev) &&
+         ep.red.other == nullptr;
+}
+
+template <int OUT, int NS>
+int run_tube_tma(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
+                 int* err, cudaStream_t st) {
+  CUtensorMap mi, mp, mo;
+  TC_TRY(make_tmap_2d(&mi, in, 0, P, (size_t)n3, TP, n3));
+  const int hp = (OUT == OUT_F32 && ep.prev) ? 1 : 0;
+  if (hp)
+    TC_TRY(make_tmap_2d(&mp, ep.prev, 0, P, (size_t)n3, TP, n3));
+  else
+    mp = mi;
+  TC_TRY(make_tmap_2d(&mo, out, OUT == OUT_BF16 ? 1 : 0, P, (size_t)n3, TP, n3));
+  const size_t ntile = (P + TP - 1) / TP;
+  const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
+  k_tube_tma<OUT, NS><<<grid, TT_NT, tube_tma_smem(NS, OUT), st>>>(mi, mp, mo, T, n3, P, hp, ep,
+                                                                   err);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 }  // namespace
 
 int launch_mode3(const float* in, float* out, const float* T_dev, int n3, size_t P,
@@ -539,7 +919,6 @@ int init_kpw() {
 }  // namespace
 
 namespace {
-int g_tube_sms = 152;  // SM count of the device (set by transform_init)
 
 // persistent grid: tube_ctas(ns) CTAs a SM, no more than one a tile
 unsigned tube_grid(size_t P, int ns) {
@@ -551,6 +930,9 @@ unsigned tube_grid(size_t P, int ns) {
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
                     const Epi& ep, int* err, cudaStream_t st, int split3) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
+  if (tube_tma_ok(in, out, P, ep))
+    return split3 ? run_tube_tma<OUT_F32, 3>(in, out, T_dev, n3, P, ep, err, st)
+                  : run_tube_tma<OUT_F32, 2>(in, out, T_dev, n3, P, ep, err, st);
   if (split3)
     k_tube<OUT_F32, 3><<<tube_grid(P, 3), TNT, tube_smem(3), st>>>(in, out, T_dev, n3, P, ep, err);
   else
@@ -564,6 +946,12 @@ int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3,
   TC_CHECK(n3 >= 1 && n3 <= TK);
   Epi ep;
   ep.skip = skip;
+  // the three-plane operand (48 KB a tile, stored directly by the TMA form)
+  // measured faster on k_tube's four CTAs a SM
+  if (kind != ROUND_BF16X3 && tube_tma_ok(in, out, P, ep)) {
+    if (kind == ROUND_BF16) return run_tube_tma<OUT_BF16, 2>(in, out, T_dev, n3, P, ep, err, st);
+    return run_tube_tma<OUT_TF32, 2>(in, out, T_dev, n3, P, ep, err, st);
+  }
   if (kind == ROUND_BF16X3)
     k_tube<OUT_BF16X3, 3><<<tube_grid(P, 3), TNT, tube_smem(3), st>>>(in, out, T_dev, n3, P, ep,
                                                                         err);
@@ -583,6 +971,14 @@ int transform_init() {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared));
   }
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(2, OUT_F32)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_BF16, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(2, OUT_BF16)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_TF32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(2, OUT_TF32)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(3, OUT_F32)));
   for (auto fn : {k_tube<OUT_F32, 3>, k_tube<OUT_BF16X3, 3>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tube_smem(3)));

@@ -451,6 +451,24 @@ int make_tmap(CUtensorMap* map, const void* base, int bf16, int inner, int rows,
   return r == CUDA_SUCCESS ? TC_OK : TC_EINVAL;
 }
 
+int make_tmap_2d(CUtensorMap* map, const void* base, int bf16, size_t inner, size_t rows,
+                 int box_inner, int box_rows) {
+  if (!g_encode) return TC_EUNSUPPORTED;
+  const cuuint64_t es = bf16 ? 2 : 4;
+  if ((reinterpret_cast<uintptr_t>(base) & 15) != 0 || ((cuuint64_t)inner * es) % 16 != 0 ||
+      ((cuuint64_t)box_inner * es) % 16 != 0 || box_inner > 256 || box_rows > 256)
+    return TC_EINVAL;
+  cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)inner * es};
+  cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                        2, const_cast<void*>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? TC_OK : TC_EINVAL;
+}
+
 // A operand: M x K per slice, K contiguous. B operand: K x N with N contiguous
 // (BF16), or its transpose N x K with K contiguous (TF32).
 int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, int N, int K,

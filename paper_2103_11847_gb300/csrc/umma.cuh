@@ -27,3 +27,9 @@ int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStre
 // planes, plane q at dlow + q slices M N).
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st);
+// 2-D tiled map over a rows x inner row-major tensor (FP32, or BF16 with
+// bf16 = 1), box (box_inner, box_rows), no swizzle, zero fill out of bounds.
+// The base must be 16-byte aligned and a row a multiple of 16 bytes.
+int make_tmap_2d(CUtensorMap* map, const void* base, int bf16, size_t inner, size_t rows,
+                 int box_inner, int box_rows);
+
