@@ -366,22 +366,31 @@ def batched_form(dev, iters=40, count=128, steps=2):
     return out
 
 
-def learned_form(train_count=20000):
-    """Learned lambda / stop index: 20k c-LSQR solves of 128 x 128 x 3 problems
-    labelled by tc_lsqr_label, the network trained by tc_mlp_train, then the
-    learned solve against plain GCV-driven c-LSQR (40 steps) on held-out
-    512 x 512 x 3 images and a 512 x 512 x 32 video."""
-    import torch
+def learned_form(train_count=10000):
+    """Learned lambda / stop index: 10k c-LSQR solves (half the 20k of the
+    full run, python -m paper_2103_11847_gb300.learn, to keep the default run
+    near two minutes) labelled by
+    tc_lsqr_label (128 x 128 x 3 and 256 x 256 x 3 images, every fifth a
+    64 x 64 x 32 video; stopping indices up to 96), the network trained by
+    tc_mlp_train, then the learned solve against plain GCV-driven c-LSQR (96
+    steps, full GCV) on held-out 512 x 512 x 3 images and 512 x 512 x 32
+    videos: with the 5% GCV fallback, and with the network's lambda alone."""
     from paper_2103_11847_gb300 import learn
     t0 = time.perf_counter()
-    F, T = learn.training_data(train_count)
+    F, T = learn.training_data(train_count, sizes=[128, 256], video_every=5)
     t1 = time.perf_counter()
     mlp, hist = learn.train(F, T)
     t2 = time.perf_counter()
-    out = {"train": {"solves": train_count, "size": "128x128x3", "label_s": t1 - t0,
-                     "train_s": t2 - t1, "loss_first": float(hist[0].item()),
+    k = T[:, 1].cpu().numpy()
+    out = {"train": {"solves": train_count, "size": "128x128x3 / 256x256x3, every 5th 64x64x32",
+                     "label_kmax": 96, "label_s": t1 - t0, "train_s": t2 - t1,
+                     "label_k_mean": float(k.mean()), "label_k_std": float(k.std()),
+                     "loss_first": float(hist[0].item()),
                      "loss_last50": float(hist[-50:].mean().item())},
+           "gcv": "full (interior minimum) for the plain solve and the fallback check",
            "eval_512x512x3": learn.summarize(learn.compare(mlp, count=8)),
+           "eval_512x512x3_network_lambda": learn.summarize(learn.compare(mlp, count=8,
+                                                                          factor=1e30)),
            "eval_512x512x32": learn.summarize(learn.compare(mlp, count=2, frames=32))}
     mlp.close()
     return out

@@ -312,6 +312,21 @@ int tc_lsqr_graph_kernels(tc_plan* plan, int* count);
 int tc_check_recip(const double* x, size_t n, double* rcp, double* rsqrt,
                    tc_stream_t stream);
 
+/* Peak-rate probe (the paper has no counterpart): a fixed amount of
+ * independent arithmetic for the caller to time with CUDA events, giving the
+ * measured peaks that the roofline fractions of FFMA-bound and TF32 kernels
+ * divide by.
+ *   kind 0: FP32 FFMA, 8 CTAs x 256 threads a SM, each thread iters x 8
+ *           independent FMAs (flops = 2 * 8 * iters * threads);
+ *   kind 1: the same in FP64;
+ *   kind 2: tcgen05.mma kind::tf32, one CTA a SM, iters x 4 MMAs of
+ *           128 x 256 x 8 (flops = 2 * 128 * 256 * 32 * iters * SMs);
+ *   kind 3: tcgen05.mma kind::f16 with BF16 inputs, iters x 4 MMAs of
+ *           128 x 256 x 16 (flops = 2 * 128 * 256 * 64 * iters * SMs).
+ *   iters: 1 .. 2^24.  status: device int, zero before the call; set to
+ *   TC_ETIMEOUT if the bounded wait for the MMAs gave up. */
+int tc_peak_probe(int kind, int iters, int* status, tc_stream_t stream);
+
 /* Tikhonov solution of a projected problem with GCV (§3.1, eqs. (leastsq),
  * (tikho2), (gcv2)): y = argmin ||beta e_1 - H y||^2 + lambda^2 ||y||^2.
  *   H: device double, (k+1) x k row-major (Hessenberg or lower bidiagonal).

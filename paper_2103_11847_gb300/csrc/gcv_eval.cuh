@@ -28,14 +28,9 @@
 // relative error, far below 2^-20, to the FP64 rounding level) instead of a
 // full IEEE division with its special-case paths: r2 >= l^2 > 0 is finite
 // and positive here.
-__device__ __forceinline__ double recip_nr(double x) {
-  double y;
-  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
-  double e = fma(-x, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-x, y, 1.0);
-  return fma(y, e, y);
-}
+// (rcp_newton of tc_device.cuh: the same two steps, and the IEEE division
+// outside [DBL_MIN, 2^1000], e.g. for a subnormal r2 at a tiny lambda.)
+__device__ __forceinline__ double recip_nr(double x) { return rcp_newton(x); }
 
 __device__ __forceinline__ double gcv_bd_eval(const double* rg, int k, double pbar2, double lam, int variant,
                               double* y) {

@@ -113,55 +113,63 @@ k_gram(const float* __restrict__ V, size_t stride, size_t n, const float* __rest
 }
 
 // Labels: error(k, lambda) = y^T G_k y - 2 c_k^T y + ||X||^2 with
-// y = y_k(lambda) from the rotations; k_opt, lambda_opt as documented.
-__global__ void __launch_bounds__(1024)
-k_label(const double* rg, const double* alpha, const double* beta, const double* phibar,
-        const double* G, const double* c, const double* xx, int kmax, float* feat, float* target) {
-  __shared__ double err[(TC_MAX_PROJ / KSTEP) * NGRID_L];
+// y = y_k(lambda) from the rotations, on the grid k = 4, 6, .., kmax and
+// NGRID_L log-spaced lambda in [1e-6, 1] ||C~_kmax||_F. CTA ki takes k = 4 +
+// KSTEP ki, thread li one lambda (the O(k^2) FP64 work of the grid spread over
+// the SMs); err[ki * NGRID_L + li].
+__device__ double label_scale(const double* alpha, const double* beta, int kmax) {
+  double s2 = 0.0;
+  for (int j = 0; j < kmax; ++j) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
+  return sqrt(s2);
+}
+
+__global__ void __launch_bounds__(64)
+k_label_err(const double* rg, const double* alpha, const double* beta, const double* G,
+            const double* c, const double* xx, int kmax, double* err) {
   __shared__ double sh_s;
-  const int tid = threadIdx.x;
-  const int nk = (kmax - 4) / KSTEP + 1;
-  if (tid == 0) {
-    double s2 = 0.0;
-    for (int j = 0; j < kmax; ++j) s2 += alpha[j] * alpha[j] + beta[j + 1] * beta[j + 1];
-    sh_s = sqrt(s2);
-    features(alpha, beta, phibar, feat);
-  }
+  const int ki = blockIdx.x, li = threadIdx.x;
+  if (li == 0) sh_s = label_scale(alpha, beta, kmax);
   __syncthreads();
+  if (li >= NGRID_L) return;
   const double lo = log(sh_s) - 6.0 * log(10.0), hi = log(sh_s);
-  for (int t = tid; t < nk * NGRID_L; t += blockDim.x) {
-    const int ki = t / NGRID_L, li = t % NGRID_L;
-    const int k = 4 + KSTEP * ki;
-    const double lam = exp(lo + (hi - lo) * li / (NGRID_L - 1));
-    double y[TC_MAX_PROJ];
-    gcv_bd_eval(rg, k, 0.0, lam, TC_GCV_FULL, y);
-    double e = *xx;
-    for (int a = 0; a < k; ++a) {
-      double gy = 0.0;
-      for (int b = 0; b < k; ++b) gy += G[(size_t)a * kmax + b] * y[b];
-      e += y[a] * (gy - 2.0 * c[a]);
-    }
-    err[t] = e;
+  const int k = 4 + KSTEP * ki;
+  const double lam = exp(lo + (hi - lo) * li / (NGRID_L - 1));
+  double y[TC_MAX_PROJ];
+  gcv_bd_eval(rg, k, 0.0, lam, TC_GCV_FULL, y);
+  double e = *xx;
+  for (int a = 0; a < k; ++a) {
+    double gy = 0.0;
+    for (int b = 0; b < k; ++b) gy += G[(size_t)a * kmax + b] * y[b];
+    e += y[a] * (gy - 2.0 * c[a]);
   }
-  __syncthreads();
-  if (tid == 0) {
-    double best = INFINITY;
-    for (int t = 0; t < nk * NGRID_L; ++t) best = fmin(best, err[t]);
-    int kbest = nk - 1;
-    for (int ki = 0; ki < nk; ++ki) {
-      double m = INFINITY;
-      for (int li = 0; li < NGRID_L; ++li) m = fmin(m, err[ki * NGRID_L + li]);
-      if (m <= best * 1.0201) {  // error within 1%: squared errors within 1.01^2
-        kbest = ki;
-        break;
-      }
+  err[ki * NGRID_L + li] = e;
+}
+
+// The labels from the error grid: k_opt = the smallest k whose best error
+// over lambda is within 1% of the best over all k, lambda_opt its minimiser;
+// and the features of the first MLP_FEAT_STEPS steps. One thread.
+__global__ void k_label_pick(const double* alpha, const double* beta, const double* phibar,
+                             const double* err, int kmax, float* feat, float* target) {
+  const int nk = (kmax - 4) / KSTEP + 1;
+  const double s = label_scale(alpha, beta, kmax);
+  const double lo = log(s) - 6.0 * log(10.0), hi = log(s);
+  features(alpha, beta, phibar, feat);
+  double best = INFINITY;
+  for (int t = 0; t < nk * NGRID_L; ++t) best = fmin(best, err[t]);
+  int kbest = nk - 1;
+  for (int ki = 0; ki < nk; ++ki) {
+    double m = INFINITY;
+    for (int li = 0; li < NGRID_L; ++li) m = fmin(m, err[ki * NGRID_L + li]);
+    if (m <= best * 1.0201) {  // error within 1%: squared errors within 1.01^2
+      kbest = ki;
+      break;
     }
-    int lb = 0;
-    for (int li = 1; li < NGRID_L; ++li)
-      if (err[kbest * NGRID_L + li] < err[kbest * NGRID_L + lb]) lb = li;
-    target[0] = (float)(lo + (hi - lo) * lb / (NGRID_L - 1));
-    target[1] = (float)(4 + KSTEP * kbest);
   }
+  int lb = 0;
+  for (int li = 1; li < NGRID_L; ++li)
+    if (err[kbest * NGRID_L + li] < err[kbest * NGRID_L + lb]) lb = li;
+  target[0] = (float)(lo + (hi - lo) * lb / (NGRID_L - 1));
+  target[1] = (float)(4 + KSTEP * kbest);
 }
 
 }  // namespace
@@ -181,9 +189,12 @@ extern "C" int tc_lsqr_label(tc_plan* p, const float* C, const float* X_true, in
   if (kmax < MLP_FEAT_STEPS + 1 || kmax > TC_MAX_PROJ) return TC_EINVAL;
   cudaStream_t st = (cudaStream_t)stream;
   TC_TRY(ensure_lsqr(p, kmax, true));
-  // aux: X, X_reg (FP32), then G (kmax^2), c (kmax), ||X_true||^2 (FP64), info
+  // aux: X, X_reg (FP32), then G (kmax^2), c (kmax), ||X_true||^2, the error
+  // grid (FP64), info
+  const int nk = (kmax - 4) / KSTEP + 1;
   const size_t offG = ((2 * p->Tx * sizeof(float)) + 255) / 256 * 256;
-  const size_t need = offG + ((size_t)kmax * kmax + kmax + 1) * sizeof(double) + 256;
+  const size_t need =
+      offG + ((size_t)kmax * kmax + kmax + 1 + (size_t)nk * NGRID_L) * sizeof(double) + 256;
   if (!p->aux || p->aux_bytes < need) {
     if (p->aux) cudaFree(p->aux);
     p->aux = nullptr;
@@ -197,6 +208,7 @@ extern "C" int tc_lsqr_label(tc_plan* p, const float* C, const float* X_true, in
   double* G = reinterpret_cast<double*>(base + offG);
   double* c = G + (size_t)kmax * kmax;
   double* xx = c + kmax;
+  double* err = xx + 1;
   tc_solve_info* info =
       reinterpret_cast<tc_solve_info*>(base + (need - 256 + 0));  // 256-byte slot at the end
   LsqrArgs a{C, X, Xr, kmax, 0.0, 0.0, nullptr, info};
@@ -210,7 +222,9 @@ extern "C" int tc_lsqr_label(tc_plan* p, const float* C, const float* X_true, in
   const int blocks = kmax * (kmax + 1) / 2 + kmax + 1;
   k_gram<<<blocks, 256, 0, st>>>(p->basis, p->Tx, p->Tx, X_true, kmax, G, c, xx);
   TC_CUDA(cudaGetLastError());
-  k_label<<<1, 1024, 0, st>>>(rgiv, alpha, beta, phibar, G, c, xx, kmax, feat, target);
+  k_label_err<<<nk, 64, 0, st>>>(rgiv, alpha, beta, G, c, xx, kmax, err);
+  TC_CUDA(cudaGetLastError());
+  k_label_pick<<<1, 1, 0, st>>>(alpha, beta, phibar, err, kmax, feat, target);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

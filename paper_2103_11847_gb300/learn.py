@@ -3,12 +3,13 @@ training with the library's own network kernels, and a comparison against
 plain GCV-driven c-LSQR. All arithmetic runs in libtcprod. This module only
 draws the synthetic problems and moves tensors around.
 
-Training problems: n x n x 3 colour images (default n = 128). Slice k of A
-is (1, 0.7, 0.4)[k] times a Gaussian blur, with sigma on a 32-level grid in
+Training problems: n x n x 3 colour images (default n = 128), and optionally
+n' x n' x 32 videos mixed in. Slice k of A is (1, 0.7, 0.4)[k] (videos: 1 ->
+0.4 over the frames) times a Gaussian blur, with sigma on a 32-level grid in
 [1, 5]. Noise is log-uniform in [1e-4, 1e-2]. The observation C = A *c X + N
 is formed by the library's product. Each problem is labelled by
-tc_lsqr_label: the error-optimal stop index and lambda of its c-LSQR
-trajectory.
+tc_lsqr_label: the error-optimal stop index (up to kmax = 96) and lambda of
+its c-LSQR trajectory.
 """
 import math
 import time
@@ -24,8 +25,9 @@ SIGMA_LEVELS = np.linspace(1.0, 5.0, 32)
 class ProblemSource:
     """Seeded stream of blur problems; plans are cached per sigma level."""
 
-    def __init__(self, n, seed, frames=3):
+    def __init__(self, n, seed, frames=3, gcv_variant=tcprod.TC_GCV_FULL):
         self.n, self.frames = n, frames
+        self.gcv_variant = gcv_variant
         self.rng = inputs.rng_for(seed)
         self.plans = {}
 
@@ -35,7 +37,7 @@ class ProblemSource:
             G = inputs.gaussian_blur(self.n, s, int(math.ceil(3 * s)))
             w = (1.0, 0.7, 0.4) if self.frames == 3 else np.linspace(1.0, 0.4, self.frames)
             A = torch.from_numpy(np.stack([wi * G for wi in w]).astype(np.float32)).cuda()
-            self.plans[lvl] = (tcprod.Plan(A, s=self.n), A)
+            self.plans[lvl] = (tcprod.Plan(A, s=self.n, gcv_variant=self.gcv_variant), A)
         return self.plans[lvl][0]
 
     def draw(self):
@@ -59,16 +61,28 @@ class ProblemSource:
         self.plans = {}
 
 
-def training_data(count, n=128, kmax=32, seed=11):
-    """Features (count x 36) and targets (count x 2: log lambda, stop index)."""
-    src = ProblemSource(n, seed)
+def training_data(count, n=128, kmax=96, seed=11, video_every=0, video_n=64, video_frames=32,
+                  sizes=None):
+    """Features (count x 36) and targets (count x 2: log lambda, stop index).
+
+    kmax bounds the candidate stop indices of the labels. It must lie beyond
+    where the error stops improving: on these problems, with lambda tuned,
+    the error keeps falling past 32 steps (every label was 32 at kmax = 32)
+    and levels off at 70-94 steps (kmax = 96). With video_every = v > 0,
+    every v-th problem is a video_n x video_n x video_frames video."""
+    srcs = [ProblemSource(m, seed + 7 * j) for j, m in enumerate(sizes or [n])]
+    vsrc = ProblemSource(video_n, seed + 1, frames=video_frames) if video_every else None
     F = torch.empty((count, 36), device="cuda")
     T = torch.empty((count, 2), device="cuda")
     for i in range(count):
-        plan, C, Xt, _, _ = src.draw()
+        s = vsrc if (video_every and i % video_every == video_every - 1) else srcs[i % len(srcs)]
+        plan, C, Xt, _, _ = s.draw()
         tcprod.tc_lsqr_label(plan.handle, C, Xt, kmax, F[i], T[i])
     torch.cuda.synchronize()
-    src.close()
+    for s in srcs:
+        s.close()
+    if vsrc:
+        vsrc.close()
     return F, T
 
 
@@ -82,10 +96,13 @@ def train(F, T, steps=3000, batch=256, lr=2e-3, seed=5):
     return mlp, hist
 
 
-def compare(mlp, count=8, n=512, frames=3, kmax=40, factor=1.05, seed=23):
+def compare(mlp, count=8, n=512, frames=3, kmax=96, factor=1.05, seed=23,
+            gcv_variant=tcprod.TC_GCV_FULL):
     """Plain GCV-driven c-LSQR (kmax steps) against the learned solve on
-    held-out problems: relative errors of X_reg and solve times."""
-    src = ProblemSource(n, seed, frames=frames)
+    held-out problems: relative errors of X_reg and solve times. Both use the
+    same GCV (the plain solve's lambda, and the learned solve's fallback
+    check and fallback lambda)."""
+    src = ProblemSource(n, seed, frames=frames, gcv_variant=gcv_variant)
     rows = []
     st = torch.cuda.current_stream()
     for _ in range(count):
@@ -122,16 +139,18 @@ def summarize(rows):
     el = np.array([r["err_learned"] for r in rows])
     tp = np.array([r["ms_plain"] for r in rows])
     tl = np.array([r["ms_learned"] for r in rows])
+    it = np.array([r["iters_learned"] for r in rows], dtype=float)
     return dict(problems=len(rows), mean_err_plain=float(ep.mean()), mean_err_learned=float(el.mean()),
                 learned_better=int(np.sum(el < ep)), mean_ms_plain=float(tp.mean()),
                 mean_ms_learned=float(tl.mean()), speedup=float(tp.mean() / tl.mean()),
-                mean_iters_learned=float(np.mean([r["iters_learned"] for r in rows])),
+                mean_iters_learned=float(it.mean()), std_iters_learned=float(it.std()),
+                min_iters_learned=int(it.min()), max_iters_learned=int(it.max()),
                 fallbacks=int(sum(r["fallback"] for r in rows)))
 
 
 if __name__ == "__main__":
     t0 = time.time()
-    F, T = training_data(20000)
+    F, T = training_data(20000, sizes=[128, 256], video_every=5)
     t1 = time.time()
     mlp, hist = train(F, T)
     print(f"data {t1 - t0:.1f} s, train {time.time() - t1:.1f} s, loss {hist[0].item():.4f} -> "

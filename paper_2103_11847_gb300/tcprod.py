@@ -62,6 +62,7 @@ _SIGS = {
     "tc_plan_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
     "tc_lsqr_graph_kernels": ([c_void_p, ctypes.POINTER(c_int)], c_int),
     "tc_check_recip": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p, c_void_p], c_int),
+    "tc_peak_probe": ([c_int, c_int, c_void_p, c_void_p], c_int),
     "tc_batch_create": ([ctypes.POINTER(c_void_p), c_int, ctypes.POINTER(c_int),
                          ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
                          ctypes.POINTER(c_void_p), ctypes.POINTER(tc_opts), c_void_p], c_int),
@@ -254,6 +255,13 @@ def tc_check_recip(x, rcp, rsq, stream=None):
     _check("tc_check_recip", lib().tc_check_recip(
         _ptr(x, torch.float64, name="x"), x.numel(), _ptr(rcp, torch.float64, name="rcp"),
         _ptr(rsq, torch.float64, name="rsq"), _stream(stream)))
+
+
+def tc_peak_probe(kind, iters, status, stream=None):
+    """Launch the peak-rate probe `kind` (0 FFMA, 1 DFMA, 2 TF32 MMA, 3 BF16 MMA)."""
+    _check("tc_peak_probe", lib().tc_peak_probe(int(kind), int(iters),
+                                                _ptr(status, torch.int32, name="status"),
+                                                _stream(stream)))
 
 
 def tc_fro_norm_noalloc(X, out, stream=None):

@@ -155,17 +155,26 @@ def test_learned_solve_stop_index_and_fallback(tc):
     src.close()
 
 
-def test_learned_gain_small(tc):
-    # A small training run (640 problems of 64 x 64 x 3), evaluated on 12
-    # held-out 64 x 64 x 3 problems against plain GCV-driven c-LSQR (32 steps).
+def test_learned_gain_on_held_out_problems(tc):
+    # Trained on 2000 solves of 64 x 64 x 3 problems (labels up to kmax = 96),
+    # evaluated on 16 held-out problems of the same size against plain
+    # c-LSQR with 96 steps and the lambda of the full GCV (the interior-minimum
+    # variant, the same GCV as the learned solve's fallback check). Measured
+    # on a GB300: plain 0.237 mean error; learned with the 5% GCV fallback
+    # 0.225 (the check replaces the network's lambda on 15 of 16 problems, so
+    # the gain comes from the predicted stopping index); learned without the
+    # fallback 0.155, lower on 10 of 16. Predicted stopping indices 61..96.
     from paper_2103_11847_gb300 import learn
-    F, T = learn.training_data(640, n=64, kmax=32, seed=41)
+    F, T = learn.training_data(2000, n=64, kmax=96, seed=41)
     mlp, hist = learn.train(F, T, steps=1500, batch=128, lr=2e-3)
-    rows = learn.compare(mlp, count=12, n=64, kmax=32, seed=43)
-    s = learn.summarize(rows)
-    print(s)
-    assert hist[-50:].mean().item() < hist[:5].mean().item()
-    # the predicted stop index stays in range, and the learned solve's error
-    # stays within 10% of GCV's (the full-size comparison is in bench.py)
-    assert 13 <= s["mean_iters_learned"] <= 32
-    assert s["mean_err_learned"] < 1.1 * s["mean_err_plain"]
+    assert hist[-50:].mean().item() < 0.5 * hist[:5].mean().item()
+    s = learn.summarize(learn.compare(mlp, count=16, n=64, kmax=96, seed=43))
+    s_net = learn.summarize(learn.compare(mlp, count=16, n=64, kmax=96, seed=43, factor=1e30))
+    print(s, s_net)
+    # the stopping index is learned, not a constant at the ceiling
+    assert s["std_iters_learned"] > 3.0 and s["min_iters_learned"] < s["max_iters_learned"]
+    # a gain in error over plain GCV-driven c-LSQR, with and without the fallback
+    assert s["mean_err_learned"] <= 0.98 * s["mean_err_plain"]
+    assert s_net["mean_err_learned"] <= 0.8 * s_net["mean_err_plain"]
+    assert s_net["fallbacks"] == 0
+    mlp.close()
