@@ -610,11 +610,16 @@ def roofline_line(dk, ms, peaks, src_peaks):
     elif dk["bound"] == "tensor":
         # FP32-level (BF16X3): six BF16 products per product; TF32 runs at half
         # the BF16 rate (the recipe's nominal ratio); BF16 at the BF16 rate
-        div = {"bf16x3": 6.0, "tf32": 2.0, "bf16": 1.0}[dk.get("precision", "bf16x3")]
-        peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / div
+        prec = dk.get("precision", "bf16x3")
+        tf = measured_peak("tf32_mma_tflops") if prec == "tf32" else None
+        if tf is not None:
+            peak, psrc = tf, "profiles/peaks.json tf32_mma_tflops (measured tcgen05 TF32 rate)"
+        else:
+            div = {"bf16x3": 6.0, "tf32": 2.0, "bf16": 1.0}[prec]
+            peak = peaks.get("bf16_tflops", FALLBACK_BF16_TFLOPS) / div
+            psrc = f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / {div:g}"
         ach = dk["work"] / (ms * 1e-3) / 1e12
         unit = "TFLOP/s"
-        psrc = f"MEASURED_PEAKS.json bf16_tflops ({src_peaks}) / {div:g}"
         extra = {"algorithmic_flops": dk["work"]}
     else:
         fp = measured_peak("fp32_ffma_tflops")
