@@ -320,7 +320,7 @@ def batched_form(dev, iters=40, count=128, steps=2):
         Cs.append((w, A))
     out = {"workload": f"{count} problems n x n x 3, n in {{64..512}} (sum n^2 = "
                        f"{sum(n * n for n in sizes)}), c-LSQR {iters} it + Tikhonov/GCV",
-           "launch": "one CUDA graph of per-problem child graphs"}
+           "launch": "one CUDA graph a batch (see each form)"}
     C_by_product = {}
     st = torch.cuda.current_stream()
     forms = (("fp32", tcprod.TC_FP32, tcprod.TC_TH), ("bf16", tcprod.TC_BF16, tcprod.TC_TH),
@@ -351,9 +351,16 @@ def batched_form(dev, iters=40, count=128, steps=2):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / steps
         errs = [float((Xr[i] - Xt[i]).norm() / Xt[i].norm()) for i in range(count)]
+        grouped, tile, tune = tcprod.tc_batch_info(h)
         out[name] = {"solves_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
                      "iters_per_s": count * iters / (ms * 1e-3),
-                     "mean_rel_err_reg": float(np.mean(errs))}
+                     "mean_rel_err_reg": float(np.mean(errs)),
+                     "form": ("grouped launches (one a phase for all problems), tile shape "
+                              "%s picked by the autotuner (forward product %.2f / %.2f / "
+                              "%.2f ms for 64x64 of 4x4, 32x32 of 4x2, 64x64 of 8x4)"
+                              % (["64x64 of 4x4", "32x32 of 4x2", "64x64 of 8x4"][tile],
+                                 tune[0], tune[1], tune[2]))
+                     if grouped else "one CUDA graph of per-problem child graphs"}
         tcprod.tc_batch_destroy(h)
     base = out["fp32"]["mean_rel_err_reg"]
     out["bf16"]["matched_error"] = bool(abs(out["bf16"]["mean_rel_err_reg"] - base) <= 0.02 * base)

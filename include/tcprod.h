@@ -200,10 +200,17 @@ int tc_gmres_c(tc_plan* plan, const float* C, const float* X0, float* X,
  *   C, X: host arrays[count] of device pointers (C[i]: n1[i] x s[i] x n3,
  *   X[i]: n2[i] x s[i] x n3). X_reg: host array of device pointers or NULL.
  *   infos: device array of count tc_solve_info.
- * Every problem's solve is captured as one child graph. The children go into a
- * single parent graph with no dependencies between them, launched once on
- * `stream`, so the problems run concurrently. The parent graph is cached while
- * the pointers and parameters stay the same. */
+ * Two forms, both replayed as one CUDA graph cached while the pointers and
+ * parameters stay the same:
+ *  - grouped (FP32 plans with n3 <= 4 and X_reg given): every phase of the
+ *    solve is one launch over all problems (a (problem, tile) work table, each
+ *    problem's own scalars, flags and deterministic reductions), about
+ *    3 itermax + 10 launches a batch. The tile shape of the fused products
+ *    (three candidates) is chosen on the first call by timing each on the
+ *    batch's forward product. Results equal tc_lsqr_c's up to the order of FP32
+ *    additions (the single solve may split K over a cluster);
+ *  - otherwise every problem's solve is captured as one child graph, side by
+ *    side in one parent graph, results bit for bit tc_lsqr_c's. */
 typedef struct tc_batch tc_batch;
 int tc_batch_create(tc_batch** batch, int count, const int* n1, const int* n2, const int* s,
                     int n3, const float* const* A, const tc_opts* opts, tc_stream_t stream);
@@ -211,6 +218,12 @@ int tc_batch_destroy(tc_batch* batch);
 int tc_lsqr_c_batched(tc_batch* batch, const float* const* C, float* const* X,
                       float* const* X_reg, int itermax, double tol, double lambda,
                       tc_solve_info* infos, tc_stream_t stream);
+/* mode 0: the grouped form where the plans allow it (the default), 1: child
+ * graphs always, -1: unchanged. Writes (host, each may be NULL) whether the
+ * last solve ran grouped, the tile shape the autotuner chose (-1 before; 0:
+ * 64 x 64 tiles of 4 x 4 a thread, 1: 32 x 32 of 4 x 2, 2: 64 x 64 of 8 x 4),
+ * and the candidates' forward-product times in ms (tune_ms[3]). */
+int tc_batch_info(tc_batch* batch, int mode, int* grouped, int* tile, float* tune_ms);
 
 /* ---- Learned lambda and stopping index --------------------------------------
  * None of this has a counterpart in the paper. A small network stands in for the

@@ -1,18 +1,21 @@
 // Batched c-LSQR: many independent problems of uneven sizes solved together.
 //
-// Each problem has its own plan: A~ resident, its own workspaces, reduction
-// scratch and device-side scalars. Its whole solve (Algorithm 6, then the
-// Tikhonov/GCV projection) is captured as a child graph. The children are
-// placed side by side in one parent graph with no edges between them, so one
-// cudaGraphLaunch submits the batch and the GPU runs the problems' kernels
-// concurrently: small problems fill the SMs that large ones leave idle. The
-// parent graph is kept and relaunched while the pointers and parameters
-// stay the same.
+// Each problem has its own plan: A~ resident, its own workspaces. Two forms:
+// * grouped (group.cu): plans on the fused FP32 route with X_reg requested.
+//   Every phase of the solve is one launch over all problems, the tile shape
+//   autotuned per batch, the whole sequence captured as one CUDA graph;
+// * otherwise each problem's whole solve (Algorithm 6, then the
+//   Tikhonov/GCV projection) is captured as a child graph, and the children
+//   sit side by side in one parent graph with no edges between them, so one
+//   cudaGraphLaunch submits the batch and the problems' kernels run
+//   concurrently.
+// Either graph is kept and relaunched while the pointers and parameters stay
+// the same.
 #include <cstring>
 #include <new>
 #include <vector>
 
-#include "tc_device.cuh"
+#include "group.cuh"
 
 struct tc_batch {
   int count = 0;
@@ -20,10 +23,13 @@ struct tc_batch {
   cudaStream_t cap = nullptr;
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;
+  GroupState grp;
+  int batch_mode = 0;  // 0: grouped where eligible, 1: child graphs always
 };
 
 extern "C" int tc_batch_destroy(tc_batch* b) {
   if (!b) return TC_EINVAL;
+  group_free(&b->grp);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->cap) cudaStreamDestroy(b->cap);
   for (tc_plan* p : b->plans)
@@ -71,7 +77,7 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
   std::memcpy(&tb, &tol, 8);
   std::memcpy(&lb, &lambda, 8);
   std::vector<uintptr_t> key = {(uintptr_t)itermax, (uintptr_t)tb, (uintptr_t)lb, (uintptr_t)infos,
-                                (uintptr_t)(X_reg != nullptr)};
+                                (uintptr_t)(X_reg != nullptr), (uintptr_t)b->batch_mode};
   for (int i = 0; i < n; ++i) {
     key.push_back((uintptr_t)C[i]);
     key.push_back((uintptr_t)X[i]);
@@ -79,7 +85,35 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
     key.push_back((uintptr_t)b->plans[i]->dscal);  // workspaces a capture depends on
     key.push_back((uintptr_t)b->plans[i]->basis);
   }
-  if (!b->exec || key != b->key) {
+  const bool grouped = b->batch_mode == 0 && group_eligible(b->plans, X_reg != nullptr);
+  if (grouped && (!b->exec || key != b->key)) {
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    TC_TRY(group_prepare(&b->grp, b->plans, C, X, X_reg, itermax, st));
+    TC_TRY(group_autotune(&b->grp, b->plans[0], st));
+    cudaGraph_t g = nullptr;
+    TC_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
+    const int rc = group_enqueue(&b->grp, b->plans[0], tol, lambda, infos, b->cap);
+    const cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+    if (rc != TC_OK || e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      if (rc != TC_OK) return rc;
+      tc_set_error("cudaStreamEndCapture", e);
+      return TC_ECUDA;
+    }
+    const cudaError_t e2 = cudaGraphInstantiate(&b->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) {
+      b->exec = nullptr;
+      tc_set_error("cudaGraphInstantiate", e2);
+      return TC_ECUDA;
+    }
+    b->key = key;
+  }
+  if (!grouped && (!b->exec || key != b->key)) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
       b->exec = nullptr;
@@ -127,3 +161,20 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
   TC_CUDA(cudaGraphLaunch(b->exec, (cudaStream_t)stream));
   return TC_OK;
 }
+
+extern "C" int tc_batch_info(tc_batch* b, int mode, int* grouped, int* tile, float* tune_ms) {
+  if (!b || mode < -1 || mode > 1) return TC_EINVAL;
+  if (mode >= 0 && mode != b->batch_mode) {
+    b->batch_mode = mode;
+    if (b->exec) {
+      cudaGraphExecDestroy(b->exec);
+      b->exec = nullptr;
+    }
+  }
+  if (grouped) *grouped = b->batch_mode == 0 && b->grp.cfg >= 0;
+  if (tile) *tile = b->grp.cfg >= 0 ? b->grp.cfg : -1;
+  if (tune_ms)
+    for (int c = 0; c < GROUP_CFGS; ++c) tune_ms[c] = b->grp.tune_ms[c];
+  return TC_OK;
+}
+

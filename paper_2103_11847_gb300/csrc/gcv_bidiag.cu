@@ -49,9 +49,16 @@ __device__ int warp_argmin(const double* v, int n) {
 }
 
 // One level of the search: warp w of CTA b evaluates grid point PPC b + w.
+// Grouped launches (grid.y = problems): problem blockIdx.y's doubles are ps
+// and its ints fsi further on (0 for a single problem).
 __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const double* alpha, const double* beta,
                                const int* kdev, int kmax, int variant, int level, double* lams,
-                               double* vals) {
+                               double* vals, size_t ps = 0, int fsi = 0) {
+  {
+    const size_t od = (size_t)blockIdx.y * ps;
+    rg += od; phibar += od; alpha += od; beta += od; lams += od; vals += od;
+    if (kdev) kdev += (size_t)blockIdx.y * fsi;
+  }
   const int k = kdev ? min(*kdev, kmax) : kmax;
   const int i = blockIdx.x * PPC + (threadIdx.x >> 5);
   if (i >= NGRID) return;
@@ -92,7 +99,16 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
 __global__ void k_gcv_bd_final(const double* rg, const double* phibar, const int* kdev, int kmax,
                                int variant, double lambda_in, const double* lams,
                                const double* vals, const double* lam_pred, double factor,
-                               int* fallback, double* lambda_out, double* y, double* gcv_out) {
+                               int* fallback, double* lambda_out, double* y, double* gcv_out,
+                               size_t ps = 0, int fsi = 0) {
+  {
+    const size_t od = (size_t)blockIdx.x * ps, oi = (size_t)blockIdx.x * fsi;
+    rg += od; phibar += od; lams += od; vals += od; lambda_out += od; y += od;
+    if (gcv_out) gcv_out += od;
+    if (lam_pred) lam_pred += od;
+    if (kdev) kdev += oi;
+    if (fallback) fallback += oi;
+  }
   const int k = kdev ? min(*kdev, kmax) : kmax;
   for (int j = (k > 0 ? k : 0) + (int)threadIdx.x; j < kmax; j += 32) y[j] = 0.0;
   double lam = lambda_in;
@@ -201,6 +217,26 @@ int launch_lcurve(const double* rg, const double* phibar, const int* kdev, int k
                   double* curve, double* y, int* kopt, cudaStream_t st) {
   TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ);
   k_lcurve<<<1, TC_MAX_PROJ, 0, st>>>(rg, phibar, kdev, kmax, curve, y, kopt);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+int launch_gcv_bidiag_group(const double* rg, const double* phibar, const double* alpha,
+                            const double* beta, const int* kdev, int kmax, int variant,
+                            double lambda_in, double* work, double* lambda_out, double* y,
+                            double* gcv_out, int count, size_t ps, int fsi, cudaStream_t st) {
+  TC_CHECK(kmax >= 1 && kmax <= TC_MAX_PROJ && count >= 1 && count <= 65535);
+  double* lams = work;
+  double* vals = work + NLEVEL * NGRID;
+  if (!(lambda_in >= 0.0)) {
+    for (int level = 0; level < NLEVEL; ++level) {
+      k_gcv_bd_level<<<dim3((NGRID + PPC - 1) / PPC, count), 32 * PPC, 0, st>>>(
+          rg, phibar, alpha, beta, kdev, kmax, variant, level, lams, vals, ps, fsi);
+      TC_CUDA(cudaGetLastError());
+    }
+  }
+  k_gcv_bd_final<<<count, 32, 0, st>>>(rg, phibar, kdev, kmax, variant, lambda_in, lams, vals,
+                                       nullptr, 0.0, nullptr, lambda_out, y, gcv_out, ps, fsi);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }

@@ -15,6 +15,8 @@
 // n3 > TC_MAX_FUSED between separate transform passes.
 #include <cooperative_groups.h>
 
+#include <type_traits>
+
 #include "tc_device.cuh"
 
 namespace cg = cooperative_groups;
@@ -33,32 +35,24 @@ struct Smem {
   static constexpr int kFloats = kMain > kPart ? kMain : kPart;
 };
 
-// SPLIT: K is split over the cluster and the epilogue runs from the summed
-// partial tiles; otherwise (cluster of one) it runs from the registers.
-template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI, bool SPLIT>
-__global__ void __launch_bounds__((BM / TM) * (BN / TN))
-k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C, int M, int N,
-             int K, int kchunk, Fused f, Epi ep) {
+// The main loop of one fused tile: acc[k] += A_k (pro B)_k over K range
+// [kbeg, kend) for the BM x BN tile at (i0, j0), all NS slices, with register
+// double buffering (the next K tile's global loads are issued before the
+// current tile's FMAs). Fast path: one float4 per thread and slice for each of
+// the A and B tiles (16-byte aligned rows). sm: the Smem<..> floats.
+template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO>
+__device__ __forceinline__ void fused_tile_mainloop(const float* __restrict__ A,
+                                                    const float* __restrict__ B, int M, int N,
+                                                    int K, int kbeg, int kend, int i0, int j0,
+                                                    const Fused& f, float* sm,
+                                                    float (&acc)[NS][TM][TN]) {
   constexpr int TX = BN / TN;
   constexpr int NT = (BM / TM) * (BN / TN);
-  if (ep.skip && *ep.skip) return;
-  __shared__ __align__(16) float sm[Smem<NS, BM, BN, BK, SPLIT>::kFloats];
-  __shared__ float sh_coef[2];
   float(*As)[BK][BM] = reinterpret_cast<float(*)[BK][BM]>(sm);
   float(*Bs)[BK][BN] = reinterpret_cast<float(*)[BK][BN]>(sm + NS * BK * BM);
-  float* P = sm;  // partial tile [NS][BM][BN] after the main loop
-
-  cg::cluster_group cluster = cg::this_cluster();
-  const int KS = (int)cluster.num_blocks();
-  const int rank = (int)cluster.block_rank();
   const int tid = threadIdx.x;
   const int tx = tid % TX, ty = tid / TX;
-  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
-  const size_t sA = (size_t)M * K, sB = (size_t)K * N, sC = (size_t)M * N;
-  const int kbeg = rank * kchunk;
-  const int kend = min(K, kbeg + kchunk);
-
-  float acc[NS][TM][TN];
+  const size_t sA = (size_t)M * K, sB = (size_t)K * N;
 #pragma unroll
   for (int k = 0; k < NS; ++k)
 #pragma unroll
@@ -66,9 +60,6 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
 #pragma unroll
       for (int j = 0; j < TN; ++j) acc[k][i][j] = 0.f;
 
-  // Register double buffering: the next K tile's global loads are issued
-  // before the current tile's FMAs. Fast path: one float4 per thread and
-  // slice for each of the A and B tiles (16-byte aligned rows).
   static_assert(BM * BK == 4 * NT && BK * BN == 4 * NT, "one float4 per thread per tile");
   const bool vec = ((K | N) % 4 == 0) && ((reinterpret_cast<uintptr_t>(A) |
                                            reinterpret_cast<uintptr_t>(B)) & 15) == 0;
@@ -148,9 +139,12 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
 #pragma unroll
       for (int k = 0; k < NS; ++k) {
         float a[TM], b[TN];
-        if (TM == 4) {
-          const float4 av = *reinterpret_cast<const float4*>(&As[k][kk][ty * TM]);
-          a[0] = av.x; a[1] = av.y; a[2] = av.z; a[3] = av.w;
+        if constexpr (TM % 4 == 0) {  // float4 reads of the A column
+#pragma unroll
+          for (int q = 0; q < TM; q += 4) {
+            const float4 av = *reinterpret_cast<const float4*>(&As[k][kk][ty * TM + q]);
+            a[q] = av.x; a[q + 1] = av.y; a[q + 2] = av.z; a[q + 3] = av.w;
+          }
         } else {
 #pragma unroll
           for (int i = 0; i < TM; ++i) a[i] = As[k][kk][ty * TM + i];
@@ -165,38 +159,81 @@ k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
     }
     __syncthreads();
   }
+}
+
+// The store of a whole tile from the registers: Y_l = sum_k epi[l][k] acc[k]
+// (EPI) back to the spatial domain, out = ca Y + cp prev; returns this
+// thread's share of the reduction (sum of squares, or dot with `other`).
+template <int NS, int BM, int BN, int TM, int TN, bool EPI>
+__device__ __forceinline__ float fused_tile_store(float* C, const float* prev, const float* other,
+                                                  bool reduce, int M, int N, int i0, int j0,
+                                                  const Fused& f, float ca, float cp,
+                                                  const float (&acc)[NS][TM][TN]) {
+  constexpr int TX = BN / TN;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
+  const size_t sC = (size_t)M * N;
+  float local = 0.f;
+#pragma unroll
+  for (int i = 0; i < TM; ++i) {
+    const int row = i0 + ty * TM + i;
+#pragma unroll
+    for (int j = 0; j < TN; ++j) {
+      const int col = j0 + tx * TN + j;
+      if (row < M && col < N) {
+#pragma unroll
+        for (int l = 0; l < NS; ++l) {
+          float y;
+          if (EPI) {
+            y = 0.f;
+#pragma unroll
+            for (int k = 0; k < NS; ++k) y = fmaf(f.epi[l * NS + k], acc[k][i][j], y);
+          } else {
+            y = acc[l][i][j];
+          }
+          const size_t o = (size_t)l * sC + (size_t)row * N + col;
+          float out = ca * y;
+          if (prev) out = fmaf(cp, prev[o], out);
+          C[o] = out;
+          if (reduce) local = fmaf(out, other ? other[o] : out, local);
+        }
+      }
+    }
+  }
+  return local;
+}
+
+// SPLIT: K is split over the cluster and the epilogue runs from the summed
+// partial tiles; otherwise (cluster of one) it runs from the registers.
+template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI, bool SPLIT>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_fused_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C, int M, int N,
+             int K, int kchunk, Fused f, Epi ep) {
+  constexpr int TX = BN / TN;
+  constexpr int NT = (BM / TM) * (BN / TN);
+  if (ep.skip && *ep.skip) return;
+  __shared__ __align__(16) float sm[Smem<NS, BM, BN, BK, SPLIT>::kFloats];
+  __shared__ float sh_coef[2];
+  float* P = sm;  // partial tile [NS][BM][BN] after the main loop
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int KS = (int)cluster.num_blocks();
+  const int rank = (int)cluster.block_rank();
+  const int tid = threadIdx.x;
+  const int tx = tid % TX, ty = tid / TX;
+  const int i0 = blockIdx.y * BM, j0 = blockIdx.x * BN;
+  const size_t sC = (size_t)M * N;
+  const int kbeg = rank * kchunk;
+  const int kend = min(K, kbeg + kchunk);
+
+  float acc[NS][TM][TN];
+  fused_tile_mainloop<NS, BM, BN, BK, TM, TN, PRO>(A, B, M, N, K, kbeg, kend, i0, j0, f, sm, acc);
 
   if (!SPLIT) {
     coef_compute(ep.coef, sh_coef);
     __syncthreads();
-    const float ca = sh_coef[0], cp = sh_coef[1];
-    float local = 0.f;
-#pragma unroll
-    for (int i = 0; i < TM; ++i) {
-      const int row = i0 + ty * TM + i;
-#pragma unroll
-      for (int j = 0; j < TN; ++j) {
-        const int col = j0 + tx * TN + j;
-        if (row < M && col < N) {
-#pragma unroll
-          for (int l = 0; l < NS; ++l) {
-            float y;
-            if (EPI) {
-              y = 0.f;
-#pragma unroll
-              for (int k = 0; k < NS; ++k) y = fmaf(f.epi[l * NS + k], acc[k][i][j], y);
-            } else {
-              y = acc[l][i][j];
-            }
-            const size_t o = (size_t)l * sC + (size_t)row * N + col;
-            float out = ca * y;
-            if (ep.prev) out = fmaf(cp, ep.prev[o], out);
-            C[o] = out;
-            if (ep.red.out) local = fmaf(out, ep.red.other ? ep.red.other[o] : out, local);
-          }
-        }
-      }
-    }
+    const float local = fused_tile_store<NS, BM, BN, TM, TN, EPI>(
+        C, ep.prev, ep.red.other, ep.red.out != nullptr, M, N, i0, j0, f, sh_coef[0], sh_coef[1],
+        acc);
     if (ep.red.out) reduce_finish(local, ep.red);
     return;
   }
@@ -304,6 +341,87 @@ k_slice_gemm(const float* __restrict__ A, const float* __restrict__ B, float* C,
   }
 }
 
+// Grouped fused products: CTA i takes tile work[i].y of problem work[i].x,
+// reads that problem's operands, epilogue scalars and done flag (g.op, g.j),
+// and reduces into that problem's partials with its tile index, so each
+// problem keeps its own deterministic reduction. The pointers follow the
+// deferred-iterate schedule of lsqr_enqueue: the forward product of step j
+// reads basis slot j and writes U (prev: C at j = 0, else U), the adjoint
+// reads U and writes basis slot j + 1 (prev: slot j), the first adjoint
+// writes slot 0 from C.
+template <int NS, int BM, int BN, int BK, int TM, int TN>
+__global__ void __launch_bounds__((BM / TM) * (BN / TN))
+k_group_gemm(const GroupProb* __restrict__ probs, const int2* __restrict__ work, GroupOp g,
+             Fused f) {
+  const int2 w = work[blockIdx.x];
+  const GroupProb& P = probs[w.x];
+  const size_t L = (size_t)g.lstride;
+  double* alpha = g.scal + (size_t)w.x * g.sstride;
+  double* beta = alpha + L;
+  int* flags = g.flags + 16 * w.x;
+  const int* done = g.done + (size_t)w.x * L;
+  if (g.op != GOP_INIT && done[g.j]) return;  // uniform over the problem's CTAs
+  __shared__ __align__(16) float sm[Smem<NS, BM, BN, BK, false>::kFloats];
+  __shared__ float sh_coef[2];
+  const bool fwd = g.op == GOP_FWD;
+  const int M = fwd ? P.n1 : P.n2, K = fwd ? P.n2 : P.n1, N = P.s;
+  const float* A = fwd ? P.Ah : P.AhT;
+  const float* B;
+  float* C;
+  const float* prev = nullptr;
+  Coef coef;
+  Red red;
+  red.sqrt_out = 1;
+  red.partials = P.partials;
+  red.ticket = P.ticket;
+  red.status = flags + 2;
+  if (g.op == GOP_INIT) {  // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
+    B = P.C;
+    C = P.basis;
+    coef.rule = COEF_INV;
+    coef.s0 = beta;
+    red.out = alpha;
+  } else if (fwd) {  // U~ = (1/alpha_j) A V~_j - (alpha_j/beta_j) U~, beta_{j+1}
+    B = P.basis + (size_t)g.j * P.Tx;
+    C = P.U;
+    prev = g.j == 0 ? P.C : P.U;
+    coef.rule = COEF_GK;
+    coef.s0 = alpha + g.j;
+    coef.s1 = beta + g.j;
+    red.out = beta + g.j + 1;
+  } else {  // V~_{j+1} = (1/beta_{j+1}) A^T U~ - (beta_{j+1}/alpha_j) V~_j, alpha_{j+1}
+    B = P.U;
+    C = g.j + 1 < g.itermax ? P.basis + (size_t)(g.j + 1) * P.Tx : P.V;
+    prev = P.basis + (size_t)g.j * P.Tx;
+    coef.rule = COEF_GK;
+    coef.s0 = beta + g.j + 1;
+    coef.s1 = alpha + g.j;
+    red.out = alpha + g.j + 1;
+  }
+  const int tn = (N + BN - 1) / BN;
+  const int i0 = (w.y / tn) * BM, j0 = (w.y % tn) * BN;
+  float acc[NS][TM][TN];
+  fused_tile_mainloop<NS, BM, BN, BK, TM, TN, true>(A, B, M, N, K, 0, K, i0, j0, f, sm, acc);
+  coef_compute(coef, sh_coef);
+  __syncthreads();
+  const float local = fused_tile_store<NS, BM, BN, TM, TN, true>(
+      C, prev, nullptr, true, M, N, i0, j0, f, sh_coef[0], sh_coef[1], acc);
+  reduce_finish_n(local, red, (unsigned)w.y, (unsigned)(fwd ? P.tiles_f : P.tiles_a));
+}
+
+// Tile shapes the autotuner chooses from: cfg 0: 64 x 64, 4 x 4 a thread
+// (256 threads); 1: 32 x 32, 4 x 2 (128); 2: 64 x 64, 8 x 4 (128, K blocks
+// of 8): fewer shared-memory loads an FMA.
+template <int NS, int CFG>
+int run_group(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
+              const Fused& f, cudaStream_t st) {
+  constexpr int T = CFG == 1 ? 32 : 64;
+  constexpr int BK = CFG == 2 ? 8 : 16, TM = CFG == 2 ? 8 : 4, TN = CFG == 0 ? 4 : (CFG == 1 ? 2 : 4);
+  k_group_gemm<NS, T, T, BK, TM, TN><<<nwork, (T / TM) * (T / TN), 0, st>>>(probs, work, g, f);
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 template <int NS, int BM, int BN, int BK, int TM, int TN, bool PRO, bool EPI, bool SPLIT>
 int run_fused(const float* A, const float* B, float* C, int M, int N, int K, const Fused& f,
               const Epi& ep, cudaStream_t st) {
@@ -348,6 +466,30 @@ int pick_flags(bool pro, bool epi, const float* A, const float* B, float* C, int
 }
 
 }  // namespace
+
+int gemm_group_tile(int cfg) { return cfg == 1 ? 32 : 64; }
+
+int launch_group_gemm(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
+                      const float* pro, const float* epi, int n3, int cfg, cudaStream_t st) {
+  TC_CHECK(n3 >= 1 && n3 <= TC_MAX_FUSED && nwork >= 1 && cfg >= 0 && cfg < GROUP_CFGS);
+  Fused f{};
+  for (int i = 0; i < n3 * n3; ++i) {
+    f.pro[i] = pro[i];
+    f.epi[i] = epi[i];
+  }
+  auto go = [&](auto ns) -> int {
+    constexpr int NS = decltype(ns)::value;
+    return cfg == 0 ? run_group<NS, 0>(probs, work, nwork, g, f, st)
+         : cfg == 1 ? run_group<NS, 1>(probs, work, nwork, g, f, st)
+                    : run_group<NS, 2>(probs, work, nwork, g, f, st);
+  };
+  switch (n3) {
+    case 1: return go(std::integral_constant<int, 1>{});
+    case 2: return go(std::integral_constant<int, 2>{});
+    case 3: return go(std::integral_constant<int, 3>{});
+    default: return go(std::integral_constant<int, 4>{});
+  }
+}
 
 int launch_slice_gemm(const float* A, const float* B, float* C, int M, int N, int K,
                       int nslices, const float* pro, const float* epi, const Epi& ep,

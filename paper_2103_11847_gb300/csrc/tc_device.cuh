@@ -97,13 +97,15 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // acquire-release atomic: it publishes this CTA's partial and, for the last
 // CTA, makes every other partial visible. Must be called by every thread of
 // every CTA of the launch.
-__device__ __forceinline__ void reduce_finish(float v, const Red& red) {
+// reduce_finish_n: the same with the CTA's index among the nblk CTAs that
+// share red's partials and ticket given explicitly (grouped launches, where
+// one launch holds the CTAs of many reductions).
+__device__ __forceinline__ void reduce_finish_n(float v, const Red& red, unsigned bid,
+                                                unsigned nblk) {
   __shared__ double sh_w[32];
   __shared__ int sh_last;
   const int nthr = blockDim.x * blockDim.y;
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
   v = warp_sum_f(v);
   if ((tid & 31) == 0) sh_w[tid >> 5] = v;
   __syncthreads();
@@ -133,6 +135,12 @@ __device__ __forceinline__ void reduce_finish(float v, const Red& red) {
       *red.ticket = 0u;
     }
   }
+}
+
+__device__ __forceinline__ void reduce_finish(float v, const Red& red) {
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+  reduce_finish_n(v, red, bid, nblk);
 }
 
 // LSQR step scalars (Algorithm 6 steps (c)-(g), 0-based step j):

@@ -252,6 +252,13 @@ int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alph
                       double* gcv_out, cudaStream_t st, const double* lam_pred = nullptr,
                       double factor = 0.0, int* fallback = nullptr);
 
+// The same for `count` problems in one launch each: problem i's doubles are
+// i ps and its ints (kdev) i fsi further on.
+int launch_gcv_bidiag_group(const double* rg, const double* phibar, const double* alpha,
+                            const double* beta, const int* kdev, int kmax, int variant,
+                            double lambda_in, double* work, double* lambda_out, double* y,
+                            double* gcv_out, int count, size_t ps, int fsi, cudaStream_t st);
+
 // gcv_bidiag.cu: the L-curve corner k_opt from LSQR's rotations (rg as in
 // launch_gcv_bidiag); writes *kopt, y_{k_opt} (kmax doubles, zero beyond
 // k_opt) and, when curve is non-null, ||R_k|| at [k-1] and ||X_k|| at
@@ -277,6 +284,48 @@ int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream
 int cprod_tdf(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st);
 int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st);
 int tc_kernels_init();
+
+// ------------------------------------------------------------ grouped solve --
+// group.cu: the batched c-LSQR of many FP32 fused-route problems (n3 <= 4,
+// one-sided, X_reg requested) as grouped launches: each phase of the solve is
+// one launch over all problems. Per problem:
+struct GroupProb {
+  const float* Ah = nullptr;   // A~ (n1 x n2 a slice) and its slice transposes
+  const float* AhT = nullptr;
+  const float* C = nullptr;
+  float* X = nullptr;
+  float* Xr = nullptr;
+  float* U = nullptr;          // U~ (n1 x s)
+  float* V = nullptr;          // the last adjoint's V~ (n2 x s)
+  float* basis = nullptr;      // V~_1 .. V~_itermax, Tx apart
+  double* partials = nullptr;  // this problem's reduction partials
+  unsigned* ticket = nullptr;  // and arrival ticket
+  size_t Tx = 0, Ty = 0;
+  int n1 = 0, n2 = 0, s = 0;
+  int tiles_f = 0, tiles_a = 0;  // CTAs of the forward (M = n1) / adjoint (M = n2) product
+  int pad = 0;
+};
+// The state of one grouped launch: which product, the step, and the
+// per-problem scalars (lsqr_enqueue's layout, sstride doubles a problem),
+// flags (16 ints a problem) and done flags (lstride ints a problem).
+enum GroupOpKind { GOP_INIT = 0, GOP_FWD = 1, GOP_ADJ = 2 };
+struct GroupOp {
+  int op = GOP_FWD;
+  int j = 0;
+  int itermax = 0;
+  int lstride = 0;     // itermax + 2
+  double* scal = nullptr;
+  size_t sstride = 0;
+  int* flags = nullptr;
+  int* done = nullptr;
+};
+// gemm.cu: the fused FP32 products of step g.j of every problem in one
+// launch; work[i] = (problem, tile) for CTA i; cfg 0 .. GROUP_CFGS - 1 are the
+// tile shapes (gemm_group_tile gives the tile edge).
+#define GROUP_CFGS 3
+int gemm_group_tile(int cfg);
+int launch_group_gemm(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
+                      const float* pro, const float* epi, int n3, int cfg, cudaStream_t st);
 
 // solvers.cu: the c-LSQR solve as a sequence of launches on one stream
 // (capturable), and the workspaces it needs.

@@ -67,6 +67,8 @@ _SIGS = {
                          ctypes.POINTER(c_int), ctypes.POINTER(c_int), c_int,
                          ctypes.POINTER(c_void_p), ctypes.POINTER(tc_opts), c_void_p], c_int),
     "tc_batch_destroy": ([c_void_p], c_int),
+    "tc_batch_info": ([c_void_p, c_int, ctypes.POINTER(c_int), ctypes.POINTER(c_int),
+                       ctypes.POINTER(ctypes.c_float)], c_int),
     "tc_mlp_create": ([ctypes.POINTER(c_void_p), ctypes.c_ulonglong, c_void_p], c_int),
     "tc_mlp_destroy": ([c_void_p], c_int),
     "tc_mlp_set_params": ([c_void_p, c_void_p, c_void_p, c_void_p], c_int),
@@ -302,6 +304,16 @@ def tc_batch_create(As, ss, precision=TC_FP32, gcv_variant=TC_GCV_PAPER, stream=
 
 def tc_batch_destroy(h):
     _check("tc_batch_destroy", lib().tc_batch_destroy(h))
+
+
+def tc_batch_info(h, mode=-1):
+    """Set the batch's form (mode 0: grouped where eligible, 1: child graphs;
+    -1 leaves it) and return (grouped, tile shape chosen, autotune times in ms)."""
+    g, t = c_int(0), c_int(0)
+    ms = (ctypes.c_float * 3)()
+    _check("tc_batch_info", lib().tc_batch_info(h, int(mode), ctypes.byref(g), ctypes.byref(t),
+                                                ms))
+    return bool(g.value), t.value, tuple(ms)
 
 
 def tc_lsqr_c_batched(h, Cs, Xs, Xregs, itermax, tol, lam, infos, stream=None):
