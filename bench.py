@@ -303,6 +303,20 @@ def precision_forms(dev, peaks, steps=3):
     return out
 
 
+GROUP_TILES = {0: ["64x64 FFMA tiles of 4x4", "32x32 FFMA tiles of 4x2", "64x64 FFMA tiles of 8x4"],
+               1: ["128x64 tcgen05 tiles", "128x128 tcgen05 tiles"]}
+
+
+def group_form_text(code, grouped, tile, tune):
+    if not grouped:
+        return "one CUDA graph of per-problem child graphs"
+    from paper_2103_11847_gb300 import tcprod
+    names = GROUP_TILES[1 if code == tcprod.TC_BF16 else 0]
+    timed = ", ".join("%s %.3f ms" % (nm, t) for nm, t in zip(names, tune))
+    return ("grouped launches (one a phase for all problems, transforms fused into the "
+            "products), %s picked by the autotuner (forward product: %s)" % (names[tile], timed))
+
+
 def batched_form(dev, iters=40, count=128, steps=2):
     """128 independent colour deblurring problems of uneven sizes n in
     {64, 96, ..., 512} (n x n x 3, sigma ~ U[1, 4], noise ~ U[1e-4, 1e-2]),
@@ -355,12 +369,7 @@ def batched_form(dev, iters=40, count=128, steps=2):
         out[name] = {"solves_per_s": count / (ms * 1e-3), "ms_per_batch": ms,
                      "iters_per_s": count * iters / (ms * 1e-3),
                      "mean_rel_err_reg": float(np.mean(errs)),
-                     "form": ("grouped launches (one a phase for all problems), tile shape "
-                              "%s picked by the autotuner (forward product %.2f / %.2f / "
-                              "%.2f ms for 64x64 of 4x4, 32x32 of 4x2, 64x64 of 8x4)"
-                              % (["64x64 of 4x4", "32x32 of 4x2", "64x64 of 8x4"][tile],
-                                 tune[0], tune[1], tune[2]))
-                     if grouped else "one CUDA graph of per-problem child graphs"}
+                     "form": group_form_text(code, grouped, tile, tune)}
         tcprod.tc_batch_destroy(h)
     base = out["fp32"]["mean_rel_err_reg"]
     out["bf16"]["matched_error"] = bool(abs(out["bf16"]["mean_rel_err_reg"] - base) <= 0.02 * base)

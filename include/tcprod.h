@@ -202,13 +202,18 @@ int tc_gmres_c(tc_plan* plan, const float* C, const float* X0, float* X,
  *   infos: device array of count tc_solve_info.
  * Two forms, both replayed as one CUDA graph cached while the pointers and
  * parameters stay the same:
- *  - grouped (FP32 plans with n3 <= 4 and X_reg given): every phase of the
- *    solve is one launch over all problems (a (problem, tile) work table, each
- *    problem's own scalars, flags and deterministic reductions), about
- *    3 itermax + 10 launches a batch. The tile shape of the fused products
- *    (three candidates) is chosen on the first call by timing each on the
- *    batch's forward product. Results equal tc_lsqr_c's up to the order of FP32
- *    additions (the single solve may split K over a cluster);
+ *  - grouped (FP32 plans, or BF16 plans of the default product, with
+ *    n3 <= 4 and X_reg given; BF16 plans also need n1, n2, s multiples of 8
+ *    and every C[i] 16-byte aligned):
+ *    every phase of the solve is one launch over all problems (a (problem,
+ *    tile) work table, each problem's own scalars, flags and deterministic
+ *    reductions), about 3 itermax + 10 launches a batch. The products fuse
+ *    both mode-3 transforms: FFMA tiles for FP32 plans, tcgen05 tiles (BF16
+ *    operands, FP32 accumulation) for BF16 plans. The tile shape is chosen
+ *    on the first call by timing each candidate on the batch's forward
+ *    product. Results equal tc_lsqr_c's up to the order of FP32 additions
+ *    (the single solve may split K over a cluster, or run the BF16 transform
+ *    as its own pass);
  *  - otherwise every problem's solve is captured as one child graph, side by
  *    side in one parent graph, results bit for bit tc_lsqr_c's. */
 typedef struct tc_batch tc_batch;
@@ -218,11 +223,15 @@ int tc_batch_destroy(tc_batch* batch);
 int tc_lsqr_c_batched(tc_batch* batch, const float* const* C, float* const* X,
                       float* const* X_reg, int itermax, double tol, double lambda,
                       tc_solve_info* infos, tc_stream_t stream);
-/* mode 0: the grouped form where the plans allow it (the default), 1: child
- * graphs always, -1: unchanged. Writes (host, each may be NULL) whether the
- * last solve ran grouped, the tile shape the autotuner chose (-1 before; 0:
- * 64 x 64 tiles of 4 x 4 a thread, 1: 32 x 32 of 4 x 2, 2: 64 x 64 of 8 x 4),
- * and the candidates' forward-product times in ms (tune_ms[3]). */
+/* mode 0: the grouped form where the plans allow it, tile shape autotuned (the
+ * default); 1: child graphs always; 2 + t: the grouped form with tile shape t
+ * (no autotuning; a t the plans do not have gives TC_EINVAL at the next
+ * solve); -1: unchanged. Writes (host, each may be NULL) whether the last
+ * solve ran grouped, the tile shape in use (-1 before the first grouped
+ * solve) and the candidates' forward-product times in ms (tune_ms[3], zero
+ * where not timed). Tile shapes: FP32 plans 0: 64 x 64 tiles of 4 x 4 a
+ * thread, 1: 32 x 32 of 4 x 2, 2: 64 x 64 of 8 x 4; BF16 plans 0: 128 x 64,
+ * 1: 128 x 128. */
 int tc_batch_info(tc_batch* batch, int mode, int* grouped, int* tile, float* tune_ms);
 
 /* ---- Learned lambda and stopping index --------------------------------------

@@ -1,7 +1,7 @@
 // Batched c-LSQR: many independent problems of uneven sizes solved together.
 //
 // Each problem has its own plan: A~ resident, its own workspaces. Two forms:
-// * grouped (group.cu): plans on the fused FP32 route with X_reg requested.
+// * grouped (group.cu): FP32 or BF16 plans with n3 <= 4 and X_reg requested.
 //   Every phase of the solve is one launch over all problems, the tile shape
 //   autotuned per batch, the whole sequence captured as one CUDA graph;
 // * otherwise each problem's whole solve (Algorithm 6, then the
@@ -24,7 +24,7 @@ struct tc_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<uintptr_t> key;
   GroupState grp;
-  int batch_mode = 0;  // 0: grouped where eligible, 1: child graphs always
+  int batch_mode = 0;  // 0: grouped where eligible, 1: child graphs always, 2 + t: tile shape t
 };
 
 extern "C" int tc_batch_destroy(tc_batch* b) {
@@ -85,7 +85,7 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
     key.push_back((uintptr_t)b->plans[i]->dscal);  // workspaces a capture depends on
     key.push_back((uintptr_t)b->plans[i]->basis);
   }
-  const bool grouped = b->batch_mode == 0 && group_eligible(b->plans, X_reg != nullptr);
+  const bool grouped = b->batch_mode != 1 && group_eligible(b->plans, C, X_reg != nullptr);
   if (grouped && (!b->exec || key != b->key)) {
     if (b->exec) {
       cudaGraphExecDestroy(b->exec);
@@ -93,7 +93,8 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
     }
     cudaStream_t st = (cudaStream_t)stream;
     TC_TRY(group_prepare(&b->grp, b->plans, C, X, X_reg, itermax, st));
-    TC_TRY(group_autotune(&b->grp, b->plans[0], st));
+    if (b->batch_mode == 0) TC_TRY(group_autotune(&b->grp, b->plans[0], st));
+    else TC_TRY(group_fix_tile(&b->grp, b->batch_mode - 2, st));
     cudaGraph_t g = nullptr;
     TC_CUDA(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal));
     const int rc = group_enqueue(&b->grp, b->plans[0], tol, lambda, infos, b->cap);
@@ -163,7 +164,7 @@ extern "C" int tc_lsqr_c_batched(tc_batch* b, const float* const* C, float* cons
 }
 
 extern "C" int tc_batch_info(tc_batch* b, int mode, int* grouped, int* tile, float* tune_ms) {
-  if (!b || mode < -1 || mode > 1) return TC_EINVAL;
+  if (!b || mode < -1 || mode > 1 + GROUP_CFGS) return TC_EINVAL;
   if (mode >= 0 && mode != b->batch_mode) {
     b->batch_mode = mode;
     if (b->exec) {
@@ -171,7 +172,7 @@ extern "C" int tc_batch_info(tc_batch* b, int mode, int* grouped, int* tile, flo
       b->exec = nullptr;
     }
   }
-  if (grouped) *grouped = b->batch_mode == 0 && b->grp.cfg >= 0;
+  if (grouped) *grouped = b->batch_mode != 1 && b->grp.cfg >= 0;
   if (tile) *tile = b->grp.cfg >= 0 ? b->grp.cfg : -1;
   if (tune_ms)
     for (int c = 0; c < GROUP_CFGS; ++c) tune_ms[c] = b->grp.tune_ms[c];

@@ -17,7 +17,7 @@
 
 #include <type_traits>
 
-#include "tc_device.cuh"
+#include "group.cuh"
 
 namespace cg = cooperative_groups;
 
@@ -355,58 +355,22 @@ k_group_gemm(const GroupProb* __restrict__ probs, const int2* __restrict__ work,
              Fused f) {
   const int2 w = work[blockIdx.x];
   const GroupProb& P = probs[w.x];
-  const size_t L = (size_t)g.lstride;
-  double* alpha = g.scal + (size_t)w.x * g.sstride;
-  double* beta = alpha + L;
-  int* flags = g.flags + 16 * w.x;
-  const int* done = g.done + (size_t)w.x * L;
-  if (g.op != GOP_INIT && done[g.j]) return;  // uniform over the problem's CTAs
+  if (g.op != GOP_INIT && g.done[(size_t)w.x * g.lstride + g.j]) return;  // uniform over the problem's CTAs
   __shared__ __align__(16) float sm[Smem<NS, BM, BN, BK, false>::kFloats];
   __shared__ float sh_coef[2];
-  const bool fwd = g.op == GOP_FWD;
-  const int M = fwd ? P.n1 : P.n2, K = fwd ? P.n2 : P.n1, N = P.s;
+  const GroupOperands o = group_operands(P, g, w.x);
+  const bool fwd = o.fwd;
+  const int M = o.M, K = o.K, N = o.N;
   const float* A = fwd ? P.Ah : P.AhT;
-  const float* B;
-  float* C;
-  const float* prev = nullptr;
-  Coef coef;
-  Red red;
-  red.sqrt_out = 1;
-  red.partials = P.partials;
-  red.ticket = P.ticket;
-  red.status = flags + 2;
-  if (g.op == GOP_INIT) {  // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
-    B = P.C;
-    C = P.basis;
-    coef.rule = COEF_INV;
-    coef.s0 = beta;
-    red.out = alpha;
-  } else if (fwd) {  // U~ = (1/alpha_j) A V~_j - (alpha_j/beta_j) U~, beta_{j+1}
-    B = P.basis + (size_t)g.j * P.Tx;
-    C = P.U;
-    prev = g.j == 0 ? P.C : P.U;
-    coef.rule = COEF_GK;
-    coef.s0 = alpha + g.j;
-    coef.s1 = beta + g.j;
-    red.out = beta + g.j + 1;
-  } else {  // V~_{j+1} = (1/beta_{j+1}) A^T U~ - (beta_{j+1}/alpha_j) V~_j, alpha_{j+1}
-    B = P.U;
-    C = g.j + 1 < g.itermax ? P.basis + (size_t)(g.j + 1) * P.Tx : P.V;
-    prev = P.basis + (size_t)g.j * P.Tx;
-    coef.rule = COEF_GK;
-    coef.s0 = beta + g.j + 1;
-    coef.s1 = alpha + g.j;
-    red.out = alpha + g.j + 1;
-  }
   const int tn = (N + BN - 1) / BN;
   const int i0 = (w.y / tn) * BM, j0 = (w.y % tn) * BN;
   float acc[NS][TM][TN];
-  fused_tile_mainloop<NS, BM, BN, BK, TM, TN, true>(A, B, M, N, K, 0, K, i0, j0, f, sm, acc);
-  coef_compute(coef, sh_coef);
+  fused_tile_mainloop<NS, BM, BN, BK, TM, TN, true>(A, o.B, M, N, K, 0, K, i0, j0, f, sm, acc);
+  coef_compute(o.coef, sh_coef);
   __syncthreads();
   const float local = fused_tile_store<NS, BM, BN, TM, TN, true>(
-      C, prev, nullptr, true, M, N, i0, j0, f, sh_coef[0], sh_coef[1], acc);
-  reduce_finish_n(local, red, (unsigned)w.y, (unsigned)(fwd ? P.tiles_f : P.tiles_a));
+      o.C, o.prev, nullptr, true, M, N, i0, j0, f, sh_coef[0], sh_coef[1], acc);
+  reduce_finish_n(local, o.red, (unsigned)w.y, (unsigned)(fwd ? P.tiles_f : P.tiles_a));
 }
 
 // Tile shapes the autotuner chooses from: cfg 0: 64 x 64, 4 x 4 a thread
@@ -467,7 +431,16 @@ int pick_flags(bool pro, bool epi, const float* A, const float* B, float* C, int
 
 }  // namespace
 
-int gemm_group_tile(int cfg) { return cfg == 1 ? 32 : 64; }
+int group_cfg_count(int bf16) { return bf16 ? 2 : 3; }
+
+void group_tile_shape(int bf16, int cfg, int* tm, int* tn) {
+  if (bf16) {  // group_tc.cu: 128 x 64 or 128 x 128
+    *tm = 128;
+    *tn = cfg == 1 ? 128 : 64;
+  } else {
+    *tm = *tn = cfg == 1 ? 32 : 64;
+  }
+}
 
 int launch_group_gemm(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
                       const float* pro, const float* epi, int n3, int cfg, cudaStream_t st) {

@@ -10,8 +10,9 @@
 // chosen per batch by timing each on the batch's own forward product (autotune),
 // and the whole grouped solve is captured once as a CUDA graph.
 //
-// It serves batches whose plans take the fused FP32 route (n3 <= 4, FP32)
-// and that request X_reg: the iterate is then formed from the kept basis at
+// It serves batches of FP32 or BF16 plans with n3 <= 4 (the products fuse
+// the mode-3 transforms: gemm.cu's FFMA tiles, group_tc.cu's tcgen05 tiles)
+// that request X_reg: the iterate is then formed from the kept basis at
 // the end (the deferred schedule of lsqr_enqueue), and every kernel here
 // follows that schedule problem by problem.
 #include <vector>
@@ -36,9 +37,10 @@ struct Layout {  // offsets of one problem's scalars (lsqr_enqueue's layout)
   __host__ __device__ size_t stride() const { return 7 * L + 1200 + kp + 16; }
 };
 
-__global__ void k_group_reset(int* flags, int* done, int L, int count) {
+__global__ void k_group_reset(int* flags, int* done, unsigned* tickets, int L, int count) {
   const int p = blockIdx.x;
   if (p >= count) return;
+  if (threadIdx.x == 0) tickets[p] = 0u;  // left set only by a product that gave up
   for (int i = threadIdx.x; i < 16; i += blockDim.x) flags[16 * p + i] = 0;
   for (int i = threadIdx.x; i < L; i += blockDim.x) done[(size_t)p * L + i] = 0;
 }
@@ -204,13 +206,27 @@ int dgrow(T** p, size_t* have, size_t need) {
 
 }  // namespace
 
-bool group_eligible(const std::vector<tc_plan*>& plans, bool keep) {
+bool group_eligible(const std::vector<tc_plan*>& plans, const float* const* C, bool keep) {
   if (!keep || plans.empty()) return false;
-  for (const tc_plan* p : plans)
-    if (p->opts.precision != TC_FP32 || p->n3 > TC_MAX_FUSED || p->two_sided ||
+  const int prec = plans[0]->opts.precision;
+  if (prec != TC_FP32 && prec != TC_BF16) return false;
+  // BF16 ORTHODCT plans iterate in the transform domain (BF16 operands written
+  // by the previous product's epilogue, no transform passes); as child graphs
+  // that form is the faster one (6.5k against 5.3k solves/s on 128 problems
+  // of n in 64..512, x3)
+  if (prec == TC_BF16 && plans[0]->opts.product == TC_ORTHODCT) return false;
+  for (const tc_plan* p : plans) {
+    if (p->opts.precision != prec || p->n3 > TC_MAX_FUSED || p->two_sided ||
         p->n3 != plans[0]->n3 || p->opts.product != plans[0]->opts.product ||
         p->opts.gcv_variant != plans[0]->opts.gcv_variant)
       return false;
+    if (prec == TC_BF16 &&
+        (!p->AhL || !p->AhTL || p->n1 % 8 != 0 || p->n2 % 8 != 0 || p->s % 8 != 0))
+      return false;
+  }
+  if (prec == TC_BF16)  // C is read as float4
+    for (size_t i = 0; i < plans.size(); ++i)
+      if (reinterpret_cast<uintptr_t>(C[i]) & 15) return false;
   return true;
 }
 
@@ -230,6 +246,7 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
                   float* const* X, float* const* Xr, int itermax, cudaStream_t st) {
   const int count = (int)plans.size();
   const Layout lay{(size_t)itermax + 2, (size_t)(itermax < TC_MAX_PROJ ? itermax : TC_MAX_PROJ)};
+  const int bf16 = plans[0]->opts.precision == TC_BF16, ncfg = group_cfg_count(bf16);
   std::vector<GroupProb> hp(count);
   std::vector<int2> wk[GROUP_CFGS][2];
   size_t npart = 0;
@@ -238,6 +255,8 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
     GroupProb& q = hp[i];
     q.Ah = p->Ah;
     q.AhT = p->AhT;
+    q.AhL = p->AhL;
+    q.AhTL = p->AhTL;
     q.C = C[i];
     q.X = X[i];
     q.Xr = Xr[i];
@@ -250,10 +269,11 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
     q.n2 = p->n2;
     q.s = p->s;
     size_t most = NORM_CTAS;
-    for (int c = 0; c < GROUP_CFGS; ++c) {
-      const int T = gemm_group_tile(c);
-      const int tn = (q.s + T - 1) / T;
-      const int tf = ((q.n1 + T - 1) / T) * tn, ta = ((q.n2 + T - 1) / T) * tn;
+    for (int c = 0; c < ncfg; ++c) {
+      int TM, TN;
+      group_tile_shape(bf16, c, &TM, &TN);
+      const int tn = (q.s + TN - 1) / TN;
+      const int tf = ((q.n1 + TM - 1) / TM) * tn, ta = ((q.n2 + TM - 1) / TM) * tn;
       for (int t = 0; t < tf; ++t) wk[c][0].push_back(make_int2(i, t));
       for (int t = 0; t < ta; ++t) wk[c][1].push_back(make_int2(i, t));
       if ((size_t)tf > most) most = tf;
@@ -271,7 +291,7 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
     TC_TRY(dgrow(&g->tickets, &g->tickets_n, (size_t)count));
     TC_CUDA(cudaMemsetAsync(g->tickets, 0, (size_t)count * sizeof(unsigned), st));
   }
-  for (int c = 0; c < GROUP_CFGS; ++c)
+  for (int c = 0; c < ncfg; ++c)
     for (int d = 0; d < 2; ++d) {
       TC_TRY(dgrow(&g->work[c][d], &g->work_n[c][d], wk[c][d].size()));
       TC_CUDA(cudaMemcpyAsync(g->work[c][d], wk[c][d].data(), wk[c][d].size() * sizeof(int2),
@@ -283,6 +303,8 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
     hp[i].ticket = g->tickets + i;
   }
   g->host = hp;
+  g->bf16 = bf16;
+  g->ncfg = ncfg;
   g->count = count;
   g->itermax = itermax;
   g->stride = lay.stride();
@@ -296,12 +318,13 @@ int group_prepare(GroupState* g, const std::vector<tc_plan*>& plans, const float
 
 namespace {
 int set_tiles(GroupState* g, int cfg) {
+  int TM, TN;
+  group_tile_shape(g->bf16, cfg, &TM, &TN);
   for (int i = 0; i < g->count; ++i) {
-    const int T = gemm_group_tile(cfg);
     GroupProb& q = g->host[i];
-    const int tn = (q.s + T - 1) / T;
-    q.tiles_f = ((q.n1 + T - 1) / T) * tn;
-    q.tiles_a = ((q.n2 + T - 1) / T) * tn;
+    const int tn = (q.s + TN - 1) / TN;
+    q.tiles_f = ((q.n1 + TM - 1) / TM) * tn;
+    q.tiles_a = ((q.n2 + TM - 1) / TM) * tn;
   }
   return TC_OK;
 }
@@ -318,30 +341,41 @@ GroupOp make_op(const GroupState* g, int kind, int j) {
   o.done = g->done;
   return o;
 }
+
+// Product `kind` of step j of every problem with tile shape cfg: the forward
+// product transforms with (M, M^-1), the adjoint and the first product with
+// (M^-T, M^T).
+int launch_op(const GroupState* g, const tc_plan* p0, int kind, int j, int cfg, cudaStream_t st) {
+  const int d = kind == GOP_FWD ? 0 : 1;
+  const float* pro = d == 0 ? p0->hM : p0->hMinvT;
+  const float* epi = d == 0 ? p0->hMinv : p0->hMT;
+  const GroupOp o = make_op(g, kind, j);
+  return g->bf16 ? launch_group_umma(g->probs, g->work[cfg][d], g->nwork[cfg][d], o, pro, epi,
+                                     p0->n3, cfg, st)
+                 : launch_group_gemm(g->probs, g->work[cfg][d], g->nwork[cfg][d], o, pro, epi,
+                                     p0->n3, cfg, st);
+}
 }  // namespace
 
 // Time the forward product of the batch with each tile shape (a warm-up and
 // three launches each, CUDA events on `st`, outside any capture) and keep the
 // fastest.
 int group_autotune(GroupState* g, const tc_plan* p0, cudaStream_t st) {
-  k_group_reset<<<g->count, 128, 0, st>>>(g->flags, g->done, (int)g->L, g->count);
+  k_group_reset<<<g->count, 128, 0, st>>>(g->flags, g->done, g->tickets, (int)g->L, g->count);
   TC_CUDA(cudaGetLastError());
   float best = 1e30f;
   int pick = 0;
   cudaEvent_t e0, e1;
   TC_CUDA(cudaEventCreate(&e0));
   TC_CUDA(cudaEventCreate(&e1));
-  for (int c = 0; c < GROUP_CFGS; ++c) {
+  for (int c = 0; c < GROUP_CFGS; ++c) g->tune_ms[c] = 0.f;
+  for (int c = 0; c < g->ncfg; ++c) {
     set_tiles(g, c);
     TC_CUDA(cudaMemcpyAsync(g->probs, g->host.data(), g->host.size() * sizeof(GroupProb),
                             cudaMemcpyHostToDevice, st));
-    const GroupOp o = make_op(g, GOP_FWD, 0);
-    TC_TRY(launch_group_gemm(g->probs, g->work[c][0], g->nwork[c][0], o, p0->hM, p0->hMinv,
-                             p0->n3, c, st));  // warm-up
+    TC_TRY(launch_op(g, p0, GOP_FWD, 0, c, st));  // warm-up
     TC_CUDA(cudaEventRecord(e0, st));
-    for (int r = 0; r < 3; ++r)
-      TC_TRY(launch_group_gemm(g->probs, g->work[c][0], g->nwork[c][0], o, p0->hM, p0->hMinv,
-                               p0->n3, c, st));
+    for (int r = 0; r < 3; ++r) TC_TRY(launch_op(g, p0, GOP_FWD, 0, c, st));
     TC_CUDA(cudaEventRecord(e1, st));
     TC_CUDA(cudaEventSynchronize(e1));
     float ms = 0.f;
@@ -362,6 +396,18 @@ int group_autotune(GroupState* g, const tc_plan* p0, cudaStream_t st) {
   return TC_OK;
 }
 
+// Tile shape cfg without timing (tc_batch_info's forced modes).
+int group_fix_tile(GroupState* g, int cfg, cudaStream_t st) {
+  TC_CHECK(cfg >= 0 && cfg < g->ncfg);
+  for (int c = 0; c < GROUP_CFGS; ++c) g->tune_ms[c] = 0.f;
+  g->cfg = cfg;
+  set_tiles(g, cfg);
+  TC_CUDA(cudaMemcpyAsync(g->probs, g->host.data(), g->host.size() * sizeof(GroupProb),
+                          cudaMemcpyHostToDevice, st));
+  TC_CUDA(cudaStreamSynchronize(st));
+  return TC_OK;
+}
+
 // The grouped solve on `st` (capturable): the same steps as lsqr_enqueue with
 // a kept basis, every launch over all problems.
 int group_enqueue(GroupState* g, const tc_plan* p0, double tol, double lambda,
@@ -369,12 +415,11 @@ int group_enqueue(GroupState* g, const tc_plan* p0, double tol, double lambda,
   const int count = g->count, itermax = g->itermax, c = g->cfg;
   const Layout lay{g->L, g->kp};
   const int tb = (count + 127) / 128;
-  k_group_reset<<<count, 128, 0, st>>>(g->flags, g->done, (int)g->L, count);
+  k_group_reset<<<count, 128, 0, st>>>(g->flags, g->done, g->tickets, (int)g->L, count);
   TC_CUDA(cudaGetLastError());
   k_group_norm_c<<<dim3(NORM_CTAS, count), GRP_NT, 0, st>>>(g->probs, g->scal, lay, g->flags);
   TC_CUDA(cudaGetLastError());
-  TC_TRY(launch_group_gemm(g->probs, g->work[c][1], g->nwork[c][1], make_op(g, GOP_INIT, 0),
-                           p0->hMinvT, p0->hMT, p0->n3, c, st));
+  TC_TRY(launch_op(g, p0, GOP_INIT, 0, c, st));
   k_group_lsqr_init<<<tb, 128, 0, st>>>(g->scal, lay, g->flags, g->done, count);
   TC_CUDA(cudaGetLastError());
   for (int j = 0; j < itermax; ++j) {
@@ -382,10 +427,8 @@ int group_enqueue(GroupState* g, const tc_plan* p0, double tol, double lambda,
       k_group_scalars<<<tb, 128, 0, st>>>(g->scal, lay, g->flags, g->done, j - 1, tol, count);
       TC_CUDA(cudaGetLastError());
     }
-    TC_TRY(launch_group_gemm(g->probs, g->work[c][0], g->nwork[c][0], make_op(g, GOP_FWD, j),
-                             p0->hM, p0->hMinv, p0->n3, c, st));
-    TC_TRY(launch_group_gemm(g->probs, g->work[c][1], g->nwork[c][1], make_op(g, GOP_ADJ, j),
-                             p0->hMinvT, p0->hMT, p0->n3, c, st));
+    TC_TRY(launch_op(g, p0, GOP_FWD, j, c, st));
+    TC_TRY(launch_op(g, p0, GOP_ADJ, j, c, st));
   }
   k_group_scalars<<<tb, 128, 0, st>>>(g->scal, lay, g->flags, g->done, itermax - 1, tol, count);
   TC_CUDA(cudaGetLastError());

@@ -289,5 +289,6 @@ int tc_kernels_init() {
   TC_TRY(cprod2_init());
   TC_TRY(vec_init());
   TC_TRY(transform_init());
+  TC_TRY(group_tc_init());
   return TC_OK;
 }

@@ -286,12 +286,14 @@ int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st);
 int tc_kernels_init();
 
 // ------------------------------------------------------------ grouped solve --
-// group.cu: the batched c-LSQR of many FP32 fused-route problems (n3 <= 4,
-// one-sided, X_reg requested) as grouped launches: each phase of the solve is
+// group.cu: the batched c-LSQR of many FP32 or BF16 problems with n3 <= 4
+// (one-sided, X_reg requested) as grouped launches: each phase of the solve is
 // one launch over all problems. Per problem:
 struct GroupProb {
   const float* Ah = nullptr;   // A~ (n1 x n2 a slice) and its slice transposes
   const float* AhT = nullptr;
+  const void* AhL = nullptr;   // BF16 plans: the same rounded to BF16
+  const void* AhTL = nullptr;
   const float* C = nullptr;
   float* X = nullptr;
   float* Xr = nullptr;
@@ -319,13 +321,20 @@ struct GroupOp {
   int* flags = nullptr;
   int* done = nullptr;
 };
-// gemm.cu: the fused FP32 products of step g.j of every problem in one
-// launch; work[i] = (problem, tile) for CTA i; cfg 0 .. GROUP_CFGS - 1 are the
-// tile shapes (gemm_group_tile gives the tile edge).
+// The fused products of step g.j of every problem in one launch; work[i] =
+// (problem, tile) for CTA i. Tile shape cfg (0 .. group_cfg_count - 1) is
+// group_tile_shape's tm x tn output tile:
+// * gemm.cu, FP32 plans: FFMA, three shapes;
+// * group_tc.cu, BF16 plans: tcgen05 with the transforms in the operand load
+//   and the epilogue, two shapes.
 #define GROUP_CFGS 3
-int gemm_group_tile(int cfg);
+int group_cfg_count(int bf16);
+void group_tile_shape(int bf16, int cfg, int* tm, int* tn);
 int launch_group_gemm(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
                       const float* pro, const float* epi, int n3, int cfg, cudaStream_t st);
+int launch_group_umma(const GroupProb* probs, const int2* work, int nwork, const GroupOp& g,
+                      const float* pro, const float* epi, int n3, int cfg, cudaStream_t st);
+int group_tc_init();
 
 // solvers.cu: the c-LSQR solve as a sequence of launches on one stream
 // (capturable), and the workspaces it needs.

@@ -307,13 +307,19 @@ def tc_batch_destroy(h):
 
 
 def tc_batch_info(h, mode=-1):
-    """Set the batch's form (mode 0: grouped where eligible, 1: child graphs;
-    -1 leaves it) and return (grouped, tile shape chosen, autotune times in ms)."""
+    """Set the batch's form (mode 0: grouped where eligible, tile autotuned;
+    1: child graphs; 2 + t: grouped with tile shape t; -1 leaves it) and
+    return (grouped, tile shape in use, autotune times in ms)."""
     g, t = c_int(0), c_int(0)
     ms = (ctypes.c_float * 3)()
     _check("tc_batch_info", lib().tc_batch_info(h, int(mode), ctypes.byref(g), ctypes.byref(t),
                                                 ms))
     return bool(g.value), t.value, tuple(ms)
+
+
+def tc_batch_force_tile(h, tile):
+    """The grouped form with tile shape `tile`, no autotuning."""
+    return tc_batch_info(h, mode=2 + int(tile))
 
 
 def tc_lsqr_c_batched(h, Cs, Xs, Xregs, itermax, tol, lam, infos, stream=None):
