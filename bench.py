@@ -317,6 +317,33 @@ def group_form_text(code, grouped, tile, tune):
             "products), %s picked by the autotuner (forward product: %s)" % (names[tile], timed))
 
 
+def group_product_roofline(code, sizes, ms):
+    """One grouped forward product of the batch (the autotuner's CUDA-event
+    time of the chosen tile shape) against its roofline. Algorithmic bytes a
+    problem: A~ (BF16 6 n^2, FP32 12 n^2) + the operand, prev and output
+    (12 n^2 each); flops 2 n^3 a slice."""
+    from paper_2103_11847_gb300 import tcprod
+    peaks, src = load_peaks()
+    sq = sum(n * n for n in sizes)
+    cube = sum(n ** 3 for n in sizes)
+    bf16 = code == tcprod.TC_BF16
+    nbytes = (42 if bf16 else 48) * sq
+    flops = 2.0 * 3 * cube
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    row = {"ms": ms, "algorithmic_bytes": nbytes, "flops": flops, "gb_s": gbs,
+           "hbm_frac": gbs / hbm, "hbm_peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+           "tflops": flops / (ms * 1e-3) / 1e12}
+    if bf16:
+        row["traffic"] = captured_traffic("k_group_umma_bf16")
+    else:
+        fp = measured_peak("fp32_ffma_tflops")
+        if fp:
+            row["ffma_frac"] = row["tflops"] / fp
+            row["ffma_peak_source"] = "profiles/peaks.json fp32_ffma_tflops (measured)"
+    return row
+
+
 def batched_form(dev, iters=40, count=128, steps=2):
     """128 independent colour deblurring problems of uneven sizes n in
     {64, 96, ..., 512} (n x n x 3, sigma ~ U[1, 4], noise ~ U[1e-4, 1e-2]),
@@ -370,6 +397,8 @@ def batched_form(dev, iters=40, count=128, steps=2):
                      "iters_per_s": count * iters / (ms * 1e-3),
                      "mean_rel_err_reg": float(np.mean(errs)),
                      "form": group_form_text(code, grouped, tile, tune)}
+        if grouped:
+            out[name]["product_kernel"] = group_product_roofline(code, sizes, tune[tile])
         tcprod.tc_batch_destroy(h)
     base = out["fp32"]["mean_rel_err_reg"]
     out["bf16"]["matched_error"] = bool(abs(out["bf16"]["mean_rel_err_reg"] - base) <= 0.02 * base)
@@ -947,6 +976,9 @@ def main():
     ap.add_argument("--kernel-only", action="store_true",
                     help="launch only the workload's dominant kernel (8 launches) and then 4 "
                          "whole c-products, for profiling captures")
+    ap.add_argument("--batched", action="store_true",
+                    help="run only the batched form (128 problems, every precision form) and "
+                         "print its JSON, for profiling captures")
     ap.add_argument("--ref-budget", type=float, default=120.0,
                     help="seconds after which the reference arm stops taking steps")
     ap.add_argument("--cpu-worker", default=None)
@@ -965,6 +997,9 @@ def main():
         return
     if args.kernel_only:
         kernel_only(args)
+        return
+    if args.batched:
+        print(json.dumps(batched_form("cuda")))
         return
     if args.impl == "reference":
         run_reference(args)
