@@ -236,7 +236,12 @@ int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream
 }
 
 // X = M^T [ A~_k^T (M^{-T} Y)_k (B~_k^T) ] with the epilogue `ep` on the last stage.
-int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st) {
+int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st,
+                const LsqrStep* after) {
+  if (after && !(lowp(p) && p->n3 > TC_TUBE_MIN_N3)) {  // the step's own launch after the product
+    TC_TRY(adjoint_epi(p, Y, X, ep, st, nullptr));
+    return launch_lsqr_scalars(*after, st);
+  }
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
   Epi mid;
   mid.skip = ep.skip;
@@ -265,7 +270,7 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
     if (p->two_sided) TC_TRY(right_factor(p, *p->uma2, (size_t)n2 * s * n3, err, ep.skip, st));
-    return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, x3(p))
+    return tct ? launch_mode3_tc(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, x3(p), after)
                : launch_mode3(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, st);
   }
   TC_TRY(launch_mode3(Y, p->tmp1, p->dMinvT, n3, (size_t)n1 * s, mid, st));

@@ -202,10 +202,15 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     if (step) TC_TRY(step->X ? launch_lsqr_update(*step, st) : launch_lsqr_scalars(*step, st));
     return tdf ? cprod_tdf(p, Yv, ep, st) : cprod_td(p, Xv, Yv, ep, st);
   };
-  auto adj = [&](const float* Yv, float* Xv, const Epi& ep) -> int {
+  auto adj = [&](const float* Yv, float* Xv, const Epi& ep, const LsqrStep* after) -> int {
     if (tdf) return adjoint_tdf(p, Xv, ep, st);
-    return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st);
+    return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st, after);
   };
+  // Deferred schedule on the tensor-core transform route: step j's scalars
+  // need alpha_{j+1}, which the adjoint product of step j finishes in its
+  // trailing transform pass; the CTA that finishes that norm runs them, and
+  // the forward product of step j + 1 starts without a launch before it.
+  const bool fold = defer && !td && tct;
   // beta_1 = ||C||_F
   TC_TRY(launch_reduce(Cin, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
   // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
@@ -214,7 +219,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     ep.coef.rule = COEF_INV;
     ep.coef.s0 = beta;
     ep.red = make_red(p, alpha, 1, nullptr, flags + 2);
-    TC_TRY(adj(Cin, defer ? slot(0) : V, ep));
+    TC_TRY(adj(Cin, defer ? slot(0) : V, ep, nullptr));
   }
   if (!defer) {  // W_1 = V_1 = V~_1 / alpha_1; X_0 = 0
     Coef c;
@@ -265,7 +270,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.red = make_red(p, beta + j + 1, 1, nullptr, flags + 2);
       ep.skip = done + j;
       const LsqrStep prev = j > 0 ? make_step(j - 1) : LsqrStep{};
-      TC_TRY(fwd(defer ? slot(j) : V, U, ep, j > 0 ? &prev : nullptr));
+      TC_TRY(fwd(defer ? slot(j) : V, U, ep, (j > 0 && !fold) ? &prev : nullptr));
     }
     // the learned predictor reads the first MLP_FEAT_STEPS steps
     if (a.mlp && j == MLP_FEAT_STEPS)
@@ -281,10 +286,13 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
       ep.skip = done + j;
       // deferred: V~_{j+1} into basis slot j + 1 (the last one, never part of
       // the basis, into the workspace)
-      TC_TRY(adj(U, defer ? (j + 1 < a.itermax ? slot(j + 1) : V) : V, ep));
+      const LsqrStep step = make_step(j);
+      TC_TRY(adj(U, defer ? (j + 1 < a.itermax ? slot(j + 1) : V) : V, ep, fold ? &step : nullptr));
     }
   }
-  if (defer)
+  if (fold) {
+    // every step's scalars ran in its adjoint product
+  } else if (defer)
     TC_TRY(launch_lsqr_scalars(make_step(a.itermax - 1), st));
   else
     TC_TRY(launch_lsqr_update(make_step(a.itermax - 1), st));

@@ -99,8 +99,10 @@ __device__ __forceinline__ float warp_sum_f(float v) {
 // every CTA of the launch.
 // reduce_finish_n: the same with the CTA's index among the nblk CTAs that
 // share red's partials and ticket given explicitly (grouped launches, where
-// one launch holds the CTAs of many reductions).
-__device__ __forceinline__ void reduce_finish_n(float v, const Red& red, unsigned bid,
+// one launch holds the CTAs of many reductions). Both return, to every
+// thread, whether this CTA was the last to arrive (the one that wrote the
+// result).
+__device__ __forceinline__ bool reduce_finish_n(float v, const Red& red, unsigned bid,
                                                 unsigned nblk) {
   __shared__ double sh_w[32];
   __shared__ int sh_last;
@@ -120,7 +122,7 @@ __device__ __forceinline__ void reduce_finish_n(float v, const Red& red, unsigne
     }
   }
   __syncthreads();
-  if (!sh_last) return;
+  if (!sh_last) return false;
   double acc = 0.0;
   for (unsigned i = tid; i < nblk; i += nthr) acc += __ldcg(red.partials + i);
   acc = warp_sum(acc);
@@ -135,12 +137,13 @@ __device__ __forceinline__ void reduce_finish_n(float v, const Red& red, unsigne
       *red.ticket = 0u;
     }
   }
+  return true;
 }
 
-__device__ __forceinline__ void reduce_finish(float v, const Red& red) {
+__device__ __forceinline__ bool reduce_finish(float v, const Red& red) {
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
   const unsigned bid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-  reduce_finish_n(v, red, bid, nblk);
+  return reduce_finish_n(v, red, bid, nblk);
 }
 
 // LSQR step scalars (Algorithm 6 steps (c)-(g), 0-based step j):

@@ -203,8 +203,13 @@ enum RoundKind { ROUND_TF32 = 0, ROUND_BF16 = 1, ROUND_BF16X3 = 2 };
 // and BF16 forms; three (split3 / ROUND_BF16X3), near 2^-27, for the
 // FP32-level form). *err is set to TC_ETIMEOUT if the bounded wait for the
 // MMAs gives up.
+// With `after` (a scalars-only LSQR step, X null, and a norm in ep.red), the
+// step's scalars run once the pass's norm is in place: inside the TMA form,
+// by the CTA that finishes the norm (a skipped pass sets after->done_out),
+// else as their own launch after the pass.
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
-                    const Epi& ep, int* err, cudaStream_t st, int split3 = 0);
+                    const Epi& ep, int* err, cudaStream_t st, int split3 = 0,
+                    const LsqrStep* after = nullptr);
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                          int kind, const int* skip, int* err, cudaStream_t st);
 // Elementwise rounding of n FP32 values to the operand type `kind` (RoundKind).
@@ -272,7 +277,10 @@ int launch_lcurve(const double* rg, const double* phibar, const int* kdev, int k
 // then be step->done_out.
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
               const LsqrStep* step = nullptr);
-int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st);
+// With `after`, a scalars-only LSQR step runs once the product's norm is in
+// place (folded into the tensor-core transform pass where there is one).
+int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st,
+                const LsqrStep* after = nullptr);
 Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
 // Transform-domain products (ORTHODCT plans off the fused route; td_route):
 // operand and result are transformed tensors, the epilogue applies to them.

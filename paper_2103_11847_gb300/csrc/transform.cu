@@ -563,7 +563,7 @@ template <int OUT, int NS>
 __global__ void __launch_bounds__(TT_NT, 1)
 k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
            const __grid_constant__ CUtensorMap tmOut, const float* __restrict__ T, int n3,
-           size_t P, int has_prev, Epi ep, int* err) {
+           size_t P, int has_prev, Epi ep, int* err, LsqrStep after) {
   constexpr int NPASS = NS == 2 ? 3 : 6;
   constexpr int NI = tube_tma_in(NS, OUT), NO = tube_tma_out(NS, OUT);
   constexpr uint32_t OSLOT = tube_tma_oslot(OUT);
@@ -571,7 +571,13 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   using namespace tc5;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
                              ((uint32_t)(TK >> 3) << 17) | ((uint32_t)(TP >> 4) << 24);
-  if (ep.skip && *ep.skip) return;
+  // `after` (alpha non-null): the scalars of an LSQR step that need this
+  // pass's norm, run by the CTA that finishes the norm (see the end); a
+  // skipped pass still hands the done flag on
+  if (ep.skip && *ep.skip) {
+    if (after.alpha && blockIdx.x == 0 && threadIdx.x == 0) *after.done_out = 1;
+    return;
+  }
   extern __shared__ uint8_t tt_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(tt_raw) + 1023) & ~(uintptr_t)1023);
@@ -856,7 +862,17 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
     for (int g = (issued_p > NO ? issued_p - NO : 0); g < issued_p; ++g)
       mbar_wait(ofull + g % NO, (uint32_t)(g / NO) & 1u);
   }
-  if (OUT == OUT_F32 && ep.red.out) reduce_finish(local, ep.red);  // every thread of every CTA
+  if (OUT == OUT_F32 && ep.red.out) {  // every thread of every CTA
+    const bool last = reduce_finish(local, ep.red);
+    if (last && after.alpha && tid == 0) {  // the norm is in place: the step's scalars
+      if (*after.done_in) {
+        *after.done_out = 1;
+      } else {
+        float sh[3];
+        lsqr_step_scalars(after, sh, true);
+      }
+    }
+  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1)
@@ -874,7 +890,7 @@ bool tube_tma_ok(const float* in, const void* out, size_t P, const Epi& ep) {
 
 template <int OUT, int NS>
 int run_tube_tma(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
-                 int* err, cudaStream_t st) {
+                 int* err, cudaStream_t st, const LsqrStep& after = LsqrStep{}) {
   CUtensorMap mi, mp, mo;
   TC_TRY(make_tmap_2d(&mi, in, 0, P, (size_t)n3, TP, n3));
   const int hp = (OUT == OUT_F32 && ep.prev) ? 1 : 0;
@@ -886,7 +902,7 @@ int run_tube_tma(const float* in, void* out, const float* T, int n3, size_t P, c
   const size_t ntile = (P + TP - 1) / TP;
   const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
   k_tube_tma<OUT, NS><<<grid, TT_NT, tube_tma_smem(NS, OUT), st>>>(mi, mp, mo, T, n3, P, hp, ep,
-                                                                   err);
+                                                                   err, after);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -928,16 +944,20 @@ unsigned tube_grid(size_t P, int ns) {
 }  // namespace
 
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
-                    const Epi& ep, int* err, cudaStream_t st, int split3) {
+                    const Epi& ep, int* err, cudaStream_t st, int split3, const LsqrStep* after) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
+  TC_CHECK(!after || (after->alpha && !after->X && ep.red.out));  // scalars after a norm only
   if (tube_tma_ok(in, out, P, ep))
-    return split3 ? run_tube_tma<OUT_F32, 3>(in, out, T_dev, n3, P, ep, err, st)
-                  : run_tube_tma<OUT_F32, 2>(in, out, T_dev, n3, P, ep, err, st);
+    return split3 ? run_tube_tma<OUT_F32, 3>(in, out, T_dev, n3, P, ep, err, st,
+                                             after ? *after : LsqrStep{})
+                  : run_tube_tma<OUT_F32, 2>(in, out, T_dev, n3, P, ep, err, st,
+                                             after ? *after : LsqrStep{});
   if (split3)
     k_tube<OUT_F32, 3><<<tube_grid(P, 3), TNT, tube_smem(3), st>>>(in, out, T_dev, n3, P, ep, err);
   else
     k_tube<OUT_F32, 2><<<tube_grid(P, 2), TNT, tube_smem(2), st>>>(in, out, T_dev, n3, P, ep, err);
   TC_CUDA(cudaGetLastError());
+  if (after) TC_TRY(launch_lsqr_scalars(*after, st));  // its own launch after the pass
   return TC_OK;
 }
 
