@@ -717,7 +717,8 @@ def run_gpu(args):
     prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16,
             "bf16x3": tcprod.TC_BF16X3}[args.precision]
     product = {"th": tcprod.TC_TH, "orthodct": tcprod.TC_ORTHODCT}[args.product]
-    plan = tcprod.Plan(A, B, s=s, precision=prec, product=product)
+    route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL}[args.route]
+    plan = tcprod.Plan(A, B, s=s, precision=prec, product=product, route=route)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
     Cc = plan.cprod(Xt)
     C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
@@ -968,6 +969,9 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16", "bf16x3"],
                     help="slice-GEMM inputs of the main workload (default: bf16 for video_512, "
                          "fp32 otherwise)")
+    ap.add_argument("--route", default="auto", choices=["auto", "spatial"],
+                    help="where c-LSQR keeps its vectors (tc_route); auto takes the "
+                    "dual-domain route where it applies")
     ap.add_argument("--product", default="th", choices=["th", "orthodct"],
                     help="c-product reading: Definition 2.1 (th) or Algorithm 1's dct "
                          "(orthodct; off the fused route LSQR then runs in the transform domain)")

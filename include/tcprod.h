@@ -80,12 +80,27 @@ typedef enum {
                       the slice transpose is then the adjoint) */
 } tc_product;
 
+/* Where c-LSQR keeps its Krylov vectors (results are the same up to rounding):
+ *   TC_ROUTE_AUTO: the library picks. Solves that keep the basis (X_reg
+ *     requested) on BF16 plans of the TH product, one-sided, 32 < n3 <= 64,
+ *     iterate in the transform domains (the dual-domain route): V as
+ *     V x_3 M^{-T}, U as U x_3 M, each product one tcgen05 GEMM with the
+ *     Krylov update in its store plus one tube pass by G = M^{-T} M^{-1} (or
+ *     G^{-1} = M M^T) that writes the next GEMM's BF16 operand and the norm of
+ *     the spatial tensor. X and X_reg are transformed back once (by M^T) at
+ *     the end. ORTHODCT plans off the fused route iterate on dct(C)
+ *     (Definition 2.2's norms are the DCT's). Every other solve is spatial.
+ *   TC_ROUTE_SPATIAL: every product transforms its operand in and its result
+ *     out (Algorithm 1), and the iteration runs on spatial tensors. */
+typedef enum { TC_ROUTE_AUTO = 0, TC_ROUTE_SPATIAL = 1 } tc_route;
+
 typedef struct {
   int precision;   /* tc_precision */
   int gcv_variant; /* tc_gcv_variant */
   int use_graphs;  /* nonzero: solves replay a captured CUDA graph */
   int product;     /* tc_product (default TC_TH) */
-  int reserved[4]; /* must be zero */
+  int route;       /* tc_route (default TC_ROUTE_AUTO) */
+  int reserved[3]; /* must be zero */
 } tc_opts;
 
 /* Outcome of a solve, written to DEVICE memory by the solve (copy it back
@@ -300,6 +315,19 @@ int tc_lsqr_c_learned(tc_plan* plan, const tc_mlp* mlp, const float* C, float* X
  * On the tensor-core forms this is one tcgen05 GEMM launch. */
 int tc_slice_gemm(tc_plan* plan, const void* Xh, float* Yh, int adjoint, tc_stream_t stream);
 
+/* The same slice products with Algorithm 4's update in their store (one
+ * Golub-Kahan half-step in the transform domain, normalisation deferred):
+ *   Yh = (1/s0) (A~_k Xh_k) - (s0/s1) prev   (prev non-NULL), or
+ *   Yh = (1/s0) (A~_k Xh_k)                  (prev NULL; s1 unused);
+ * adjoint = 1 takes A~_k^T. s0, s1: device doubles (s0 = 0 gives a zero
+ * product term, s1 = 0 a zero prev term). prev: device FP32 like Yh, may
+ * alias Yh. sumsq: device double for ||Yh||_F^2 (the library's
+ * deterministic reduction), or NULL. Xh: BF16 as for tc_slice_gemm. TC_BF16
+ * one-sided plans only (TC_EUNSUPPORTED otherwise); one tcgen05 launch, the
+ * GEMM the dual-domain c-LSQR route runs. */
+int tc_slice_gemm_gk(tc_plan* plan, const void* Xh, float* Yh, int adjoint, const double* s0,
+                     const double* s1, const float* prev, double* sumsq, tc_stream_t stream);
+
 /* Steps 1 and 3 of Algorithm 1 alone: the mode-3 transform of Remark 2.1,
  * out = in x_3 T (+ prev), on the plan's transform matrices:
  *   which: TC_M (M, forward), TC_MINV (M^{-1}, inverse), TC_MINVT (M^{-T}, the
@@ -315,6 +343,25 @@ int tc_slice_gemm(tc_plan* plan, const void* Xh, float* Yh, int adjoint, tc_stre
 typedef enum { TC_M = 0, TC_MINV = 1, TC_MINVT = 2, TC_MT = 3 } tc_transform_kind;
 int tc_transform(tc_plan* plan, int which, const float* in, float* out, size_t P,
                  const float* prev, double* sumsq, tc_stream_t stream);
+
+/* The change of domain of the dual-domain c-LSQR route (tc_route): the
+ * forward product's result lives in the M domain (U^ = U x_3 M) and the
+ * adjoint's operand in the M^{-T} domain, so between them
+ *   which = TC_DUAL_U: out = bf16(in x_3 G), G = M^{-T} M^{-1}, and
+ *                      *sumsq = ||in x_3 M^{-1}||_F^2 = ||U||_F^2;
+ *   which = TC_DUAL_V: out = bf16(in x_3 G^{-1}), G^{-1} = M M^T, and
+ *                      *sumsq = ||in x_3 M^T||_F^2 = ||V||_F^2 (in = V x_3 M^{-T}).
+ * Definition 2.2's norm is taken of the spatial tensor, which the pass forms
+ * from the same split BF16 planes of `in` (two planes, error near 2^-16 a
+ * term) and reduces without storing. One tcgen05 pass.
+ *   in: device FP32, n3 slices of P values (slice k at k P); out: device
+ *   BF16, same layout; both 16-byte aligned, P a multiple of 8,
+ *   P n3 <= max(n1, n2) s n3. sumsq: device double.
+ * Plans of the dual-domain route only (TC_TH, TC_BF16, one-sided,
+ * 32 < n3 <= 64, route TC_ROUTE_AUTO); TC_EUNSUPPORTED otherwise. */
+typedef enum { TC_DUAL_U = 0, TC_DUAL_V = 1 } tc_dual_kind;
+int tc_transform_dual(tc_plan* plan, int which, const float* in, void* out, size_t P,
+                      double* sumsq, tc_stream_t stream);
 
 /* The plan's device status word (TC_OK, or TC_ETIMEOUT once a bounded wait of
  * its tensor-core kernels gave up), copied to the host *status. Synchronous. */

@@ -178,7 +178,20 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
 // GEMMs plus the epilogue pass. The DCT is orthogonal, so Definition 2.2's
 // inner products and norms are the same there, and LSQR can run on the
 // transformed tensors throughout.
-bool td_route(const tc_plan* p) { return p->opts.product == TC_ORTHODCT && !fused(p); }
+bool td_route(const tc_plan* p) {
+  return p->opts.product == TC_ORTHODCT && !fused(p) && p->opts.route == TC_ROUTE_AUTO;
+}
+
+// Dual-domain route (TH product, BF16, one-sided, 32 < n3 <= 64): V is kept
+// as V x_3 M^{-T} and U as U x_3 M. The forward product is facewise in the
+// M domain and the exact adjoint (M^T [A~_k^T (Y x_3 M^{-T})_k]) is facewise
+// in the M^{-T} domain, so each product is one slice GEMM plus one change of
+// domain, by G = M^{-T} M^{-1} (U) or G^{-1} = M M^T (V); the norm of the
+// spatial tensor is ||U x_3 M^{-1}|| (||V x_3 M^T||), formed in the same pass.
+bool thd_route(const tc_plan* p) {
+  return p->opts.product == TC_TH && p->opts.precision == TC_BF16 && !p->two_sided &&
+         p->n3 > TC_TUBE_MIN_N3 && p->n3 <= 64 && p->opts.route == TC_ROUTE_AUTO;
+}
 
 int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st) {
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
@@ -212,6 +225,37 @@ int cprod_tdf(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st) {
 int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st) {
   int* err = ep.red.status ? ep.red.status : p->dev_err;
   return launch_umma_epi(*p->uma_td, Xt, static_cast<__nv_bfloat16*>(p->lowV), ep, err, st);
+}
+
+// Dual-domain products (thd_route). Forward: U^ = ca A~ V^ + cp prev in the
+// M domain (the GEMM reads bf16(V^) from lowV, the Krylov update is in its
+// store), then one pass writes lowU = bf16(U^ x_3 G), the adjoint's operand
+// in the M^{-T} domain, and reduces ||U^ x_3 M^{-1}||^2 = ||U||^2 into
+// ep.red. Adjoint: V' = ca A~^T U' + cp prev in the M^{-T} domain, then
+// lowV = bf16(V' x_3 G^{-1}) and ||V' x_3 M^T||^2 = ||V||^2; `after` (an
+// LSQR step's scalars) runs once that norm is in place.
+int cprod_thd(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st) {
+  int* err = ep.red.status ? ep.red.status : p->dev_err;
+  Epi g = ep;
+  g.red = Red{};
+  TC_TRY(launch_umma_epi(*p->umf_td, Yt, nullptr, g, err, st));
+  Epi n;
+  n.red = ep.red;
+  n.skip = ep.skip;
+  return launch_mode3_tc_norm(Yt, p->lowU, p->dG, p->dMinv, p->n3, (size_t)p->n1 * p->s, n, err,
+                              st, nullptr);
+}
+
+int adjoint_thd(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st, const LsqrStep* after) {
+  int* err = ep.red.status ? ep.red.status : p->dev_err;
+  Epi g = ep;
+  g.red = Red{};
+  TC_TRY(launch_umma_epi(*p->uma_td, Xt, nullptr, g, err, st));
+  Epi n;
+  n.red = ep.red;
+  n.skip = ep.skip;
+  return launch_mode3_tc_norm(Xt, p->lowV, p->dGi, p->dMT, p->n3, (size_t)p->n2 * p->s, n, err,
+                              st, after);
 }
 
 int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st) {
@@ -329,6 +373,23 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
   TC_CUDA(cudaMemcpyAsync(p->dMinv, fMi.data(), nn * 4, cudaMemcpyHostToDevice, st));
   TC_CUDA(cudaMemcpyAsync(p->dMinvT, fMiT.data(), nn * 4, cudaMemcpyHostToDevice, st));
   TC_CUDA(cudaMemcpyAsync(p->dMT, fMT.data(), nn * 4, cudaMemcpyHostToDevice, st));
+  if (thd_route(p)) {  // G = M^{-T} M^{-1} and G^{-1} = M M^T, formed in FP64
+    std::vector<float> fG(nn), fGi(nn);
+    for (int i = 0; i < n3; ++i)
+      for (int j = 0; j < n3; ++j) {
+        double g = 0.0, gi = 0.0;
+        for (int r = 0; r < n3; ++r) {
+          g += Mi[(size_t)r * n3 + i] * Mi[(size_t)r * n3 + j];
+          gi += M[(size_t)i * n3 + r] * M[(size_t)j * n3 + r];
+        }
+        fG[(size_t)i * n3 + j] = (float)g;
+        fGi[(size_t)i * n3 + j] = (float)gi;
+      }
+    TC_TRY(dalloc(&p->dG, nn));
+    TC_TRY(dalloc(&p->dGi, nn));
+    TC_CUDA(cudaMemcpyAsync(p->dG, fG.data(), nn * 4, cudaMemcpyHostToDevice, st));
+    TC_CUDA(cudaMemcpyAsync(p->dGi, fGi.data(), nn * 4, cudaMemcpyHostToDevice, st));
+  }
 
   const size_t TA = (size_t)n3 * n1 * n2;
   TC_TRY(dalloc(&p->Ah, TA));
@@ -387,10 +448,11 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
       TC_TRY(make_umma_maps(p->umf2, kind, lowop(p), p->BfL, n1, s, s, n3, ns));
       TC_TRY(make_umma_maps(p->uma2, kind, lowop(p), p->BaL, n2, s, s, n3, ns));
     }
-    if (bf16 && p->opts.product == TC_ORTHODCT && !B) {
-      // transform-domain LSQR with the epilogue in the GEMM: each product's
-      // store also writes the BF16 operand of the next one, so the forward and
-      // adjoint GEMMs read separate buffers (bV: V~, n2 x s; bU: U~, n1 x s)
+    if (bf16 && ((p->opts.product == TC_ORTHODCT && !B) || thd_route(p))) {
+      // transform-domain LSQR with the epilogue in the GEMM: the forward and
+      // adjoint GEMMs read separate BF16 operands (lowV: V~, n2 x s; lowU:
+      // U~, n1 x s), each written by the other product (ORTHODCT: by its
+      // GEMM's store; dual-domain route: by its change-of-domain pass)
       TC_CUDA(cudaMalloc(&p->lowV, (size_t)n2 * s * n3 * 2 * ns));
       TC_CUDA(cudaMalloc(&p->lowU, (size_t)n1 * s * n3 * 2 * ns));
       p->umf_td = new UmmaMaps();
@@ -413,7 +475,7 @@ extern "C" int tc_plan_destroy(tc_plan* p) {
   if (!p) return TC_EINVAL;
   if (p->lsqr_graph) cudaGraphExecDestroy(p->lsqr_graph);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
-  float* fs[] = {p->Ah, p->AhT, p->Bh, p->BhT, p->dM, p->dMinv, p->dMinvT, p->dMT,
+  float* fs[] = {p->Ah, p->AhT, p->Bh, p->BhT, p->dM, p->dMinv, p->dMinvT, p->dMT, p->dG, p->dGi,
                  p->tmp1, p->tmp2, p->tmp3, p->lsqr_U, p->lsqr_V, p->lsqr_W, p->basis,
                  p->gm_basis, p->lsqr_Ct, p->lsqr_Xt};
   for (float* f : fs) dfree(f);
@@ -463,6 +525,7 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
       return TC_EINVAL;
     if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
     if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
+    if (o.route != TC_ROUTE_AUTO && o.route != TC_ROUTE_SPATIAL) return TC_EINVAL;
   }
   if (o.precision != TC_FP32) {
     // tensor-core forms: every dimension a multiple of 8 (16-byte rows for
@@ -529,6 +592,24 @@ extern "C" int tc_slice_gemm(tc_plan* p, const void* Xh, float* Yh, int adjoint,
   return launch_umma(m, Yh, p->dev_err, nullptr, st);
 }
 
+extern "C" int tc_slice_gemm_gk(tc_plan* p, const void* Xh, float* Yh, int adjoint,
+                                const double* s0, const double* s1, const float* prev,
+                                double* sumsq, tc_stream_t stream) {
+  if (!p || !Xh || !Yh || !s0 || (const void*)Xh == (const void*)Yh) return TC_EINVAL;
+  if (p->two_sided || p->opts.precision != TC_BF16) return TC_EUNSUPPORTED;
+  if (prev && !s1) return TC_EINVAL;
+  const int M = adjoint ? p->n2 : p->n1, K = adjoint ? p->n1 : p->n2;
+  UmmaMaps m;
+  TC_TRY(make_umma_maps(&m, 0, adjoint ? p->AhTL : p->AhL, Xh, M, p->s, K, p->n3, 1));
+  Epi ep;
+  ep.coef.rule = prev ? COEF_GK : COEF_INV;
+  ep.coef.s0 = s0;
+  ep.coef.s1 = s1;
+  ep.prev = prev;
+  if (sumsq) ep.red = make_red(p, sumsq, 0, nullptr, nullptr);
+  return launch_umma_epi(m, Yh, nullptr, ep, p->dev_err, (cudaStream_t)stream);
+}
+
 extern "C" int tc_transform(tc_plan* p, int which, const float* in, float* out, size_t P,
                             const float* prev, double* sumsq, tc_stream_t stream) {
   if (!p || !in || !out || (const void*)in == (const void*)out) return TC_EINVAL;
@@ -549,6 +630,21 @@ extern "C" int tc_transform(tc_plan* p, int which, const float* in, float* out, 
   if (lowp(p) && p->n3 > TC_TUBE_MIN_N3)
     return launch_mode3_tc(in, out, T, p->n3, P, ep, p->dev_err, st, x3(p));
   return launch_mode3(in, out, T, p->n3, P, ep, st);
+}
+
+extern "C" int tc_transform_dual(tc_plan* p, int which, const float* in, void* out, size_t P,
+                                 double* sumsq, tc_stream_t stream) {
+  if (!p || !in || !out || !sumsq || (const void*)in == out) return TC_EINVAL;
+  if ((which != TC_DUAL_U && which != TC_DUAL_V) || P < 1 || P * (size_t)p->n3 > p->tmp_elems)
+    return TC_EINVAL;
+  if (!thd_route(p)) return TC_EUNSUPPORTED;
+  if (P % 8 || (reinterpret_cast<uintptr_t>(in) & 15) || (reinterpret_cast<uintptr_t>(out) & 15))
+    return TC_EINVAL;
+  Epi ep;
+  ep.red = make_red(p, sumsq, 0, nullptr, nullptr);
+  const bool u = which == TC_DUAL_U;
+  return launch_mode3_tc_norm(in, out, u ? p->dG : p->dGi, u ? p->dMinv : p->dMT, p->n3, P, ep,
+                              p->dev_err, (cudaStream_t)stream, nullptr);
 }
 
 extern "C" int tc_plan_status(tc_plan* p, int* status) {

@@ -43,7 +43,7 @@ int ensure_lsqr(tc_plan* p, int itermax, bool keep_basis) {
     if (cudaMalloc((void**)&p->lsqr_V, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
     if (cudaMalloc((void**)&p->lsqr_W, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
   }
-  if (td_route(p) && !p->lsqr_Ct) {
+  if ((td_route(p) || thd_route(p)) && !p->lsqr_Ct) {
     moved = true;
     if (cudaMalloc((void**)&p->lsqr_Ct, p->Ty * 4) != cudaSuccess) return TC_ENOMEM;
     if (cudaMalloc((void**)&p->lsqr_Xt, p->Tx * 4) != cudaSuccess) return TC_ENOMEM;
@@ -175,6 +175,12 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   // transformed back once at the end. Norms are unchanged by the orthogonal
   // transform, so every scalar of the solve is the same.
   const bool td = td_route(p) && !a.spatial_basis;
+  // Dual-domain route (TH plans, thd_route, with the basis kept): U^ = U x_3 M
+  // and V' = V x_3 M^{-T} throughout; C^ = C x_3 M is the first forward
+  // product's prev and bf16(C x_3 M^{-T}) the first adjoint's operand. The
+  // basis holds V'_1..V'_k, so X and X_reg are formed there and transformed
+  // back by M^T once. Every scalar is the spatial route's, up to rounding.
+  const bool thd = thd_route(p) && defer;
   const float* Cin = a.C;
   float* Xw = a.X;
   // The tensor-core transform (split BF16, error near 2^-16) serves the TF32
@@ -191,6 +197,13 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     Cin = p->lsqr_Ct;
     Xw = p->lsqr_Xt;
   }
+  if (thd) {
+    TC_TRY(mode3(a.C, p->lsqr_Ct, p->dM, p->Ty / p->n3));
+    TC_TRY(launch_mode3_tc_lowp(a.C, p->lowU, p->dMinvT, p->n3, p->Ty / p->n3, ROUND_BF16,
+                                nullptr, p->dev_err, st));
+    Cin = p->lsqr_Ct;
+    Xw = p->lsqr_Xt;
+  }
   // BF16 plans with fused epilogues keep the GEMM operands as BF16 copies that
   // each product's store writes for the next one; the first is bf16(C~).
   const bool tdf = td && p->umf_td != nullptr;
@@ -198,11 +211,13 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     TC_TRY(launch_round(Cin, p->lowU, p->Ty,
                         p->opts.precision == TC_BF16X3 ? ROUND_BF16X3 : ROUND_BF16, st));
   auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
+    if (thd) return cprod_thd(p, Yv, ep, st);  // steps run in the adjoint's pass (fold)
     if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
     if (step) TC_TRY(step->X ? launch_lsqr_update(*step, st) : launch_lsqr_scalars(*step, st));
     return tdf ? cprod_tdf(p, Yv, ep, st) : cprod_td(p, Xv, Yv, ep, st);
   };
   auto adj = [&](const float* Yv, float* Xv, const Epi& ep, const LsqrStep* after) -> int {
+    if (thd) return adjoint_thd(p, Xv, ep, st, after);
     if (tdf) return adjoint_tdf(p, Xv, ep, st);
     return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st, after);
   };
@@ -212,7 +227,8 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   // the forward product of step j + 1 starts without a launch before it.
   const bool fold = defer && !td && tct;
   // beta_1 = ||C||_F
-  TC_TRY(launch_reduce(Cin, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2), nullptr, st));
+  TC_TRY(launch_reduce(thd ? a.C : Cin, nullptr, p->Ty, make_red(p, beta, 1, nullptr, flags + 2),
+                       nullptr, st));
   // V~_1 = A^T (C / beta_1), alpha_1 = ||V~_1||
   {
     Epi ep;
@@ -300,7 +316,7 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     TC_TRY(launch_learned_predict(a.mlp, alpha, beta, phibar, a.itermax, lam_pred, flags + 6, st));
   const bool gcv_on = keep && !a.lcurve;
   // the basis combination lands in X_reg, or in a workspace to transform back
-  float* Xr_w = td ? p->tmp2 : a.X_reg;
+  float* Xr_w = (td || thd) ? p->tmp2 : a.X_reg;
   if (keep && a.lcurve) {  // X_reg = X_{k_opt} at the L-curve corner (flags[8] = k_opt)
     TC_TRY(launch_lcurve(rgiv, phibar, flags + 1, kp, a.curve, y, flags + 8, st));
   } else if (keep) {
@@ -320,9 +336,10 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
     TC_TRY(launch_combine(Xr_w, nullptr, p->basis, p->Tx, kp, a.lcurve ? flags + 8 : flags + 1,
                           y, p->Tx, nullptr, st));
   }
-  if (td) {  // back to the spatial domain: X = idct(X~), X_reg likewise
-    TC_TRY(mode3(Xw, a.X, p->dMinv, p->Tx / p->n3));
-    if (keep) TC_TRY(mode3(Xr_w, a.X_reg, p->dMinv, p->Tx / p->n3));
+  if (td || thd) {  // back to the spatial domain: X = idct(X~) (X' x_3 M^T), X_reg likewise
+    const float* back = thd ? p->dMT : p->dMinv;
+    TC_TRY(mode3(Xw, a.X, back, p->Tx / p->n3));
+    if (keep) TC_TRY(mode3(Xr_w, a.X_reg, back, p->Tx / p->n3));
   }
   k_lsqr_info<<<1, 1, 0, st>>>(a.info, flags, phibar, beta, gcv_on ? lam : nullptr,
                                gcv_on ? gcv : nullptr, (keep && a.lcurve) ? flags + 8 : nullptr);

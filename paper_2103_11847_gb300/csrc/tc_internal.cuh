@@ -105,6 +105,7 @@ struct tc_plan {
   float *Ah = nullptr, *AhT = nullptr;     // A x_3 M and its slice transposes
   float *Bh = nullptr, *BhT = nullptr;
   float *dM = nullptr, *dMinv = nullptr, *dMinvT = nullptr, *dMT = nullptr;  // n3 x n3
+  float *dG = nullptr, *dGi = nullptr;  // dual-domain route: M^{-T} M^{-1} and M M^T
   float hM[TC_MAX_FUSED * TC_MAX_FUSED], hMinv[TC_MAX_FUSED * TC_MAX_FUSED];
   float hMinvT[TC_MAX_FUSED * TC_MAX_FUSED], hMT[TC_MAX_FUSED * TC_MAX_FUSED];
   float *tmp1 = nullptr, *tmp2 = nullptr;  // transform-domain intermediates
@@ -210,6 +211,13 @@ enum RoundKind { ROUND_TF32 = 0, ROUND_BF16 = 1, ROUND_BF16X3 = 2 };
 int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, size_t P,
                     const Epi& ep, int* err, cudaStream_t st, int split3 = 0,
                     const LsqrStep* after = nullptr);
+// Dual-domain pass (BF16 plans, n3 <= 64, P % 8 == 0, 16-byte aligned
+// tensors; else TC_EUNSUPPORTED): out = bf16(in x_3 T) and ep.red = the
+// reduction of ||in x_3 N||_F^2, both from the same split planes of `in`.
+// No prev, no coefficients. after: as for launch_mode3_tc.
+int launch_mode3_tc_norm(const float* in, void* out, const float* T_dev, const float* N_dev,
+                         int n3, size_t P, const Epi& ep, int* err, cudaStream_t st,
+                         const LsqrStep* after);
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                          int kind, const int* skip, int* err, cudaStream_t st);
 // Elementwise rounding of n FP32 values to the operand type `kind` (RoundKind).
@@ -285,11 +293,17 @@ Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* sta
 // Transform-domain products (ORTHODCT plans off the fused route; td_route):
 // operand and result are transformed tensors, the epilogue applies to them.
 bool td_route(const tc_plan* p);
+// The dual-domain route of TH plans (BF16, one-sided, 32 < n3 <= 64).
+bool thd_route(const tc_plan* p);
 int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st);
 int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream_t st);
 // With a fused-epilogue BF16 plan (umf_td set): operands from lowV / lowU,
 // and each product writes the other's operand (see plan.cu).
 int cprod_tdf(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st);
+// Dual-domain products (thd_route): the GEMM with the Krylov update, then the
+// change of domain writing the other product's BF16 operand and the norm.
+int cprod_thd(tc_plan* p, float* Yt, const Epi& ep, cudaStream_t st);
+int adjoint_thd(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st, const LsqrStep* after);
 int adjoint_tdf(tc_plan* p, float* Xt, const Epi& ep, cudaStream_t st);
 int tc_kernels_init();
 

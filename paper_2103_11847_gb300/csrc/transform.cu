@@ -545,6 +545,12 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
 // the split and the MMAs of the next tiles. Requirements (checked by the
 // launcher, else k_tube runs): P % 8 == 0 (16-byte rows of the FP32 and BF16
 // boxes), 16-byte aligned tensors, no dot-product reduction.
+// NRM (BF16 output, two planes): a second matrix N multiplies the same A
+// planes into a second pair of accumulators, and the epilogue sums the
+// squares of in x_3 N into ep.red instead of storing them. The dual-domain
+// iteration (transform-domain LSQR under the TH product) uses it to form the
+// next GEMM operand, bf16(in x_3 G), and the Frobenius norm of the spatial
+// tensor, ||in x_3 N||_F, in one pass over `in`.
 constexpr int TT_NT = 608;
 constexpr uint32_t TT_SLOT = TK * TP * 4;  // one FP32 box of 64 x 128: 32 KB
 // Slots: two planes (A in the input slot) 3 input + 3 output, or 4 + 4
@@ -553,21 +559,25 @@ constexpr uint32_t TT_SLOT = TK * TP * 4;  // one FP32 box of 64 x 128: 32 KB
 constexpr int tube_tma_in(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
 constexpr int tube_tma_out(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
 constexpr uint32_t tube_tma_oslot(int out) { return out == OUT_BF16 ? TT_SLOT / 2 : TT_SLOT; }
-constexpr size_t tube_tma_smem(int ns, int out) {
+constexpr size_t tube_tma_smem(int ns, int out, bool nrm = false) {
   return 1024 + tube_tma_in(ns, out) * TT_SLOT + tube_tma_out(ns, out) * tube_tma_oslot(out) +
-         (ns == 3 ? ns * TA_BYTES : 0) + ns * TB_BYTES +
+         (ns == 3 ? ns * TA_BYTES : 0) + (nrm ? 2 : 1) * ns * TB_BYTES +
          (3 * tube_tma_in(ns, out) + 3 * tube_tma_out(ns, out) + 7) * 8 + 16;
 }
 
-template <int OUT, int NS>
+template <int OUT, int NS, bool NRM = false>
 __global__ void __launch_bounds__(TT_NT, 1)
 k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
-           const __grid_constant__ CUtensorMap tmOut, const float* __restrict__ T, int n3,
-           size_t P, int has_prev, Epi ep, int* err, LsqrStep after) {
+           const __grid_constant__ CUtensorMap tmOut, const float* __restrict__ T,
+           const float* __restrict__ N, int n3, size_t P, int has_prev, Epi ep, int* err,
+           LsqrStep after) {
   constexpr int NPASS = NS == 2 ? 3 : 6;
   constexpr int NI = tube_tma_in(NS, OUT), NO = tube_tma_out(NS, OUT);
   constexpr uint32_t OSLOT = tube_tma_oslot(OUT);
   constexpr bool INPLACE = NS == 2;  // A planes over the input slot
+  constexpr bool RED = OUT == OUT_F32 || NRM;  // the pass reduces into ep.red
+  constexpr uint32_t NCOL = NRM ? 4 * TK : 2 * TK;  // tensor-memory columns
+  static_assert(!NRM || (OUT == OUT_BF16 && NS == 2), "the norm pass writes a BF16 operand");
   using namespace tc5;
   constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
                              ((uint32_t)(TK >> 3) << 17) | ((uint32_t)(TP >> 4) << 24);
@@ -584,8 +594,8 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   uint8_t* sin = base;                    // NI input slots
   uint8_t* sout = base + NI * TT_SLOT;    // NO prev / output slots
   uint8_t* sAx = sout + NO * OSLOT;       // three planes: the A buffer
-  uint8_t* sB = sAx + (INPLACE ? 0 : NS * TA_BYTES);  // NS B planes
-  uint64_t* ifull = reinterpret_cast<uint64_t*>(sB + NS * TB_BYTES);  // [NI] input loaded
+  uint8_t* sB = sAx + (INPLACE ? 0 : NS * TA_BYTES);  // NS B planes (NRM: then N's NS planes)
+  uint64_t* ifull = reinterpret_cast<uint64_t*>(sB + (NRM ? 2 : 1) * NS * TB_BYTES);  // [NI] input loaded
   uint64_t* iempty = ifull + NI;          // [NI] input split (8 converter warps)
   // A planes written (8 converter warps), one barrier an input slot: the
   // converters may run up to NI tiles ahead of the MMAs when A is in place,
@@ -632,25 +642,27 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   if (warp >= 3 && warp < 11) {  // B = T once: unit u is row n = u / 8, slices 8 (u % 8) + 0..7
     const int ct = tid - 96;
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int u = ct + 256 * j, n = u >> 3, c = u & 7;
+    for (int j = 0; j < (NRM ? 4 : 2); ++j) {  // NRM: j >= 2 stages N
+      const int u = ct + 256 * (j & 1), n = u >> 3, c = u & 7;
+      const float* src = j < 2 ? T : N;
+      uint8_t* dst = sB + (j < 2 ? 0 : NS * TB_BYTES);
       float t[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
         const int l = 8 * c + e;
-        t[e] = (n < n3 && l < n3) ? __ldg(T + (size_t)n * n3 + l) : 0.f;
+        t[e] = (n < n3 && l < n3) ? __ldg(src + (size_t)n * n3 + l) : 0.f;
       }
       uint4 pl[NS];
       split8<NS>(t, pl);
       const uint32_t off = n * 128 + ((c ^ (n & 7)) << 4);
 #pragma unroll
-      for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(sB + q * TB_BYTES + off) = pl[q];
+      for (int q = 0; q < NS; ++q) *reinterpret_cast<uint4*>(dst + q * TB_BYTES + off) = pl[q];
     }
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      su32(tslot)),
-                 "r"(2 * TK)
+                 "r"(NCOL)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -711,13 +723,17 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
         const uint32_t acc = tmem + (uint32_t)(d * TK);
         uint8_t* sA = INPLACE ? sin + (i % NI) * TT_SLOT : sAx;
 #pragma unroll
-        for (int pass = 0; pass < NPASS; ++pass) {
-          const uint32_t a0 = su32(sA + tube_pa(pass) * TA_BYTES);
-          const uint32_t b0 = su32(sB + tube_pb(pass) * TB_BYTES);
+        for (int m = 0; m < (NRM ? 2 : 1); ++m) {  // m = 1: N into the second pair
 #pragma unroll
-          for (int kk = 0; kk < TK / 16; ++kk)
-            umma<0>(acc, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
-                    smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+          for (int pass = 0; pass < NPASS; ++pass) {
+            const uint32_t a0 = su32(sA + tube_pa(pass) * TA_BYTES);
+            const uint32_t b0 = su32(sB + (m * NS + tube_pb(pass)) * TB_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk)
+              umma<0>(acc + (uint32_t)(m * 2 * TK),
+                      smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
+                      smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+          }
         }
         umma_commit(INPLACE ? iempty + (i % NI) : aempty);  // the A planes are read
         umma_commit(dfull + d);
@@ -800,6 +816,15 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
         const int h = hh;
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(d * TK + 32 * h), v);
+        if (NRM) {  // the squares of in x_3 N (the second pair) into the norm
+          float w[32];
+          tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(2 * TK + d * TK + 32 * h), w);
+          if (live) {
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+              if (32 * h + j < n3) local = fmaf(w[j], w[j], local);
+          }
+        }
         // this warp's part of the accumulator is read: hand it back
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -862,7 +887,7 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
     for (int g = (issued_p > NO ? issued_p - NO : 0); g < issued_p; ++g)
       mbar_wait(ofull + g % NO, (uint32_t)(g / NO) & 1u);
   }
-  if (OUT == OUT_F32 && ep.red.out) {  // every thread of every CTA
+  if (RED && ep.red.out) {  // every thread of every CTA
     const bool last = reduce_finish(local, ep.red);
     if (last && after.alpha && tid == 0) {  // the norm is in place: the step's scalars
       if (*after.done_in) {
@@ -876,7 +901,7 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TK)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NCOL)
                  : "memory");
 }
 
@@ -888,9 +913,10 @@ bool tube_tma_ok(const float* in, const void* out, size_t P, const Epi& ep) {
          ep.red.other == nullptr;
 }
 
-template <int OUT, int NS>
+template <int OUT, int NS, bool NRM = false>
 int run_tube_tma(const float* in, void* out, const float* T, int n3, size_t P, const Epi& ep,
-                 int* err, cudaStream_t st, const LsqrStep& after = LsqrStep{}) {
+                 int* err, cudaStream_t st, const LsqrStep& after = LsqrStep{},
+                 const float* N = nullptr) {
   CUtensorMap mi, mp, mo;
   TC_TRY(make_tmap_2d(&mi, in, 0, P, (size_t)n3, TP, n3));
   const int hp = (OUT == OUT_F32 && ep.prev) ? 1 : 0;
@@ -901,8 +927,8 @@ int run_tube_tma(const float* in, void* out, const float* T, int n3, size_t P, c
   TC_TRY(make_tmap_2d(&mo, out, OUT == OUT_BF16 ? 1 : 0, P, (size_t)n3, TP, n3));
   const size_t ntile = (P + TP - 1) / TP;
   const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
-  k_tube_tma<OUT, NS><<<grid, TT_NT, tube_tma_smem(NS, OUT), st>>>(mi, mp, mo, T, n3, P, hp, ep,
-                                                                   err, after);
+  k_tube_tma<OUT, NS, NRM><<<grid, TT_NT, tube_tma_smem(NS, OUT, NRM), st>>>(
+      mi, mp, mo, T, N, n3, P, hp, ep, err, after);
   TC_CUDA(cudaGetLastError());
   return TC_OK;
 }
@@ -961,6 +987,16 @@ int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, siz
   return TC_OK;
 }
 
+int launch_mode3_tc_norm(const float* in, void* out, const float* T_dev, const float* N_dev,
+                         int n3, size_t P, const Epi& ep, int* err, cudaStream_t st,
+                         const LsqrStep* after) {
+  TC_CHECK(n3 > 0 && n3 <= TK && ep.red.out && !ep.prev);
+  TC_CHECK(!after || (after->alpha && !after->X));
+  if (!tube_tma_ok(in, out, P, ep)) return TC_EUNSUPPORTED;
+  return run_tube_tma<OUT_BF16, 2, true>(in, out, T_dev, n3, P, ep, err, st,
+                                         after ? *after : LsqrStep{}, N_dev);
+}
+
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                          int kind, const int* skip, int* err, cudaStream_t st) {
   TC_CHECK(n3 >= 1 && n3 <= TK);
@@ -999,6 +1035,9 @@ int transform_init() {
                                (int)tube_tma_smem(2, OUT_TF32)));
   TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tube_tma_smem(3, OUT_F32)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_BF16, 2, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(2, OUT_BF16, true)));
   for (auto fn : {k_tube<OUT_F32, 3>, k_tube<OUT_BF16X3, 3>}) {
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)tube_smem(3)));

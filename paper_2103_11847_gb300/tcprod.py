@@ -19,13 +19,15 @@ TC_FP32, TC_TF32, TC_BF16, TC_BF16X3 = 0, 1, 2, 3
 TC_GCV_PAPER, TC_GCV_FULL = 0, 1
 TC_TH, TC_ORTHODCT = 0, 1
 TC_M, TC_MINV, TC_MINVT, TC_MT = 0, 1, 2, 3
+TC_ROUTE_AUTO, TC_ROUTE_SPATIAL = 0, 1
+TC_DUAL_U, TC_DUAL_V = 0, 1
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
                 TC_ENONFINITE: "nonfinite"}
 
 
 class tc_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("gcv_variant", c_int), ("use_graphs", c_int),
-                ("product", c_int), ("reserved", c_int * 4)]
+                ("product", c_int), ("route", c_int), ("reserved", c_int * 3)]
 
 
 class tc_solve_info(ctypes.Structure):
@@ -59,6 +61,10 @@ _SIGS = {
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
     "tc_transform": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p, c_void_p,
                       c_void_p], c_int),
+    "tc_slice_gemm_gk": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
+                          c_void_p, c_void_p], c_int),
+    "tc_transform_dual": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p,
+                           c_void_p], c_int),
     "tc_plan_status": ([c_void_p, ctypes.POINTER(c_int)], c_int),
     "tc_lsqr_graph_kernels": ([c_void_p, ctypes.POINTER(c_int)], c_int),
     "tc_check_recip": ([c_void_p, ctypes.c_size_t, c_void_p, c_void_p, c_void_p], c_int),
@@ -140,7 +146,7 @@ def tc_version():
 
 
 def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                   use_graphs=True, stream=None, product=TC_TH):
+                   use_graphs=True, stream=None, product=TC_TH, route=TC_ROUTE_AUTO):
     """A: (n3, n1, n2); B: (n3, s, s) or None (then s must be given)."""
     n3, n1, n2 = A.shape
     if B is not None:
@@ -148,7 +154,7 @@ def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPE
         _ptr(B, shape=(n3, s, s), name="B")
     if s is None:
         raise ValueError("s (columns of X) is required for a one-sided plan")
-    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)), product)
+    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)), product, route)
     h = c_void_p()
     _check("tc_plan_create", lib().tc_plan_create(ctypes.byref(h), n1, n2, s, n3, _ptr(A, name="A"),
                                                   _ptr(B, name="B"), ctypes.byref(o),
@@ -236,6 +242,28 @@ def tc_transform(h, which, X, Y, prev=None, sumsq=None, stream=None):
                                               P, _ptr(prev, name="prev"),
                                               _ptr(sumsq, torch.float64, name="sumsq"),
                                               _stream(stream)))
+
+
+def tc_slice_gemm_gk(h, Xh, Yh, s0, s1=None, prev=None, sumsq=None, adjoint=False,
+                     stream=None):
+    """Yh = (1/s0) A~_k Xh_k - (s0/s1) prev (A~^T for adjoint); Xh BF16;
+    s0, s1, sumsq: device float64 tensors of one element."""
+    _check("tc_slice_gemm_gk", lib().tc_slice_gemm_gk(
+        h, _ptr(Xh, torch.bfloat16, name="Xh"), _ptr(Yh, name="Yh"), int(bool(adjoint)),
+        _ptr(s0, torch.float64, name="s0"), _ptr(s1, torch.float64, name="s1"),
+        _ptr(prev, name="prev"), _ptr(sumsq, torch.float64, name="sumsq"), _stream(stream)))
+
+
+def tc_transform_dual(h, which, X, Y, sumsq, stream=None):
+    """Y = bf16(X x_3 G) (which = TC_DUAL_U) or bf16(X x_3 G^-1) (TC_DUAL_V),
+    sumsq = ||X x_3 M^-1||^2 or ||X x_3 M^T||^2; X FP32, Y BF16, same shape
+    (n3, ...); sumsq: device double."""
+    P = X[0].numel()
+    if Y.shape != X.shape:
+        raise ValueError("X and Y must have the same shape")
+    _check("tc_transform_dual", lib().tc_transform_dual(
+        h, int(which), _ptr(X, name="X"), _ptr(Y, torch.bfloat16, name="Y"), P,
+        _ptr(sumsq, torch.float64, name="sumsq"), _stream(stream)))
 
 
 def tc_plan_status(h):
@@ -413,12 +441,12 @@ class Plan:
     """Owns a tc_plan for A (and B); methods allocate outputs as torch tensors."""
 
     def __init__(self, A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                 use_graphs=True, product=TC_TH):
+                 use_graphs=True, product=TC_TH, route=TC_ROUTE_AUTO):
         self.n3, self.n1, self.n2 = A.shape
         self.s = B.shape[1] if B is not None else s
         self.two_sided = B is not None
         self.handle = tc_plan_create(A, B, s, precision, gcv_variant, use_graphs,
-                                     product=product)
+                                     product=product, route=route)
 
     def close(self):
         if self.handle is not None:
