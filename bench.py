@@ -271,8 +271,9 @@ def precision_forms(dev, peaks, steps=3):
                                     "hbm_frac": gbs / peaks.get("hbm_gbs", FALLBACK_HBM_GBS),
                                     "algorithmic_bytes": gbytes}}
         plan.close()
+    out["bf16_dual"] = dual_route_form(A, C, Xt, s, iters, dev, peaks, steps)
     base = out["fp32"]["rel_err_reg"]
-    for name in ("tf32", "bf16", "bf16x3"):
+    for name in ("tf32", "bf16", "bf16x3", "bf16_dual"):
         out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
         out[name]["speedup_vs_fp32"] = out[name]["iters_per_s"] / out["fp32"]["iters_per_s"]
     # Algorithm 1's dct reading (ORTHODCT): off the fused route LSQR runs in the
@@ -301,6 +302,60 @@ def precision_forms(dev, peaks, steps=3):
                                        <= 0.02 * od["fp32"]["rel_err_reg"])
     out["orthodct_transform_domain"] = od
     return out
+
+
+def dual_route_form(A, C, Xt, s, iters, dev, peaks, steps):
+    """The BF16 form on the dual-domain route (TC_ROUTE_DUAL): the solve's
+    LSQR iterations/s and reconstruction error, and its two kernels timed
+    alone against the HBM roofline. Per product: the tcgen05 GEMM with the
+    Golub-Kahan update in its store (reads A~ and the operand in BF16 and prev
+    in FP32, writes the FP32 result) and the change-of-domain pass (reads the
+    FP32 result, writes the BF16 operand of the other product)."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    n3, n1, n2 = A.shape
+    st = torch.cuda.current_stream()
+    plan = tcprod.Plan(A, s=s, precision=tcprod.TC_BF16, route=tcprod.TC_ROUTE_DUAL)
+    X = torch.empty(plan.xshape(), device=dev)
+    Xr = torch.empty(plan.xshape(), device=dev)
+    info = tcprod.new_info()
+    tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    kernels = tcprod.tc_lsqr_graph_kernels(plan.handle)
+    Xh = torch.randn((n3, n2, s), device=dev).to(torch.bfloat16)
+    Y = torch.empty((n3, n1, s), device=dev)
+    prev = torch.randn((n3, n1, s), device=dev)
+    Yb = torch.empty((n3, n1, s), dtype=torch.bfloat16, device=dev)
+    s0 = torch.tensor([2.0], dtype=torch.float64, device=dev)
+    s1 = torch.tensor([3.0], dtype=torch.float64, device=dev)
+    ss = torch.zeros(1, dtype=torch.float64, device=dev)
+    hbm = peaks.get("hbm_gbs", FALLBACK_HBM_GBS)
+    T = n3 * n1 * s
+    gk_ms = graph_time(lambda: tcprod.tc_slice_gemm_gk(plan.handle, Xh, Y, s0, s1, prev), 30)
+    gk_bytes = 2 * n3 * n1 * n2 + 2 * n3 * n2 * s + 8 * T
+    du_ms = graph_time(lambda: tcprod.tc_transform_dual(plan.handle, tcprod.TC_DUAL_U, Y, Yb, ss),
+                       30)
+    du_bytes = 6 * T
+    plan.close()
+    k = lambda name, t, b: {"kernel": name, "ms": t, "GB_per_s": b / (t * 1e-3) / 1e9,
+                            "hbm_frac": b / (t * 1e-3) / 1e9 / hbm, "algorithmic_bytes": b}
+    return {"iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+            "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+            "rel_err_lsqr": float((X - Xt).norm() / Xt.norm()),
+            "kernels_per_solve": kernels,
+            "route": "dual-domain (TC_ROUTE_DUAL): V x_3 M^-T and U x_3 M, one GEMM and one "
+                     "change of domain a product",
+            "gemm_gk": k("k_umma_gemm<EPI> (tcgen05, Golub-Kahan update in the store)", gk_ms,
+                         gk_bytes),
+            "change_of_domain": k("k_tube_tma<OUT_BF16, 2, NRM> (x_3 G, norm of x_3 M^-1)", du_ms,
+                                  du_bytes)}
 
 
 GROUP_TILES = {0: ["64x64 FFMA tiles of 4x4", "32x32 FFMA tiles of 4x2", "64x64 FFMA tiles of 8x4"],
@@ -717,7 +772,8 @@ def run_gpu(args):
     prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16,
             "bf16x3": tcprod.TC_BF16X3}[args.precision]
     product = {"th": tcprod.TC_TH, "orthodct": tcprod.TC_ORTHODCT}[args.product]
-    route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL}[args.route]
+    route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL,
+             "dual": tcprod.TC_ROUTE_DUAL}[args.route]
     plan = tcprod.Plan(A, B, s=s, precision=prec, product=product, route=route)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
     Cc = plan.cprod(Xt)
@@ -969,9 +1025,8 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16", "bf16x3"],
                     help="slice-GEMM inputs of the main workload (default: bf16 for video_512, "
                          "fp32 otherwise)")
-    ap.add_argument("--route", default="auto", choices=["auto", "spatial"],
-                    help="where c-LSQR keeps its vectors (tc_route); auto takes the "
-                    "dual-domain route where it applies")
+    ap.add_argument("--route", default="auto", choices=["auto", "spatial", "dual"],
+                    help="where c-LSQR keeps its vectors (tc_route)")
     ap.add_argument("--product", default="th", choices=["th", "orthodct"],
                     help="c-product reading: Definition 2.1 (th) or Algorithm 1's dct "
                          "(orthodct; off the fused route LSQR then runs in the transform domain)")

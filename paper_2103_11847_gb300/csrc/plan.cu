@@ -179,7 +179,7 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
 // inner products and norms are the same there, and LSQR can run on the
 // transformed tensors throughout.
 bool td_route(const tc_plan* p) {
-  return p->opts.product == TC_ORTHODCT && !fused(p) && p->opts.route == TC_ROUTE_AUTO;
+  return p->opts.product == TC_ORTHODCT && !fused(p) && p->opts.route != TC_ROUTE_SPATIAL;
 }
 
 // Dual-domain route (TH product, BF16, one-sided, 32 < n3 <= 64): V is kept
@@ -190,7 +190,7 @@ bool td_route(const tc_plan* p) {
 // spatial tensor is ||U x_3 M^{-1}|| (||V x_3 M^T||), formed in the same pass.
 bool thd_route(const tc_plan* p) {
   return p->opts.product == TC_TH && p->opts.precision == TC_BF16 && !p->two_sided &&
-         p->n3 > TC_TUBE_MIN_N3 && p->n3 <= 64 && p->opts.route == TC_ROUTE_AUTO;
+         p->n3 > TC_TUBE_MIN_N3 && p->n3 <= 64 && p->opts.route == TC_ROUTE_DUAL;
 }
 
 int cprod_td(tc_plan* p, const float* Xt, float* Yt, const Epi& ep, cudaStream_t st) {
@@ -525,7 +525,8 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
       return TC_EINVAL;
     if (o.gcv_variant != TC_GCV_PAPER && o.gcv_variant != TC_GCV_FULL) return TC_EINVAL;
     if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
-    if (o.route != TC_ROUTE_AUTO && o.route != TC_ROUTE_SPATIAL) return TC_EINVAL;
+    if (o.route != TC_ROUTE_AUTO && o.route != TC_ROUTE_SPATIAL && o.route != TC_ROUTE_DUAL)
+      return TC_EINVAL;
   }
   if (o.precision != TC_FP32) {
     // tensor-core forms: every dimension a multiple of 8 (16-byte rows for

@@ -19,7 +19,7 @@ TC_FP32, TC_TF32, TC_BF16, TC_BF16X3 = 0, 1, 2, 3
 TC_GCV_PAPER, TC_GCV_FULL = 0, 1
 TC_TH, TC_ORTHODCT = 0, 1
 TC_M, TC_MINV, TC_MINVT, TC_MT = 0, 1, 2, 3
-TC_ROUTE_AUTO, TC_ROUTE_SPATIAL = 0, 1
+TC_ROUTE_AUTO, TC_ROUTE_SPATIAL, TC_ROUTE_DUAL = 0, 1, 2
 TC_DUAL_U, TC_DUAL_V = 0, 1
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
                 TC_ENONFINITE: "nonfinite"}

@@ -51,7 +51,7 @@ def test_change_of_domain_pass(tc, n3, P):
     # P = 1000: seven full tiles of 128 pixels and a ragged tail of 104
     rng = np.random.default_rng(n3 + P)
     A = f32(rng.standard_normal((n3, 64, 64)))
-    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16)
+    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16, route=tc.TC_ROUTE_DUAL)
     M = cp.transform_matrix(n3)
     Mi = np.linalg.inv(M)
     X = f32(rng.standard_normal((n3, P)))
@@ -76,14 +76,16 @@ def test_change_of_domain_pass_rejects_other_plans(tc):
     Y = torch.empty((64, 64), dtype=torch.bfloat16, device="cuda")
     ss = torch.zeros(1, dtype=torch.float64, device="cuda")
     for kw in [dict(precision=tc.TC_FP32), dict(precision=tc.TC_TF32),
-               dict(precision=tc.TC_BF16, product=tc.TC_ORTHODCT),
-               dict(precision=tc.TC_BF16, route=tc.TC_ROUTE_SPATIAL)]:
+               dict(precision=tc.TC_BF16, product=tc.TC_ORTHODCT, route=tc.TC_ROUTE_DUAL),
+               dict(precision=tc.TC_BF16, route=tc.TC_ROUTE_SPATIAL),
+               dict(precision=tc.TC_BF16, route=tc.TC_ROUTE_AUTO)]:
         plan = tc.Plan(dev(rng.standard_normal((64, 64, 64))), s=64, **kw)
         with pytest.raises(tc.TcError) as e:
             tc.tc_transform_dual(plan.handle, tc.TC_DUAL_U, X, Y, ss)
         assert e.value.code == tc.TC_EUNSUPPORTED
         plan.close()
-    plan = tc.Plan(dev(rng.standard_normal((16, 64, 64))), s=64, precision=tc.TC_BF16)
+    plan = tc.Plan(dev(rng.standard_normal((16, 64, 64))), s=64, precision=tc.TC_BF16,
+                   route=tc.TC_ROUTE_DUAL)
     with pytest.raises(tc.TcError):  # n3 = 16: no dual-domain route
         tc.tc_transform_dual(plan.handle, tc.TC_DUAL_U, X[:16], Y[:16], ss)
     plan.close()
@@ -106,7 +108,7 @@ def test_dual_route_lsqr_against_oracle_and_spatial(tc, video64):
     A, C, Xt, ref = video64
     e_ref = mt.relative_error(Xt, ref["X_reg"])
     out = {}
-    for route in (tc.TC_ROUTE_AUTO, tc.TC_ROUTE_SPATIAL):
+    for route in (tc.TC_ROUTE_DUAL, tc.TC_ROUTE_SPATIAL):
         plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16, route=route)
         X, Xr, hist, info = plan.lsqr(dev(C), 20, regularize=True, history=True)
         torch.cuda.synchronize()
@@ -116,7 +118,7 @@ def test_dual_route_lsqr_against_oracle_and_spatial(tc, video64):
         out[route] = (rel(Xr.cpu().numpy(), Xt), hist.cpu().numpy(), X.cpu().numpy(),
                       tc.tc_lsqr_graph_kernels(plan.handle))
         plan.close()
-    e_d, h_d, X_d, k_d = out[tc.TC_ROUTE_AUTO]
+    e_d, h_d, X_d, k_d = out[tc.TC_ROUTE_DUAL]
     e_s, h_s, X_s, k_s = out[tc.TC_ROUTE_SPATIAL]
     print("oracle", e_ref, "dual", e_d, "spatial", e_s, "kernels", k_d, k_s)
     assert abs(e_d - e_ref) < 0.02 * e_ref
@@ -134,7 +136,7 @@ def test_dual_route_short_solves(tc, video64, itermax):
     op = lambda X: cp.cprod(A, X)
     adj = lambda Y: cp.cprod_adjoint(A, Y)
     ref = kr.lsqr_gcv(op, adj, C, itermax=itermax)
-    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16)
+    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16, route=tc.TC_ROUTE_DUAL)
     X, Xr, _, info = plan.lsqr(dev(C), itermax, regularize=True)
     torch.cuda.synchronize()
     assert tc.read_info(info)["iters"] == itermax
@@ -151,7 +153,7 @@ def test_dual_route_early_stop(tc, video64):
     op = lambda X: cp.cprod(A, X)
     adj = lambda Y: cp.cprod_adjoint(A, Y)
     r = kr.lsqr(op, adj, C, 20, tol=tol)
-    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16)
+    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16, route=tc.TC_ROUTE_DUAL)
     X, Xr, _, info = plan.lsqr(dev(C), 20, tol=tol, regularize=True)
     torch.cuda.synchronize()
     inf = tc.read_info(info)
