@@ -1080,10 +1080,26 @@ def kernel_only(args):
     B = torch.from_numpy(w["B"].astype(np.float32)).to(dev) if two else None
     prec = {"fp32": tcprod.TC_FP32, "tf32": tcprod.TC_TF32, "bf16": tcprod.TC_BF16,
             "bf16x3": tcprod.TC_BF16X3}[args.precision]
-    plan = tcprod.Plan(A, B, s=s, precision=prec)
+    route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL,
+             "dual": tcprod.TC_ROUTE_DUAL}[args.route]
+    plan = tcprod.Plan(A, B, s=s, precision=prec, route=route)
     dk = dominant_kernel(plan, args, (n1, n2, s, n3, two), dev)
     for _ in range(8):
         dk["call"]()
+    if route == tcprod.TC_ROUTE_DUAL:
+        # the dual-domain route's two kernels, four launches each: the GEMM
+        # with the Golub-Kahan update, then the change of domain
+        Xh = torch.randn((n3, n2, s), device=dev).to(torch.bfloat16)
+        Y = torch.empty((n3, n1, s), device=dev)
+        prev = torch.randn((n3, n1, s), device=dev)
+        Yb = torch.empty((n3, n1, s), dtype=torch.bfloat16, device=dev)
+        s0 = torch.tensor([2.0], dtype=torch.float64, device=dev)
+        s1 = torch.tensor([3.0], dtype=torch.float64, device=dev)
+        ss = torch.zeros(1, dtype=torch.float64, device=dev)
+        for _ in range(4):
+            tcprod.tc_slice_gemm_gk(plan.handle, Xh, Y, s0, s1, prev)
+        for _ in range(4):
+            tcprod.tc_transform_dual(plan.handle, tcprod.TC_DUAL_U, Y, Yb, ss)
     # then whole forward products (every pass of one product, e.g. the
     # transform to the GEMM operand before the slice GEMMs)
     Xp, Yp = torch.randn(plan.xshape(), device=dev), torch.empty(plan.yshape(), device=dev)
