@@ -186,18 +186,43 @@ def cpu_run(workload, sample, steps, budget_s, threads=None):
     return out
 
 
+def cpu_run_all_cores(workload, sample):
+    """One single-threaded oracle worker per core this process may run on,
+    all started together, each running the same bounded sample (independent
+    replicas of the solve, as the GPU's replicas are): their times."""
+    n = len(os.sched_getaffinity(0))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", workload, "--cpu-sample",
+           str(sample), "--cpu-steps", "1", "--cpu-budget", "0"]
+    t0 = time.perf_counter()
+    procs = [subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.PIPE, text=True,
+                              env=env) for _ in range(n)]
+    outs = [p.communicate(timeout=1800) for p in procs]
+    wall = time.perf_counter() - t0
+    if any(p.returncode != 0 for p in procs):
+        raise RuntimeError("an oracle worker failed: " + next(e for (o, e), p in zip(outs, procs)
+                                                          if p.returncode != 0)[-2000:])
+    times = [json.loads(o.strip().splitlines()[-1])["times"][0] for o, _ in outs]
+    return n, times, wall
+
+
 def cpu_baseline(workload, sample=None):
-    """The FP64 oracle as it stands on this host's cores: one run of `sample`
-    c-LSQR iterations of the workload (the bounded sample), iterations/s."""
+    """The FP64 oracle as it stands on this host's cores: `sample` c-LSQR
+    iterations of the workload (the bounded sample) by one process alone, then
+    by one single-threaded process per core at once; iterations/s of the whole
+    host (the all-core figure is the value, the one-core figure beside it)."""
     sample = sample or CPU_SAMPLE.get(workload, 2)
     out = cpu_run(workload, sample, 1, 0.0)
-    t = out["times"][0]
-    return {"value": sample / t, "unit": "LSQR iterations/s", "cores": out["cores_used"],
+    t1 = out["times"][0]
+    n, times, wall = cpu_run_all_cores(workload, sample)
+    return {"value": n * sample / wall, "unit": "LSQR iterations/s", "cores": n,
             "cores_available": out["cores_available"], "kind": "oracle",
-            "sample": (f"one c-LSQR run of {sample} iterations from X_0 = 0 on the {workload} "
-                       f"workload, start-up product and norms included (FP64 NumPy oracle, "
-                       f"{t:.1f} s, {out['cpu']:.1f} s of CPU time on {out['cores_available']} "
-                       f"available cores)")}
+            "single_core": {"value": sample / t1, "cores": out["cores_used"], "seconds": t1},
+            "sample": (f"c-LSQR runs of {sample} iterations from X_0 = 0 on the {workload} "
+                       f"workload, start-up product and norms included (FP64 NumPy oracle): "
+                       f"{n} single-threaded runs at once, one a core, {wall:.1f} s for all "
+                       f"(slowest {max(times):.1f} s); one run alone {t1:.1f} s")}
 
 
 # ---------------------------------------------------------------- GPU arm ----
@@ -272,8 +297,9 @@ def precision_forms(dev, peaks, steps=3):
                                     "algorithmic_bytes": gbytes}}
         plan.close()
     out["bf16_dual"] = dual_route_form(A, C, Xt, s, iters, dev, peaks, steps)
+    out["bf16_store"] = stored_products_form(A, C, Xt, s, iters, dev, steps)
     base = out["fp32"]["rel_err_reg"]
-    for name in ("tf32", "bf16", "bf16x3", "bf16_dual"):
+    for name in ("tf32", "bf16", "bf16x3", "bf16_dual", "bf16_store"):
         out[name]["matched_error"] = bool(abs(out[name]["rel_err_reg"] - base) <= 0.02 * base)
         out[name]["speedup_vs_fp32"] = out[name]["iters_per_s"] / out["fp32"]["iters_per_s"]
     # Algorithm 1's dct reading (ORTHODCT): off the fused route LSQR runs in the
@@ -302,6 +328,33 @@ def precision_forms(dev, peaks, steps=3):
                                        <= 0.02 * od["fp32"]["rel_err_reg"])
     out["orthodct_transform_domain"] = od
     return out
+
+
+def stored_products_form(A, C, Xt, s, iters, dev, steps):
+    """The BF16 form with its slice products stored in BF16 (TC_STORE_BF16):
+    LSQR iterations/s and the reconstruction error (the headline's form)."""
+    import torch
+    from paper_2103_11847_gb300 import tcprod
+    st = torch.cuda.current_stream()
+    plan = tcprod.Plan(A, s=s, precision=tcprod.TC_BF16, store=tcprod.TC_STORE_BF16)
+    X = torch.empty(plan.xshape(), device=dev)
+    Xr = torch.empty(plan.xshape(), device=dev)
+    info = tcprod.new_info()
+    tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        tcprod.tc_lsqr_c(plan.handle, C, X, Xr, iters, 0.0, None, None, info)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    plan.close()
+    return {"iters_per_s": iters / (ms * 1e-3), "ms_per_solve": ms,
+            "rel_err_reg": float((Xr - Xt).norm() / Xt.norm()),
+            "rel_err_lsqr": float((X - Xt).norm() / Xt.norm()),
+            "store": "slice products rounded once to BF16 (TC_STORE_BF16), read back by the "
+                     "BF16-input transform pass"}
 
 
 def dual_route_form(A, C, Xt, s, iters, dev, peaks, steps):
@@ -640,6 +693,13 @@ def lsqr_floor_bytes(n1, n2, s, n3, precision, two_sided):
     return 2 * TA + 11 * T
 
 
+def effective_store(args, n3, two):
+    """--store bf16 where the plan takes it (BF16, one-sided, 32 < n3 <= 64),
+    else the FP32-stored products."""
+    ok = args.precision == "bf16" and not two and 32 < n3 <= 64
+    return "bf16" if (args.store == "bf16" and ok) else "f32"
+
+
 def dominant_kernel(plan, args, dims, dev):
     """The kernel that takes the largest share of the workload's solve, as a
     callable that launches it once on the current stream with the operands
@@ -656,6 +716,18 @@ def dominant_kernel(plan, args, dims, dev):
     from paper_2103_11847_gb300 import tcprod
     n1, n2, s, n3, two = dims
     prec = args.precision
+    if prec == "bf16" and n3 > 32 and getattr(args, "store", "f32") == "bf16" and not two:
+        # BF16-stored slice products: the pass back reads them in BF16 (T/2),
+        # reads prev and writes the output (T each), and reduces the norm
+        P = n1 * s
+        Yb = torch.randn((n3, n1, s), device=dev).to(torch.bfloat16)
+        prev = torch.randn((n3, n1, s), device=dev)
+        out = torch.empty((n3, n1, s), device=dev)
+        ss = torch.zeros(1, dtype=torch.float64, device=dev)
+        call = lambda: tcprod.tc_transform_bf16in(plan.handle, tcprod.TC_MINV, Yb, out, prev, ss)
+        return dict(kernel="k_tube_tma<OUT_F32, 2, INB> (tcgen05 mode-3 transform M^-1 from the "
+                           "BF16 slice products, Krylov epilogue and norm)", call=call, bound="hbm",
+                    work=(2.0 + 4.0 + 4.0) * n3 * P, traffic_key="k_tube_f32_bf16in", reps=50)
     if prec != "fp32" and n3 > 32:
         P = n1 * s
         Yh = torch.randn((n3, n1, s), device=dev)
@@ -774,7 +846,9 @@ def run_gpu(args):
     product = {"th": tcprod.TC_TH, "orthodct": tcprod.TC_ORTHODCT}[args.product]
     route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL,
              "dual": tcprod.TC_ROUTE_DUAL}[args.route]
-    plan = tcprod.Plan(A, B, s=s, precision=prec, product=product, route=route)
+    args.store = effective_store(args, n3, two)
+    store = {"f32": tcprod.TC_STORE_F32, "bf16": tcprod.TC_STORE_BF16}[args.store]
+    plan = tcprod.Plan(A, B, s=s, precision=prec, product=product, route=route, store=store)
     # observation C = M(X_true) + N with ||N|| = nu ||M(X_true)||, formed on the GPU
     Cc = plan.cprod(Xt)
     C = (Cc + (w["nu"] * Cc.norm() / G.norm()) * G).contiguous()
@@ -852,11 +926,13 @@ def run_gpu(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp32": "f32", "bf16x3": "f32-level: three BF16 planes an operand, six "
                       "products, f32 accumulate"}.get(args.precision,
-                                                       f"{args.precision} GEMM inputs, f32"),
+                                                       f"{args.precision} GEMM inputs, f32")
+            + (" (slice products stored in bf16)" if args.store == "bf16" else ""),
             "data": "synthetic (seeded video/image + Gaussian Toeplitz blurs + 1e-3 noise)",
             "config": {"workload": WORKLOAD_NAMES[args.workload].format(
                            iters=iters, n1=n1, n2=n2, n3=n3, s=s),
                        "precision": args.precision, "product": args.product,
+                       "store": args.store,
                        "l2": "flushed between timed steps (256 MB write)",
                        "parallelism": f"replicas x{world}"},
             "roofline": roofline_line(dk, dk_ms, peaks, src_peaks),
@@ -884,11 +960,12 @@ def run_gpu(args):
             if args.workload == "video_512":
                 pf = precision_forms(dev, peaks)
                 line["precision_forms"] = pf
-                if args.precision in pf:
+                form = "bf16_store" if args.store == "bf16" else args.precision
+                if form in pf:
                     line["matched_error"] = {
-                        "form": args.precision, "rel_err_reg": pf[args.precision]["rel_err_reg"],
+                        "form": form, "rel_err_reg": pf[form]["rel_err_reg"],
                         "fp32_rel_err_reg": pf["fp32"]["rel_err_reg"],
-                        "matched": pf[args.precision].get("matched_error", True),
+                        "matched": pf[form].get("matched_error", True),
                         "rule": "|e - e_fp32| <= 0.02 e_fp32 on X_reg vs the clean video",
                         "speedup_vs_fp32": value / pf["fp32"]["iters_per_s"]}
             line["two_sided_256"] = two_sided_form(dev, peaks, src_peaks)
@@ -1025,6 +1102,9 @@ def main():
     ap.add_argument("--precision", default=None, choices=["fp32", "tf32", "bf16", "bf16x3"],
                     help="slice-GEMM inputs of the main workload (default: bf16 for video_512, "
                          "fp32 otherwise)")
+    ap.add_argument("--store", default="bf16", choices=["f32", "bf16"],
+                    help="how the BF16 slice products reach the transform back (tc_store; "
+                    "bf16 applies to BF16 one-sided plans with 32 < n3 <= 64)")
     ap.add_argument("--route", default="auto", choices=["auto", "spatial", "dual"],
                     help="where c-LSQR keeps its vectors (tc_route)")
     ap.add_argument("--product", default="th", choices=["th", "orthodct"],
@@ -1082,7 +1162,9 @@ def kernel_only(args):
             "bf16x3": tcprod.TC_BF16X3}[args.precision]
     route = {"auto": tcprod.TC_ROUTE_AUTO, "spatial": tcprod.TC_ROUTE_SPATIAL,
              "dual": tcprod.TC_ROUTE_DUAL}[args.route]
-    plan = tcprod.Plan(A, B, s=s, precision=prec, route=route)
+    args.store = effective_store(args, n3, two)
+    store = {"f32": tcprod.TC_STORE_F32, "bf16": tcprod.TC_STORE_BF16}[args.store]
+    plan = tcprod.Plan(A, B, s=s, precision=prec, route=route, store=store)
     dk = dominant_kernel(plan, args, (n1, n2, s, n3, two), dev)
     for _ in range(8):
         dk["call"]()

@@ -96,13 +96,26 @@ typedef enum {
  *     fast on the 512 x 512 x 64 video, so AUTO keeps the spatial one. */
 typedef enum { TC_ROUTE_AUTO = 0, TC_ROUTE_SPATIAL = 1, TC_ROUTE_DUAL = 2 } tc_route;
 
+/* How the tensor-core slice products reach the transform back (Algorithm 1,
+ * step 3) on the spatial route:
+ *   TC_STORE_F32: in FP32, the accumulator as it is (default);
+ *   TC_STORE_BF16: rounded once to BF16 (the accumulation stays FP32), and
+ *     the pass back reads them by TMA straight into its tensor-core operand.
+ *     Each product then moves a quarter less: the GEMM writes and the pass
+ *     reads half the bytes. The error this adds (one BF16 rounding of each
+ *     transformed product, next to the operand's) keeps the regularised
+ *     reconstruction error within the precision form's 2% of FP32's.
+ *     TC_BF16 plans only, one-sided, 32 < n3 <= 64; TC_EUNSUPPORTED else. */
+typedef enum { TC_STORE_F32 = 0, TC_STORE_BF16 = 1 } tc_store;
+
 typedef struct {
   int precision;   /* tc_precision */
   int gcv_variant; /* tc_gcv_variant */
   int use_graphs;  /* nonzero: solves replay a captured CUDA graph */
   int product;     /* tc_product (default TC_TH) */
   int route;       /* tc_route (default TC_ROUTE_AUTO) */
-  int reserved[3]; /* must be zero */
+  int store;       /* tc_store (default TC_STORE_F32) */
+  int reserved[2]; /* must be zero */
 } tc_opts;
 
 /* Outcome of a solve, written to DEVICE memory by the solve (copy it back
@@ -345,6 +358,16 @@ int tc_slice_gemm_gk(tc_plan* plan, const void* Xh, float* Yh, int adjoint, cons
 typedef enum { TC_M = 0, TC_MINV = 1, TC_MINVT = 2, TC_MT = 3 } tc_transform_kind;
 int tc_transform(tc_plan* plan, int which, const float* in, float* out, size_t P,
                  const float* prev, double* sumsq, tc_stream_t stream);
+
+/* tc_transform from BF16 input, the pass back that plans with TC_STORE_BF16
+ * run (Algorithm 1's step 3 on BF16-stored slice products): out = in x_3 T
+ * (+ prev), sumsq as for tc_transform. in: device BF16, n3 slices of P
+ * values, 16-byte aligned, P a multiple of 8; out, prev: device FP32, same
+ * layout (prev may not alias out). TC_STORE_BF16 plans only, else
+ * TC_EUNSUPPORTED. One tcgen05 pass: the input lands by TMA straight in the
+ * tensor-core operand (one BF16 plane times the transform's two). */
+int tc_transform_bf16in(tc_plan* plan, int which, const void* in, float* out, size_t P,
+                        const float* prev, double* sumsq, tc_stream_t stream);
 
 /* The change of domain of the dual-domain c-LSQR route (tc_route): the
  * forward product's result lives in the M domain (U^ = U x_3 M) and the

@@ -158,6 +158,10 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
       TC_TRY(launch_mode3_lowp(X, p->tmp1, p->dM, n3, P, rkind(p) == ROUND_BF16, ep.skip, st));
     }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
+    if (p->store_bf16) {  // BF16 slice products, read back by the BF16-input pass
+      TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st, true));
+      return launch_mode3_tc_inb(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st, nullptr);
+    }
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
     if (p->two_sided) TC_TRY(right_factor(p, *p->umf2, (size_t)n1 * s * n3, err, ep.skip, st));
     return tct ? launch_mode3_tc(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st, x3(p))
@@ -311,6 +315,10 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
       TC_TRY(launch_mode3_lowp(Y, p->tmp1, p->dMinvT, n3, P, rkind(p) == ROUND_BF16, ep.skip,
                                st));
     }
+    if (p->store_bf16) {  // BF16 slice products, read back by the BF16-input pass
+      TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st, true));
+      return launch_mode3_tc_inb(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, after);
+    }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
     TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st));
     if (p->two_sided) TC_TRY(right_factor(p, *p->uma2, (size_t)n2 * s * n3, err, ep.skip, st));
@@ -407,6 +415,10 @@ int plan_build(tc_plan* p, const float* A, const float* B, cudaStream_t st) {
   p->tmp_elems = p->Tx > p->Ty ? p->Tx : p->Ty;
   TC_TRY(dalloc(&p->tmp1, p->tmp_elems));
   TC_TRY(dalloc(&p->tmp2, p->tmp_elems));
+  if (p->opts.store == TC_STORE_BF16) {
+    p->store_bf16 = tube_inb_ok(p->tmp2, n3, (size_t)(n1 > n2 ? n1 : n2) * s);
+    if (!p->store_bf16) return TC_EUNSUPPORTED;
+  }
   // partials: one per CTA of the largest reducing launch (vector passes are
   // capped at 152*32 CTAs, transform passes use P/128, fused GEMMs tiles).
   size_t np = 152 * 32 + 64;
@@ -527,6 +539,12 @@ extern "C" int tc_plan_create(tc_plan** out, int n1, int n2, int s, int n3, cons
     if (o.product != TC_TH && o.product != TC_ORTHODCT) return TC_EINVAL;
     if (o.route != TC_ROUTE_AUTO && o.route != TC_ROUTE_SPATIAL && o.route != TC_ROUTE_DUAL)
       return TC_EINVAL;
+    if (o.store != TC_STORE_F32 && o.store != TC_STORE_BF16) return TC_EINVAL;
+    // BF16-stored slice products: BF16 plans, one-sided, with the tensor-core
+    // passes (32 < n3 <= 64)
+    if (o.store == TC_STORE_BF16 &&
+        (o.precision != TC_BF16 || B || n3 <= TC_TUBE_MIN_N3 || n3 > 64))
+      return TC_EUNSUPPORTED;
   }
   if (o.precision != TC_FP32) {
     // tensor-core forms: every dimension a multiple of 8 (16-byte rows for
@@ -646,6 +664,25 @@ extern "C" int tc_transform_dual(tc_plan* p, int which, const float* in, void* o
   const bool u = which == TC_DUAL_U;
   return launch_mode3_tc_norm(in, out, u ? p->dG : p->dGi, u ? p->dMinv : p->dMT, p->n3, P, ep,
                               p->dev_err, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" int tc_transform_bf16in(tc_plan* p, int which, const void* in, float* out, size_t P,
+                                   const float* prev, double* sumsq, tc_stream_t stream) {
+  if (!p || !in || !out || (const void*)in == (const void*)out) return TC_EINVAL;
+  if (which < TC_M || which > TC_MT || P < 1 || P * (size_t)p->n3 > p->tmp_elems)
+    return TC_EINVAL;
+  if (prev && prev == out) return TC_EINVAL;
+  if (!p->store_bf16) return TC_EUNSUPPORTED;
+  const float* T = which == TC_M ? p->dM : which == TC_MINV ? p->dMinv
+                   : which == TC_MINVT ? p->dMinvT : p->dMT;
+  Epi ep;
+  if (prev) {
+    ep.coef.rule = COEF_ADD;
+    ep.prev = prev;
+  }
+  if (sumsq) ep.red = make_red(p, sumsq, 0, nullptr, nullptr);
+  return launch_mode3_tc_inb(in, out, T, p->n3, P, ep, p->dev_err, (cudaStream_t)stream,
+                             nullptr);
 }
 
 extern "C" int tc_plan_status(tc_plan* p, int* status) {

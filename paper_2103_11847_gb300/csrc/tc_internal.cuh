@@ -106,6 +106,7 @@ struct tc_plan {
   float *Bh = nullptr, *BhT = nullptr;
   float *dM = nullptr, *dMinv = nullptr, *dMinvT = nullptr, *dMT = nullptr;  // n3 x n3
   float *dG = nullptr, *dGi = nullptr;  // dual-domain route: M^{-T} M^{-1} and M M^T
+  bool store_bf16 = false;  // opts.store TC_STORE_BF16: slice products stored in BF16 (tmp2)
   float hM[TC_MAX_FUSED * TC_MAX_FUSED], hMinv[TC_MAX_FUSED * TC_MAX_FUSED];
   float hMinvT[TC_MAX_FUSED * TC_MAX_FUSED], hMT[TC_MAX_FUSED * TC_MAX_FUSED];
   float *tmp1 = nullptr, *tmp2 = nullptr;  // transform-domain intermediates
@@ -220,6 +221,15 @@ int launch_mode3_tc_norm(const float* in, void* out, const float* T_dev, const f
                          const LsqrStep* after);
 int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3, size_t P,
                          int kind, const int* skip, int* err, cudaStream_t st);
+// The pass back from BF16 slice products (plans with opts.store TC_STORE_BF16):
+// out = in x_3 T with the Krylov epilogue (ep: coef, prev, red) as
+// launch_mode3_tc, `in` BF16 loaded by TMA straight into the MMA operand.
+// TC_EUNSUPPORTED for shapes tube_inb_ok rejects. after: as launch_mode3_tc.
+int launch_mode3_tc_inb(const void* in, float* out, const float* T_dev, int n3, size_t P,
+                        const Epi& ep, int* err, cudaStream_t st, const LsqrStep* after);
+// Whether launch_mode3_tc_inb takes n3 slices of P values at buf (a device
+// buffer of the plan, 16-byte aligned).
+bool tube_inb_ok(const void* buf, int n3, size_t P);
 // Elementwise rounding of n FP32 values to the operand type `kind` (RoundKind).
 int transform_init();  // shared-memory limits of the transform passes
 int launch_round(const float* in, void* out, size_t n, int kind, cudaStream_t st,

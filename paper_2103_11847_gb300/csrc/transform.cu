@@ -551,28 +551,36 @@ k_tube(const float* __restrict__ in, void* out_v, const float* __restrict__ T, i
 // iteration (transform-domain LSQR under the TH product) uses it to form the
 // next GEMM operand, bf16(in x_3 G), and the Frobenius norm of the spatial
 // tensor, ||in x_3 N||_F, in one pass over `in`.
+// INB (FP32 output, two B planes): the input is BF16 and lands by TMA (128-byte
+// swizzle, two boxes of 64 pixels x 64 slices) directly in the A operand's
+// layout, one plane, so no converter stage runs; two MMA passes (B hi, lo).
 constexpr int TT_NT = 608;
 constexpr uint32_t TT_SLOT = TK * TP * 4;  // one FP32 box of 64 x 128: 32 KB
 // Slots: two planes (A in the input slot) 3 input + 3 output, or 4 + 4
 // half-size output slots for a BF16 output (16 KB a tile); three planes (a
 // separate A buffer, larger B) 2 + 2.
-constexpr int tube_tma_in(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
+constexpr int tube_tma_in(int ns, int out, bool inb = false) {
+  return inb ? 6 : (ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3));
+}
 constexpr int tube_tma_out(int ns, int out) { return ns == 3 ? 2 : (out == OUT_BF16 ? 4 : 3); }
 constexpr uint32_t tube_tma_oslot(int out) { return out == OUT_BF16 ? TT_SLOT / 2 : TT_SLOT; }
-constexpr size_t tube_tma_smem(int ns, int out, bool nrm = false) {
-  return 1024 + tube_tma_in(ns, out) * TT_SLOT + tube_tma_out(ns, out) * tube_tma_oslot(out) +
-         (ns == 3 ? ns * TA_BYTES : 0) + (nrm ? 2 : 1) * ns * TB_BYTES +
-         (3 * tube_tma_in(ns, out) + 3 * tube_tma_out(ns, out) + 7) * 8 + 16;
+constexpr size_t tube_tma_smem(int ns, int out, bool nrm = false, bool inb = false) {
+  return 1024 + tube_tma_in(ns, out, inb) * (inb ? TA_BYTES : TT_SLOT) +
+         tube_tma_out(ns, out) * tube_tma_oslot(out) + (ns == 3 ? ns * TA_BYTES : 0) +
+         (nrm ? 2 : 1) * ns * TB_BYTES + (3 * tube_tma_in(ns, out, inb) + 3 * tube_tma_out(ns, out) + 7) * 8 +
+         16;
 }
 
-template <int OUT, int NS, bool NRM = false>
+template <int OUT, int NS, bool NRM = false, bool INB = false>
 __global__ void __launch_bounds__(TT_NT, 1)
 k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
            const __grid_constant__ CUtensorMap tmOut, const float* __restrict__ T,
            const float* __restrict__ N, int n3, size_t P, int has_prev, Epi ep, int* err,
            LsqrStep after) {
-  constexpr int NPASS = NS == 2 ? 3 : 6;
-  constexpr int NI = tube_tma_in(NS, OUT), NO = tube_tma_out(NS, OUT);
+  static_assert(!INB || (OUT == OUT_F32 && NS == 2 && !NRM), "BF16 input: the pass back");
+  constexpr int NPASS = INB ? 2 : (NS == 2 ? 3 : 6);  // INB: A (one plane) x B hi, lo
+  constexpr int NI = tube_tma_in(NS, OUT, INB), NO = tube_tma_out(NS, OUT);
+  constexpr uint32_t ISLOT = INB ? TA_BYTES : TT_SLOT;  // one input slot
   constexpr uint32_t OSLOT = tube_tma_oslot(OUT);
   constexpr bool INPLACE = NS == 2;  // A planes over the input slot
   constexpr bool RED = OUT == OUT_F32 || NRM;  // the pass reduces into ep.red
@@ -592,7 +600,7 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   uint8_t* base = reinterpret_cast<uint8_t*>(
       (reinterpret_cast<uintptr_t>(tt_raw) + 1023) & ~(uintptr_t)1023);
   uint8_t* sin = base;                    // NI input slots
-  uint8_t* sout = base + NI * TT_SLOT;    // NO prev / output slots
+  uint8_t* sout = base + NI * ISLOT;      // NO prev / output slots
   uint8_t* sAx = sout + NO * OSLOT;       // three planes: the A buffer
   uint8_t* sB = sAx + (INPLACE ? 0 : NS * TA_BYTES);  // NS B planes (NRM: then N's NS planes)
   uint64_t* ifull = reinterpret_cast<uint64_t*>(sB + (NRM ? 2 : 1) * NS * TB_BYTES);  // [NI] input loaded
@@ -620,7 +628,7 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
   if (tid == 0) {
     for (int b = 0; b < NI; ++b) {
       mbar_init(ifull + b, 1);
-      mbar_init(iempty + b, INPLACE ? 1 : 8);
+      mbar_init(iempty + b, (INPLACE || INB) ? 1 : 8);
       mbar_init(afull + b, 8);
     }
     for (int b = 0; b < NO; ++b) {
@@ -684,8 +692,14 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
           *vfail = 1;
           break;
         }
-        mbar_expect_tx(ifull + s, box);
-        tma_load_2d(sin + s * TT_SLOT, &tmIn, t * TP, 0, ifull + s);
+        if (INB) {  // two 64-pixel halves of the BF16 A operand, 128-byte swizzle
+          mbar_expect_tx(ifull + s, TA_BYTES);
+          tma_load_3d(sin + s * ISLOT, &tmIn, t * TP, 0, 0, ifull + s);
+          tma_load_3d(sin + s * ISLOT + TA_BYTES / 2, &tmIn, t * TP + TP / 2, 0, 0, ifull + s);
+        } else {
+          mbar_expect_tx(ifull + s, box);
+          tma_load_2d(sin + s * TT_SLOT, &tmIn, t * TP, 0, ifull + s);
+        }
         issued = i + 1;
       }
     }
@@ -714,14 +728,14 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
       for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
         const int d = i & 1;
         const uint32_t u = (uint32_t)(i >> 1) & 1u;
-        if (!mbar_wait(afull + i % NI, (uint32_t)(i / NI) & 1u) ||
+        if (!mbar_wait((INB ? ifull : afull) + i % NI, (uint32_t)(i / NI) & 1u) ||
             !mbar_wait(dempty + d, u ^ 1u)) {
           *vfail = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t acc = tmem + (uint32_t)(d * TK);
-        uint8_t* sA = INPLACE ? sin + (i % NI) * TT_SLOT : sAx;
+        uint8_t* sA = INPLACE ? sin + (i % NI) * ISLOT : sAx;
 #pragma unroll
         for (int m = 0; m < (NRM ? 2 : 1); ++m) {  // m = 1: N into the second pair
 #pragma unroll
@@ -740,10 +754,10 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
       }
       umma_commit(fin);
     }
-  } else if (warp < 11) {  // converters
+  } else if (warp < 11) {  // converters (none with INB: the input is the A operand)
     const int ct = tid - 96;
     int i = 0;
-    for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+    for (int t = blockIdx.x; t < ntile && !INB; t += gridDim.x, ++i) {
       if (__any_sync(0xffffffffu, *vfail)) break;
       const int s = i % NI;
       const uint32_t u = (uint32_t)(i / NI) & 1u;
@@ -987,6 +1001,39 @@ int launch_mode3_tc(const float* in, float* out, const float* T_dev, int n3, siz
   return TC_OK;
 }
 
+int launch_mode3_tc_inb(const void* in, float* out, const float* T_dev, int n3, size_t P,
+                        const Epi& ep, int* err, cudaStream_t st, const LsqrStep* after) {
+  TC_CHECK(n3 > 0 && n3 <= TK);
+  TC_CHECK(!after || (after->alpha && !after->X && ep.red.out));
+  auto al = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  if (P % 8 || P / TP >= (1u << 30) || !al(in) || !al(out) || !al(ep.prev) || ep.red.other)
+    return TC_EUNSUPPORTED;
+  CUtensorMap mi, mp, mo;
+  // BF16 input as a 3-D map (P, n3, 1), box 64 pixels x 64 slices, 128-byte
+  // swizzle: the A operand's layout; slices >= n3 read as zero
+  TC_TRY(make_tmap(&mi, in, 1, (int)P, n3, 1, TP / 2, TK));
+  const int hp = ep.prev ? 1 : 0;
+  if (hp)
+    TC_TRY(make_tmap_2d(&mp, ep.prev, 0, P, (size_t)n3, TP, n3));
+  TC_TRY(make_tmap_2d(&mo, out, 0, P, (size_t)n3, TP, n3));
+  if (!hp) mp = mo;
+  const size_t ntile = (P + TP - 1) / TP;
+  const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
+  k_tube_tma<OUT_F32, 2, false, true><<<grid, TT_NT, tube_tma_smem(2, OUT_F32, false, true), st>>>(
+      mi, mp, mo, T_dev, nullptr, n3, P, hp, ep, err, after ? *after : LsqrStep{});
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
+// Whether the BF16-input pass takes this plan's shapes: the encoder accepts
+// the input map (box of 64 slices over n3 of them).
+bool tube_inb_ok(const void* buf, int n3, size_t P) {
+  if (n3 <= TC_TUBE_MIN_N3 || n3 > TK || P % 8 || P / TP >= (1u << 30)) return false;
+  if (reinterpret_cast<uintptr_t>(buf) & 15) return false;
+  CUtensorMap m;
+  return make_tmap(&m, buf, 1, (int)P, n3, 1, TP / 2, TK) == TC_OK;
+}
+
 int launch_mode3_tc_norm(const float* in, void* out, const float* T_dev, const float* N_dev,
                          int n3, size_t P, const Epi& ep, int* err, cudaStream_t st,
                          const LsqrStep* after) {
@@ -1035,6 +1082,9 @@ int transform_init() {
                                (int)tube_tma_smem(2, OUT_TF32)));
   TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tube_tma_smem(3, OUT_F32)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 2, false, true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_tma_smem(2, OUT_F32, false, true)));
   TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_BF16, 2, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tube_tma_smem(2, OUT_BF16, true)));

@@ -73,7 +73,9 @@ size_t smem_bytes(int npair = 1) {
 __device__ __forceinline__ int pair_a(int p) { return p == 2 || p == 4 ? 1 : (p == 5 ? 2 : 0); }
 __device__ __forceinline__ int pair_b(int p) { return p == 1 || p == 4 ? 1 : (p == 3 ? 2 : 0); }
 
-template <int KIND, int BKMAJ, bool EPI, int NPAIR = 1>
+// OUTB (plain store, BF16 inputs): D holds BF16 values (one rounding of the
+// FP32 accumulator), for a consumer that reads BF16.
+template <int KIND, int BKMAJ, bool EPI, int NPAIR = 1, bool OUTB = false>
 __global__ void __launch_bounds__(NT, NPAIR == 6 ? 1 : 2)
 k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
             float* D, int M, int N, int K, int Z, int* err, const int* skip, Epi ep,
@@ -88,6 +90,7 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
   constexpr uint32_t BMAJ = BKMAJ ? 0u : 1u;
   constexpr uint32_t IDESC = (1u << 4) | (FMT << 7) | (FMT << 10) | (0u << 15) | (BMAJ << 16) |
                              ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+  static_assert(!OUTB || (!EPI && KIND == 0), "BF16 store: the plain BF16 GEMM");
   constexpr int PL = stage_planes(NPAIR), NST = stage_count(NPAIR);
   constexpr uint32_t SA = PL * A_BYTES, SB = PL * B_BYTES;  // one stage's A, B bytes
   if (skip && *skip) return;
@@ -312,7 +315,16 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 local = fmaf(y.x, ov.x, fmaf(y.y, ov.y, fmaf(y.z, ov.z, fmaf(y.w, ov.w, local))));
               }
             }
-            *reinterpret_cast<float4*>(D + o) = y;
+            if (OUTB) {
+              const __nv_bfloat162 lo = __floats2bfloat162_rn(y.x, y.y);
+              const __nv_bfloat162 hi = __floats2bfloat162_rn(y.z, y.w);
+              uint2 pk;
+              pk.x = *reinterpret_cast<const uint32_t*>(&lo);
+              pk.y = *reinterpret_cast<const uint32_t*>(&hi);
+              *reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(D) + o) = pk;
+            } else {
+              *reinterpret_cast<float4*>(D + o) = y;
+            }
             if (EPI && dlow) {  // PL planes of the next operand, Z M N values apart
               float4 r = y;
 #pragma unroll
@@ -338,7 +350,10 @@ k_umma_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUt
                 if (ep.prev) w = fmaf(cp, ep.prev[o + e], w);
                 if (ep.red.out) local = fmaf(w, ep.red.other ? ep.red.other[o + e] : w, local);
               }
-              D[o + e] = w;
+              if (OUTB)
+                reinterpret_cast<__nv_bfloat16*>(D)[o + e] = __float2bfloat16_rn(w);
+              else
+                D[o + e] = w;
               if (EPI && dlow) {
                 float r = w;
 #pragma unroll
@@ -409,7 +424,8 @@ extern "C" int tc_check_bounded_wait(int spins, int* status, tc_stream_t stream)
 
 int umma_init() {
   for (auto fn : {k_umma_gemm<0, 0, false>, k_umma_gemm<1, 1, false>, k_umma_gemm<0, 0, true>,
-                  k_umma_gemm<0, 0, false, 6>, k_umma_gemm<0, 0, true, 6>}) {
+                  k_umma_gemm<0, 0, false, 6>, k_umma_gemm<0, 0, true, 6>,
+                  k_umma_gemm<0, 0, false, 1, true>}) {
     const int npair =
         (fn == k_umma_gemm<0, 0, false, 6> || fn == k_umma_gemm<0, 0, true, 6>) ? 6 : 1;
     TC_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -498,9 +514,14 @@ unsigned grid_size(const UmmaMaps& m) {
 }
 }  // namespace
 
-int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st) {
+int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st,
+                bool out_bf16) {
   Epi none;
-  if (m.nsplit == 3)
+  TC_CHECK(!out_bf16 || (m.kind == 0 && m.nsplit == 1));
+  if (out_bf16)
+    k_umma_gemm<0, 0, false, 1, true><<<grid_size(m), NT, smem_bytes(), st>>>(
+        m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
+  else if (m.nsplit == 3)
     k_umma_gemm<0, 0, false, 6><<<grid_size(m), NT, smem_bytes(6), st>>>(
         m.a, m.b, D, m.M, m.N, m.K, m.slices, err, skip, none, nullptr);
   else if (m.kind == 0)

@@ -20,13 +20,21 @@ int make_umma_maps(UmmaMaps* m, int kind, const void* A, const void* B, int M, i
                    int slices, int nsplit = 1);
 // D_z = A_z B_z in FP32 for every slice (nsplit 3: the six split products);
 // *err is set to TC_ETIMEOUT if a bounded wait gives up.
-int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st);
+// out_bf16 (BF16 maps, one plane): D receives BF16 values, bf16(A_z B_z).
+int launch_umma(const UmmaMaps& m, float* D, int* err, const int* skip, cudaStream_t st,
+                bool out_bf16 = false);
 // BF16 maps only: the same GEMM with the Krylov epilogue in its store
 // (D = ca * acc + cp * ep.prev, the reduction ep.red of D, ep.skip) and, when
 // dlow is non-null, a BF16 copy of D written beside it (nsplit 3: its three
 // planes, plane q at dlow + q slices M N).
 int launch_umma_epi(const UmmaMaps& m, float* D, __nv_bfloat16* dlow, const Epi& ep, int* err,
                     cudaStream_t st);
+// 3-D tiled map over `slices` row-major rows x inner matrices (FP32, or BF16
+// with bf16 = 1), box (box_inner, box_rows, 1), 128-byte swizzle, zero fill
+// out of bounds. The base must be 16-byte aligned and a row a multiple of 16
+// bytes.
+int make_tmap(CUtensorMap* map, const void* base, int bf16, int inner, int rows, int slices,
+              int box_inner, int box_rows);
 // 2-D tiled map over a rows x inner row-major tensor (FP32, or BF16 with
 // bf16 = 1), box (box_inner, box_rows), no swizzle, zero fill out of bounds.
 // The base must be 16-byte aligned and a row a multiple of 16 bytes.

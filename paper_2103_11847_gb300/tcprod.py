@@ -21,13 +21,15 @@ TC_TH, TC_ORTHODCT = 0, 1
 TC_M, TC_MINV, TC_MINVT, TC_MT = 0, 1, 2, 3
 TC_ROUTE_AUTO, TC_ROUTE_SPATIAL, TC_ROUTE_DUAL = 0, 1, 2
 TC_DUAL_U, TC_DUAL_V = 0, 1
+TC_STORE_F32, TC_STORE_BF16 = 0, 1
 STATUS_NAMES = {0: "maxiter", 1: "converged", TC_EBREAKDOWN: "breakdown",
                 TC_ENONFINITE: "nonfinite"}
 
 
 class tc_opts(ctypes.Structure):
     _fields_ = [("precision", c_int), ("gcv_variant", c_int), ("use_graphs", c_int),
-                ("product", c_int), ("route", c_int), ("reserved", c_int * 3)]
+                ("product", c_int), ("route", c_int), ("store", c_int),
+                ("reserved", c_int * 2)]
 
 
 class tc_solve_info(ctypes.Structure):
@@ -61,6 +63,8 @@ _SIGS = {
     "tc_slice_gemm": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p], c_int),
     "tc_transform": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p, c_void_p,
                       c_void_p], c_int),
+    "tc_transform_bf16in": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p,
+                             c_void_p, c_void_p], c_int),
     "tc_slice_gemm_gk": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int),
     "tc_transform_dual": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p,
@@ -146,7 +150,8 @@ def tc_version():
 
 
 def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                   use_graphs=True, stream=None, product=TC_TH, route=TC_ROUTE_AUTO):
+                   use_graphs=True, stream=None, product=TC_TH, route=TC_ROUTE_AUTO,
+                   store=TC_STORE_F32):
     """A: (n3, n1, n2); B: (n3, s, s) or None (then s must be given)."""
     n3, n1, n2 = A.shape
     if B is not None:
@@ -154,7 +159,7 @@ def tc_plan_create(A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPE
         _ptr(B, shape=(n3, s, s), name="B")
     if s is None:
         raise ValueError("s (columns of X) is required for a one-sided plan")
-    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)), product, route)
+    o = tc_opts(precision, gcv_variant, int(bool(use_graphs)), product, route, store)
     h = c_void_p()
     _check("tc_plan_create", lib().tc_plan_create(ctypes.byref(h), n1, n2, s, n3, _ptr(A, name="A"),
                                                   _ptr(B, name="B"), ctypes.byref(o),
@@ -242,6 +247,16 @@ def tc_transform(h, which, X, Y, prev=None, sumsq=None, stream=None):
                                               P, _ptr(prev, name="prev"),
                                               _ptr(sumsq, torch.float64, name="sumsq"),
                                               _stream(stream)))
+
+
+def tc_transform_bf16in(h, which, X, Y, prev=None, sumsq=None, stream=None):
+    """Y = X x_3 T (+ prev) from BF16 X (plans with TC_STORE_BF16); Y FP32."""
+    P = X[0].numel()
+    if Y.shape != X.shape or (prev is not None and prev.shape != X.shape):
+        raise ValueError("X, Y (and prev) must have the same shape")
+    _check("tc_transform_bf16in", lib().tc_transform_bf16in(
+        h, int(which), _ptr(X, torch.bfloat16, name="X"), _ptr(Y, name="Y"), P,
+        _ptr(prev, name="prev"), _ptr(sumsq, torch.float64, name="sumsq"), _stream(stream)))
 
 
 def tc_slice_gemm_gk(h, Xh, Yh, s0, s1=None, prev=None, sumsq=None, adjoint=False,
@@ -441,12 +456,12 @@ class Plan:
     """Owns a tc_plan for A (and B); methods allocate outputs as torch tensors."""
 
     def __init__(self, A, B=None, s=None, precision=TC_FP32, gcv_variant=TC_GCV_PAPER,
-                 use_graphs=True, product=TC_TH, route=TC_ROUTE_AUTO):
+                 use_graphs=True, product=TC_TH, route=TC_ROUTE_AUTO, store=TC_STORE_F32):
         self.n3, self.n1, self.n2 = A.shape
         self.s = B.shape[1] if B is not None else s
         self.two_sided = B is not None
         self.handle = tc_plan_create(A, B, s, precision, gcv_variant, use_graphs,
-                                     product=product, route=route)
+                                     product=product, route=route, store=store)
 
     def close(self):
         if self.handle is not None:

@@ -265,3 +265,51 @@ def test_slice_scales_pass_through_exactly(tc, name):
         pf.close()
     plan.close()
 
+
+
+@pytest.mark.parametrize("n1,n2,s,n3", [(128, 256, 200, 64), (72, 40, 56, 37), (24, 40, 24, 33),
+                                        (136, 96, 40, 64)])
+def test_bf16_stored_products(tc, n1, n2, s, n3):
+    # TC_STORE_BF16: the slice products rounded once to BF16 and read back by
+    # the BF16-input pass; the product and adjoint within the BF16 bound.
+    p = inputs.random_problem(n1, n2, s, n3, seed=n1 + 3 * s)
+    A, X, Y = f32(p["A"]), f32(p["X"]), f32(p["Y"])
+    plan = tc.Plan(dev(A), s=s, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    Yg = plan.cprod(dev(X)).cpu().numpy()
+    Xg = plan.adjoint(dev(Y)).cpu().numpy()
+    e1 = rel(Yg, cp.cprod(A.astype(np.float64), X.astype(np.float64)))
+    e2 = rel(Xg, cp.cprod_adjoint(A.astype(np.float64), Y.astype(np.float64)))
+    print(n1, n2, s, n3, e1, e2)
+    assert e1 < TOL["bf16"] and e2 < TOL["bf16"]
+    assert tc.tc_plan_status(plan.handle) == tc.TC_OK
+    plan.close()
+
+
+def test_bf16_stored_products_reconstruction(tc, video_oracle_reg):
+    # The 128x128x64 video, 20 c-LSQR iterations + GCV: the BF16-stored form
+    # within the precision form's 2% of the FP64 oracle's reconstruction error.
+    A, C, Xt, e_ref = video_oracle_reg
+    plan = tc.Plan(dev(A), s=128, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    X, Xr, _, info = plan.lsqr(dev(C), 20, regularize=True)
+    torch.cuda.synchronize()
+    inf = tc.read_info(info)
+    assert inf["iters"] == 20 and inf["status"] == "maxiter", inf
+    e = rel(Xr.cpu().numpy(), Xt)
+    print("bf16 stored", e, e_ref)
+    assert abs(e - e_ref) < 0.02 * e_ref
+    plan.close()
+
+
+def test_bf16_stored_products_rejected_elsewhere(tc):
+    rng = np.random.default_rng(5)
+    for kw, shape in [(dict(precision=tc.TC_FP32), (64, 64, 64)),
+                      (dict(precision=tc.TC_TF32), (64, 64, 64)),
+                      (dict(precision=tc.TC_BF16X3), (64, 64, 64)),
+                      (dict(precision=tc.TC_BF16), (16, 64, 64))]:
+        with pytest.raises(tc.TcError) as e:
+            tc.Plan(dev(rng.standard_normal(shape)), s=64, store=tc.TC_STORE_BF16, **kw)
+        assert e.value.code == tc.TC_EUNSUPPORTED
+    Ad = dev(rng.standard_normal((64, 64, 64)))
+    with pytest.raises(tc.TcError) as e:
+        tc.Plan(Ad, B=Ad, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    assert e.value.code == tc.TC_EUNSUPPORTED

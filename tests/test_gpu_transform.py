@@ -167,3 +167,30 @@ def test_graph_kernel_count_grows_by_a_fixed_count_per_iteration(tc):
     assert counts[0] > 0
     assert counts[1] - counts[0] == counts[2] - counts[1] > 0
     plan.close()
+
+
+@pytest.mark.parametrize("n3,P", [(64, 8192), (64, 1000), (37, 2056)])
+def test_transform_from_bf16_input(tc, n3, P):
+    # tc_transform_bf16in (TC_STORE_BF16 plans): out = in x_3 T + prev from a
+    # BF16 input, against the FP64 transform of the same BF16 values; the
+    # transform's two BF16 planes bound the error near 2^-16 a term.
+    rng = np.random.default_rng(7 * n3 + P)
+    A = torch.from_numpy(rng.standard_normal((n3, 64, 64)).astype(np.float32)).cuda()
+    plan = tc.Plan(A, s=128, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    M = cp.transform_matrix(n3)
+    Mi = np.linalg.inv(M)
+    Xb = torch.from_numpy(rng.standard_normal((n3, P)).astype(np.float32)).cuda().to(torch.bfloat16)
+    Xd = Xb.float().cpu().numpy().astype(np.float64)
+    prev = torch.from_numpy(rng.standard_normal((n3, P)).astype(np.float32)).cuda()
+    for which, T in [(tc.TC_M, M), (tc.TC_MINV, Mi), (tc.TC_MINVT, Mi.T), (tc.TC_MT, M.T)]:
+        Y = torch.empty((n3, P), device="cuda")
+        ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tc.tc_transform_bf16in(plan.handle, which, Xb, Y, prev, ss)
+        torch.cuda.synchronize()
+        ref = T @ Xd + prev.cpu().numpy().astype(np.float64)
+        e = np.linalg.norm(Y.cpu().numpy() - ref) / np.linalg.norm(ref)
+        es = abs(float(ss.item()) - float(np.sum(ref ** 2))) / float(np.sum(ref ** 2))
+        print(n3, P, which, e, es)
+        assert e < 1e-4 and es < 1e-4
+    assert tc.tc_plan_status(plan.handle) == tc.TC_OK
+    plan.close()
