@@ -717,17 +717,21 @@ def dominant_kernel(plan, args, dims, dev):
     n1, n2, s, n3, two = dims
     prec = args.precision
     if prec == "bf16" and n3 > 32 and getattr(args, "store", "f32") == "bf16" and not two:
-        # BF16-stored slice products: the pass back reads them in BF16 (T/2),
-        # reads prev and writes the output (T each), and reduces the norm
+        # BF16-stored slice products, chained passes: the pass back reads
+        # them in BF16 (T/2), reads prev and writes the output (T each),
+        # reduces the norm, and writes the next product's BF16 operand (T/2)
         P = n1 * s
         Yb = torch.randn((n3, n1, s), device=dev).to(torch.bfloat16)
         prev = torch.randn((n3, n1, s), device=dev)
         out = torch.empty((n3, n1, s), device=dev)
+        nxt = torch.empty((n3, n1, s), dtype=torch.bfloat16, device=dev)
         ss = torch.zeros(1, dtype=torch.float64, device=dev)
-        call = lambda: tcprod.tc_transform_bf16in(plan.handle, tcprod.TC_MINV, Yb, out, prev, ss)
-        return dict(kernel="k_tube_tma<OUT_F32, 2, INB> (tcgen05 mode-3 transform M^-1 from the "
-                           "BF16 slice products, Krylov epilogue and norm)", call=call, bound="hbm",
-                    work=(2.0 + 4.0 + 4.0) * n3 * P, traffic_key="k_tube_f32_bf16in", reps=50)
+        call = lambda: tcprod.tc_transform_bf16in(plan.handle, tcprod.TC_MINV, Yb, out, prev, ss,
+                                                  which_next=tcprod.TC_MINVT, nxt=nxt)
+        return dict(kernel="k_tube_chain (tcgen05 mode-3 transform M^-1 from the BF16 slice "
+                           "products, Krylov epilogue and norm, and the next product's operand "
+                           "x_3 M^-T in BF16)", call=call, bound="hbm",
+                    work=(2.0 + 4.0 + 4.0 + 2.0) * n3 * P, traffic_key="k_tube_chain", reps=50)
     if prec != "fp32" and n3 > 32:
         P = n1 * s
         Yh = torch.randn((n3, n1, s), device=dev)

@@ -363,11 +363,18 @@ int tc_transform(tc_plan* plan, int which, const float* in, float* out, size_t P
  * run (Algorithm 1's step 3 on BF16-stored slice products): out = in x_3 T
  * (+ prev), sumsq as for tc_transform. in: device BF16, n3 slices of P
  * values, 16-byte aligned, P a multiple of 8; out, prev: device FP32, same
- * layout (prev may not alias out). TC_STORE_BF16 plans only, else
- * TC_EUNSUPPORTED. One tcgen05 pass: the input lands by TMA straight in the
- * tensor-core operand (one BF16 plane times the transform's two). */
+ * layout (prev may not alias out). One tcgen05 pass: the input lands by TMA
+ * straight in the tensor-core operand (one BF16 plane times the transform's
+ * two).
+ * nxt (device BF16, same layout, or NULL): the same pass also writes
+ * nxt = bf16(out x_3 T_next), T_next chosen by which_next (TC_M .. TC_MT),
+ * from out's FP32 values split into two BF16 planes, as tc_transform's BF16
+ * form would from out. This is the first step of the product that follows
+ * (c-LSQR chains its products this way). nxt may not alias in, out or prev.
+ * TC_STORE_BF16 plans only, else TC_EUNSUPPORTED. */
 int tc_transform_bf16in(tc_plan* plan, int which, const void* in, float* out, size_t P,
-                        const float* prev, double* sumsq, tc_stream_t stream);
+                        const float* prev, double* sumsq, int which_next, void* nxt,
+                        tc_stream_t stream);
 
 /* The change of domain of the dual-domain c-LSQR route (tc_route): the
  * forward product's result lives in the M domain (U^ = U x_3 M) and the

@@ -131,7 +131,9 @@ int right_factor(tc_plan* p, const UmmaMaps& m, size_t n, int* err, const int* s
 
 // Y = A *c X [*c B] with the epilogue `ep` on the last stage.
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
-              const LsqrStep* step) {
+              const LsqrStep* step, const Chain* ch) {
+  const bool ready = ch && ch->in_ready && p->store_bf16;
+  const float* next_T = (ch && p->store_bf16) ? ch->next_T : nullptr;
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
   if (fused(p) && p->two_sided && cprod2_fits(s))  // the step runs inside the product
     return launch_cprod2(p->AhT, X, p->Bh, Y, n1, n2, s, n3, p->hM, p->hMinv, ep,
@@ -149,7 +151,8 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     int* err = ep.red.status ? ep.red.status : p->dev_err;
     const bool tct = n3 > TC_TUBE_MIN_N3;
     const size_t P = (size_t)n2 * s;
-    if (tct) {
+    if (ready) {  // the pass back of the product before wrote bf16(X x_3 M)
+    } else if (tct) {
       TC_TRY(launch_mode3_tc_lowp(X, lowop(p), p->dM, n3, P, rkind(p), ep.skip, err, st));
     } else if (x3(p)) {  // the exact FP32 pass, then the three planes
       TC_TRY(launch_mode3(X, p->tmp2, p->dM, n3, P, mid, st));
@@ -160,6 +163,9 @@ int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t 
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n2, s, n3, st, ep.skip));
     if (p->store_bf16) {  // BF16 slice products, read back by the BF16-input pass
       TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st, true));
+      if (next_T)
+        return launch_mode3_tc_chain(p->tmp2, Y, p->dMinv, lowop(p), next_T, n3, (size_t)n1 * s,
+                                     ep, err, st, nullptr);
       return launch_mode3_tc_inb(p->tmp2, Y, p->dMinv, n3, (size_t)n1 * s, ep, err, st, nullptr);
     }
     TC_TRY(launch_umma(*p->umf, p->tmp2, err, ep.skip, st));
@@ -285,11 +291,13 @@ int adjoint_td(tc_plan* p, const float* Yt, float* Xt, const Epi& ep, cudaStream
 
 // X = M^T [ A~_k^T (M^{-T} Y)_k (B~_k^T) ] with the epilogue `ep` on the last stage.
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st,
-                const LsqrStep* after) {
+                const LsqrStep* after, const Chain* ch) {
   if (after && !(lowp(p) && p->n3 > TC_TUBE_MIN_N3)) {  // the step's own launch after the product
-    TC_TRY(adjoint_epi(p, Y, X, ep, st, nullptr));
+    TC_TRY(adjoint_epi(p, Y, X, ep, st, nullptr, ch));
     return launch_lsqr_scalars(*after, st);
   }
+  const bool ready = ch && ch->in_ready && p->store_bf16;
+  const float* next_T = (ch && p->store_bf16) ? ch->next_T : nullptr;
   const int n1 = p->n1, n2 = p->n2, s = p->s, n3 = p->n3;
   Epi mid;
   mid.skip = ep.skip;
@@ -306,7 +314,8 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     int* err = ep.red.status ? ep.red.status : p->dev_err;
     const bool tct = n3 > TC_TUBE_MIN_N3;
     const size_t P = (size_t)n1 * s;
-    if (tct) {
+    if (ready) {  // the pass back of the product before wrote bf16(Y x_3 M^{-T})
+    } else if (tct) {
       TC_TRY(launch_mode3_tc_lowp(Y, lowop(p), p->dMinvT, n3, P, rkind(p), ep.skip, err, st));
     } else if (x3(p)) {
       TC_TRY(launch_mode3(Y, p->tmp2, p->dMinvT, n3, P, mid, st));
@@ -317,6 +326,9 @@ int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_
     }
     if (p->store_bf16) {  // BF16 slice products, read back by the BF16-input pass
       TC_TRY(launch_umma(*p->uma, p->tmp2, err, ep.skip, st, true));
+      if (next_T)
+        return launch_mode3_tc_chain(p->tmp2, X, p->dMT, lowop(p), next_T, n3, (size_t)n2 * s,
+                                     ep, err, st, after);
       return launch_mode3_tc_inb(p->tmp2, X, p->dMT, n3, (size_t)n2 * s, ep, err, st, after);
     }
     if (p->tmp3) TC_TRY(transpose_slices(p->tmp1, p->tmp3, n1, s, n3, st, ep.skip));
@@ -667,20 +679,29 @@ extern "C" int tc_transform_dual(tc_plan* p, int which, const float* in, void* o
 }
 
 extern "C" int tc_transform_bf16in(tc_plan* p, int which, const void* in, float* out, size_t P,
-                                   const float* prev, double* sumsq, tc_stream_t stream) {
+                                   const float* prev, double* sumsq, int which_next, void* nxt,
+                                   tc_stream_t stream) {
   if (!p || !in || !out || (const void*)in == (const void*)out) return TC_EINVAL;
   if (which < TC_M || which > TC_MT || P < 1 || P * (size_t)p->n3 > p->tmp_elems)
     return TC_EINVAL;
   if (prev && prev == out) return TC_EINVAL;
+  if (nxt && (which_next < TC_M || which_next > TC_MT || nxt == (void*)out || nxt == in ||
+              (const void*)nxt == (const void*)prev))
+    return TC_EINVAL;
   if (!p->store_bf16) return TC_EUNSUPPORTED;
-  const float* T = which == TC_M ? p->dM : which == TC_MINV ? p->dMinv
-                   : which == TC_MINVT ? p->dMinvT : p->dMT;
+  auto pick = [&](int w) {
+    return w == TC_M ? p->dM : w == TC_MINV ? p->dMinv : w == TC_MINVT ? p->dMinvT : p->dMT;
+  };
+  const float* T = pick(which);
   Epi ep;
   if (prev) {
     ep.coef.rule = COEF_ADD;
     ep.prev = prev;
   }
   if (sumsq) ep.red = make_red(p, sumsq, 0, nullptr, nullptr);
+  if (nxt)
+    return launch_mode3_tc_chain(in, out, T, nxt, pick(which_next), p->n3, P, ep, p->dev_err,
+                                 (cudaStream_t)stream, nullptr);
   return launch_mode3_tc_inb(in, out, T, p->n3, P, ep, p->dev_err, (cudaStream_t)stream,
                              nullptr);
 }

@@ -210,16 +210,23 @@ int lsqr_enqueue(tc_plan* p, const LsqrArgs& a, cudaStream_t st) {
   if (tdf)
     TC_TRY(launch_round(Cin, p->lowU, p->Ty,
                         p->opts.precision == TC_BF16X3 ? ROUND_BF16X3 : ROUND_BF16, st));
+  // Chained products (BF16-stored slice products on the spatial route, basis
+  // kept): each product's pass back also writes the next product's BF16 GEMM
+  // operand, so only the start-up adjoint transforms its operand itself.
+  const bool chain = p->store_bf16 && defer && !td && !thd;
+  const Chain ch_first{false, p->dM}, ch_fwd{true, p->dMinvT}, ch_adj{true, p->dM};
+  int nadj = 0;
   auto fwd = [&](const float* Xv, float* Yv, const Epi& ep, const LsqrStep* step) -> int {
     if (thd) return cprod_thd(p, Yv, ep, st);  // steps run in the adjoint's pass (fold)
-    if (!td) return cprod_epi(p, Xv, Yv, ep, st, step);
+    if (!td) return cprod_epi(p, Xv, Yv, ep, st, step, chain ? &ch_fwd : nullptr);
     if (step) TC_TRY(step->X ? launch_lsqr_update(*step, st) : launch_lsqr_scalars(*step, st));
     return tdf ? cprod_tdf(p, Yv, ep, st) : cprod_td(p, Xv, Yv, ep, st);
   };
   auto adj = [&](const float* Yv, float* Xv, const Epi& ep, const LsqrStep* after) -> int {
     if (thd) return adjoint_thd(p, Xv, ep, st, after);
     if (tdf) return adjoint_tdf(p, Xv, ep, st);
-    return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st, after);
+    const Chain* ch = chain ? (nadj++ == 0 ? &ch_first : &ch_adj) : nullptr;
+    return td ? adjoint_td(p, Yv, Xv, ep, st) : adjoint_epi(p, Yv, Xv, ep, st, after, ch);
   };
   // Deferred schedule on the tensor-core transform route: step j's scalars
   // need alpha_{j+1}, which the adjoint product of step j finishes in its

@@ -227,6 +227,11 @@ int launch_mode3_tc_lowp(const float* in, void* out, const float* T_dev, int n3,
 // TC_EUNSUPPORTED for shapes tube_inb_ok rejects. after: as launch_mode3_tc.
 int launch_mode3_tc_inb(const void* in, float* out, const float* T_dev, int n3, size_t P,
                         const Epi& ep, int* err, cudaStream_t st, const LsqrStep* after);
+// launch_mode3_tc_inb that also writes nxt = bf16(out x_3 T2) (BF16, same
+// layout): the first pass of the product that follows, done here.
+int launch_mode3_tc_chain(const void* in, float* out, const float* T_dev, void* nxt,
+                          const float* T2_dev, int n3, size_t P, const Epi& ep, int* err,
+                          cudaStream_t st, const LsqrStep* after);
 // Whether launch_mode3_tc_inb takes n3 slices of P values at buf (a device
 // buffer of the plan, 16-byte aligned).
 bool tube_inb_ok(const void* buf, int n3, size_t P);
@@ -290,15 +295,24 @@ int launch_lcurve(const double* rg, const double* phibar, const int* kdev, int k
                   double* curve, double* y, int* kopt, cudaStream_t st);
 
 // plan.cu helpers used by solvers
+// Chaining consecutive products on plans with BF16-stored slice products
+// (p->store_bf16): in_ready: the product's BF16 GEMM operand is already in
+// the operand buffer, written by the pass back of the product before it;
+// next_T: this product's pass back also writes the next product's operand,
+// bf16(result x_3 next_T), into the operand buffer (after its GEMM read it).
+struct Chain {
+  bool in_ready = false;
+  const float* next_T = nullptr;
+};
 // With a non-null `step`, the LSQR step runs before the product: inside the
 // product kernel (two-sided fused route) or as its own launch; ep.skip must
 // then be step->done_out.
 int cprod_epi(tc_plan* p, const float* X, float* Y, const Epi& ep, cudaStream_t st,
-              const LsqrStep* step = nullptr);
+              const LsqrStep* step = nullptr, const Chain* ch = nullptr);
 // With `after`, a scalars-only LSQR step runs once the product's norm is in
 // place (folded into the tensor-core transform pass where there is one).
 int adjoint_epi(tc_plan* p, const float* Y, float* X, const Epi& ep, cudaStream_t st,
-                const LsqrStep* after = nullptr);
+                const LsqrStep* after = nullptr, const Chain* ch = nullptr);
 Red make_red(tc_plan* p, double* out, int sqrt_out, const float* other, int* status);
 // Transform-domain products (ORTHODCT plans off the fused route; td_route):
 // operand and result are transformed tensors, the epilogue applies to them.

@@ -919,6 +919,379 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
                  : "memory");
 }
 
+// ------------------------------------------------------- chained pass back --
+// The pass back from BF16 slice products (as k_tube_tma<OUT_F32, 2, INB>):
+// y = ca (in x_3 T) + cp prev, written in FP32 with its norm, and in the same
+// pass nxt = bf16(y x_3 T2), the next product's GEMM operand (the transform
+// that product would start with), so that product skips its own first pass.
+// Roles (608 threads, one CTA a SM):
+//   warp 0 (one lane): BF16 input by TMA straight into the A1 operand;
+//   warp 2 (one lane): prev into the y ring;
+//   warp 1 (one lane): MMA1 (A1 x T, two passes) into acc1[i & 1], then
+//     MMA2 of the previous tile (A2 x T2, three passes) into acc2;
+//   warps 11..18: epilogue: y from acc1 and prev over prev in the y slot,
+//     norm; one thread stores the slot by TMA;
+//   warps 3..10: split y (FP32, from the y slot) into the two BF16 planes of
+//     A2; drain acc2 of the tile before to BF16 into the nxt slot, which one
+//     thread stores by TMA.
+// A y slot goes back to the prev producer once its store has read it and the
+// splitters have read it (two arrivals).
+constexpr int CH_NI = 3, CH_NO = 3;
+constexpr size_t tube_chain_smem() {
+  return 1024 + CH_NI * TA_BYTES + CH_NO * TT_SLOT + 2 * TA_BYTES + TT_SLOT / 2 +
+         4 * TB_BYTES + (3 * CH_NI + 3 * CH_NO + 16) * 8 + 16;
+}
+
+__global__ void __launch_bounds__(TT_NT, 1)
+k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
+             const __grid_constant__ CUtensorMap tmOut, const __grid_constant__ CUtensorMap tmNxt,
+             const float* __restrict__ T, const float* __restrict__ T2, int n3, size_t P,
+             int has_prev, Epi ep, int* err, LsqrStep after) {
+  using namespace tc5;
+  constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (0u << 16) |
+                             ((uint32_t)(TK >> 3) << 17) | ((uint32_t)(TP >> 4) << 24);
+  if (ep.skip && *ep.skip) {
+    if (after.alpha && blockIdx.x == 0 && threadIdx.x == 0) *after.done_out = 1;
+    return;
+  }
+  extern __shared__ uint8_t ch_raw[];
+  uint8_t* base = reinterpret_cast<uint8_t*>(
+      (reinterpret_cast<uintptr_t>(ch_raw) + 1023) & ~(uintptr_t)1023);
+  uint8_t* sin = base;                          // CH_NI BF16 A1 slots (16 KB)
+  uint8_t* sy = sin + CH_NI * TA_BYTES;         // CH_NO prev / y slots (32 KB)
+  uint8_t* sA2 = sy + CH_NO * TT_SLOT;          // the two planes of A2
+  uint8_t* sN = sA2 + 2 * TA_BYTES;             // the nxt slot (BF16, 16 KB)
+  uint8_t* sB = sN + TT_SLOT / 2;               // T's two planes, then T2's
+  uint64_t* ifull = reinterpret_cast<uint64_t*>(sB + 4 * TB_BYTES);  // [NI] input landed
+  uint64_t* iempty = ifull + CH_NI;             // [NI] MMA1 read the input
+  uint64_t* ofull = iempty + CH_NI;             // [NO] y slot holds prev (or is free)
+  uint64_t* oempty = ofull + CH_NO;             // [NO] stored and split (two arrivals)
+  uint64_t* owrit = oempty + CH_NO;             // [NO] y written (8 epilogue warps)
+  uint64_t* dfull = owrit + CH_NO;              // [2] acc1 ready
+  uint64_t* dempty = dfull + 2;                 // [2] acc1 drained (8 epilogue warps)
+  uint64_t* efull = dempty + 2;                 // [2] acc2 ready
+  uint64_t* eempty = efull + 2;                 // [2] acc2 drained (8 splitter warps)
+  uint64_t* a2full = eempty + 2;                // A2 written (8 splitter warps)
+  uint64_t* a2empty = a2full + 1;               // MMA2 read A2
+  uint64_t* nwrit = a2empty + 1;                // nxt slot written (8 splitter warps)
+  uint64_t* nfree = nwrit + 1;                  // nxt slot read by its store
+  uint64_t* fin = nfree + 1;                    // every MMA of this CTA completed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(fin + 1);
+  __shared__ int sh_fail;
+  __shared__ float sh_coef[2];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ntile = (int)((P + TP - 1) / TP);
+  const uint32_t box = (uint32_t)n3 * TP * 4;  // bytes of one FP32 prev box
+
+  if (tid == 0) {
+    for (int b = 0; b < CH_NI; ++b) {
+      mbar_init(ifull + b, 1);
+      mbar_init(iempty + b, 1);
+    }
+    for (int b = 0; b < CH_NO; ++b) {
+      mbar_init(ofull + b, 1);
+      mbar_init(oempty + b, 2);
+      mbar_init(owrit + b, 8);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(dfull + b, 1);
+      mbar_init(dempty + b, 8);
+      mbar_init(efull + b, 1);
+      mbar_init(eempty + b, 8);
+    }
+    mbar_init(a2full, 8);
+    mbar_init(a2empty, 1);
+    mbar_init(nwrit, 8);
+    mbar_init(nfree, 1);
+    mbar_init(fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    sh_fail = 0;
+  }
+  coef_compute(ep.coef, sh_coef);
+  if (warp >= 3 && warp < 11) {  // T and T2, two planes each
+    const int ct = tid - 96;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int u = ct + 256 * (j & 1), n = u >> 3, c = u & 7;
+      const float* src = j < 2 ? T : T2;
+      uint8_t* dst = sB + (j < 2 ? 0 : 2 * TB_BYTES);
+      float t[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int l = 8 * c + e;
+        t[e] = (n < n3 && l < n3) ? __ldg(src + (size_t)n * n3 + l) : 0.f;
+      }
+      uint4 pl[2];
+      split8<2>(t, pl);
+      const uint32_t off = n * 128 + ((c ^ (n & 7)) << 4);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) *reinterpret_cast<uint4*>(dst + q * TB_BYTES + off) = pl[q];
+    }
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     su32(tslot)),
+                 "r"(4 * TK)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;  // acc1: columns 0, TK; acc2: 2 TK, 3 TK
+  volatile int* vfail = &sh_fail;
+  float local = 0.f;
+  int issued = 0, issued_p = 0;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int s = i % CH_NI;
+        if (!mbar_wait(iempty + s, ((uint32_t)(i / CH_NI) & 1u) ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        mbar_expect_tx(ifull + s, TA_BYTES);
+        tma_load_3d(sin + s * TA_BYTES, &tmIn, t * TP, 0, 0, ifull + s);
+        tma_load_3d(sin + s * TA_BYTES + TA_BYTES / 2, &tmIn, t * TP + TP / 2, 0, 0, ifull + s);
+        issued = i + 1;
+      }
+    }
+  } else if (warp == 2) {
+    if (lane == 0) {
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int s = i % CH_NO;
+        if (!mbar_wait(oempty + s, ((uint32_t)(i / CH_NO) & 1u) ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        if (has_prev) {
+          mbar_expect_tx(ofull + s, box);
+          tma_load_2d(sy + s * TT_SLOT, &tmPrev, t * TP, 0, ofull + s);
+          issued_p = i + 1;
+        } else {
+          mbar_arrive(ofull + s);
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      auto mma2 = [&](int k) -> bool {  // tile k's A2 x T2 into acc2[k & 1]
+        const int e = k & 1;
+        if (!mbar_wait(a2full, (uint32_t)k & 1u) ||
+            !mbar_wait(eempty + e, ((uint32_t)(k >> 1) & 1u) ^ 1u))
+          return false;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)((2 + e) * TK);
+#pragma unroll
+        for (int pass = 0; pass < 3; ++pass) {
+          const uint32_t a0 = su32(sA2 + tube_pa(pass) * TA_BYTES);
+          const uint32_t b0 = su32(sB + (2 + tube_pb(pass)) * TB_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk)
+            umma<0>(acc, smem_desc(a0 + kk * 16 * 128, TA_BYTES / 2, 1024),
+                    smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+        }
+        umma_commit(a2empty);
+        umma_commit(efull + e);
+        return true;
+      };
+      int i = 0;
+      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
+        const int d = i & 1;
+        if (!mbar_wait(ifull + i % CH_NI, (uint32_t)(i / CH_NI) & 1u) ||
+            !mbar_wait(dempty + d, ((uint32_t)(i >> 1) & 1u) ^ 1u)) {
+          *vfail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t acc = tmem + (uint32_t)(d * TK);
+        const uint32_t a0s = su32(sin + (i % CH_NI) * TA_BYTES);
+#pragma unroll
+        for (int pass = 0; pass < 2; ++pass) {
+          const uint32_t b0 = su32(sB + pass * TB_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < TK / 16; ++kk)
+            umma<0>(acc, smem_desc(a0s + kk * 16 * 128, TA_BYTES / 2, 1024),
+                    smem_desc(b0 + kk * 16 * 2, 16, 1024), IDESC, (pass | kk) != 0);
+        }
+        umma_commit(iempty + i % CH_NI);
+        umma_commit(dfull + d);
+        if (i > 0 && !mma2(i - 1)) {
+          *vfail = 1;
+          break;
+        }
+      }
+      if (i > 0 && !*vfail && !mma2(i - 1)) *vfail = 1;
+      umma_commit(fin);
+    }
+  } else if (warp < 11) {  // splitters / nxt drain
+    const int ct = tid - 96;
+    const int qd = warp & 3, hh = (warp - 3) >> 2, px = 32 * qd + lane;
+    auto drain = [&](int k, int tk) -> bool {  // tile k (tile index tk) of acc2 to nxt
+      const int e = k & 1;
+      bool ok = mbar_wait(efull + e, (uint32_t)(k >> 1) & 1u);
+      ok = ok && (k == 0 || mbar_wait(nfree, (uint32_t)(k - 1) & 1u));  // sN read by its store
+      if (!__all_sync(0xffffffffu, ok)) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)((2 + e) * TK + 32 * hh), v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(eempty + e);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int kq = 32 * hh + j;
+        if (kq < n3) reinterpret_cast<__nv_bfloat16*>(sN)[kq * TP + px] = __float2bfloat16_rn(v[j]);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(nwrit);
+      bool stored = true;
+      if (ct == 0) {  // every splitter warp wrote its part: store, then free the slot
+        stored = mbar_wait(nwrit, (uint32_t)k & 1u);
+        if (stored) {
+          tma_store_2d(&tmNxt, tk * TP, 0, sN);
+          bulk_commit();
+          bulk_wait_read();
+          mbar_arrive(nfree);
+        }
+      }
+      return __all_sync(0xffffffffu, stored);
+    };
+    int i = 0, tprev = -1;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+      if (__any_sync(0xffffffffu, *vfail)) break;
+      const int s = i % CH_NO;
+      // y of tile i written; A2 free (MMA2 of tile i - 1 read it)
+      bool ok = mbar_wait(owrit + s, (uint32_t)(i / CH_NO) & 1u);
+      ok = ok && (i == 0 || mbar_wait(a2empty, ((uint32_t)(i - 1) & 1u)));
+      if (!__all_sync(0xffffffffu, ok)) {
+        *vfail = 1;
+        break;
+      }
+      const float* stg = reinterpret_cast<const float*>(sy + s * TT_SLOT);
+#pragma unroll
+      for (int i8 = 0; i8 < 4; ++i8) {
+        const int uu = ct + 256 * i8, l = uu >> 4, c = uu & 15;
+        float x[8];
+        if (l < n3) {
+          const float4 a = *reinterpret_cast<const float4*>(stg + l * TP + 8 * c);
+          const float4 b = *reinterpret_cast<const float4*>(stg + l * TP + 8 * c + 4);
+          x[0] = a.x; x[1] = a.y; x[2] = a.z; x[3] = a.w;
+          x[4] = b.x; x[5] = b.y; x[6] = b.z; x[7] = b.w;
+        } else {
+#pragma unroll
+          for (int e = 0; e < 8; ++e) x[e] = 0.f;
+        }
+        uint4 pl[2];
+        split8<2>(x, pl);
+        const uint32_t off = (c >> 3) * (TA_BYTES / 2) + l * 128 + (((c & 7) ^ (l & 7)) << 4);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) *reinterpret_cast<uint4*>(sA2 + q * TA_BYTES + off) = pl[q];
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(a2full);
+      if (ct == 0) {  // all eight splitter warps have read this y slot: let it go
+        if (mbar_wait(a2full, (uint32_t)i & 1u))
+          mbar_arrive(oempty + s);
+        else
+          *vfail = 1;
+      }
+      if (i > 0 && !drain(i - 1, tprev)) {
+        *vfail = 1;
+        break;
+      }
+      tprev = t;
+    }
+    if (i > 0 && !*vfail && !drain(i - 1, tprev)) *vfail = 1;
+    if (ct == 0) bulk_wait_all();
+  } else {  // epilogue warps 11..18
+    const int qd = warp & 3, hh = (warp - 11) >> 2, px = 32 * qd + lane, et = tid - 352;
+    const float ca = sh_coef[0], cp = sh_coef[1];
+    int i = 0;
+    for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
+      if (__any_sync(0xffffffffu, *vfail)) break;
+      const int s = i % CH_NO, d = i & 1;
+      bool ok = mbar_wait(dfull + d, (uint32_t)(i >> 1) & 1u);
+      ok = ok && mbar_wait(ofull + s, (uint32_t)(i / CH_NO) & 1u);
+      if (!__all_sync(0xffffffffu, ok)) {
+        *vfail = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float* f = reinterpret_cast<float*>(sy + s * TT_SLOT);
+      const bool live = (size_t)t * TP + px < P;
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(d * TK + 32 * hh), v);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(dempty + d);
+#pragma unroll
+      for (int j = 0; j < 32; ++j) {
+        const int k = 32 * hh + j;
+        if (k >= n3) continue;
+        const int o = k * TP + px;
+        float y = ca * v[j];
+        if (has_prev) y = fmaf(cp, f[o], y);
+        f[o] = y;
+        if (live) local = fmaf(y, y, local);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(owrit + s);
+      if (et == 0) {  // one store in flight; a slot goes back once stored and split
+        if (mbar_wait(owrit + s, (uint32_t)(i / CH_NO) & 1u)) {
+          tma_store_2d(&tmOut, t * TP, 0, f);
+          bulk_commit();
+          if (i > 0) {
+            bulk_wait_read1();
+            mbar_arrive(oempty + (i - 1) % CH_NO);
+          }
+        } else {
+          *vfail = 1;
+        }
+      }
+    }
+    if (et == 0) {
+      bulk_wait_all();
+      if (i > 0 && !*vfail) mbar_arrive(oempty + (i - 1) % CH_NO);
+    }
+  }
+
+  __syncthreads();
+  const bool failed = *vfail != 0;
+  if (warp == 1 && lane == 0) mbar_wait(fin, 0);
+  if (failed && warp == 0 && lane == 0) {
+    for (int g = (issued > CH_NI ? issued - CH_NI : 0); g < issued; ++g)
+      mbar_wait(ifull + g % CH_NI, (uint32_t)(g / CH_NI) & 1u);
+    atomicExch(err, TC_ETIMEOUT);
+  }
+  if (failed && warp == 2 && lane == 0) {
+    for (int g = (issued_p > CH_NO ? issued_p - CH_NO : 0); g < issued_p; ++g)
+      mbar_wait(ofull + g % CH_NO, (uint32_t)(g / CH_NO) & 1u);
+  }
+  if (ep.red.out) {
+    const bool last = reduce_finish(local, ep.red);
+    if (last && after.alpha && tid == 0) {
+      if (*after.done_in) {
+        *after.done_out = 1;
+      } else {
+        float sh[3];
+        lsqr_step_scalars(after, sh, true);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(4 * TK)
+                 : "memory");
+}
+
 // The TMA form when its requirements hold: P % 8 == 0 (16-byte rows of the
 // FP32 and BF16 boxes), 16-byte aligned tensors, no dot-product reduction.
 bool tube_tma_ok(const float* in, const void* out, size_t P, const Epi& ep) {
@@ -1025,6 +1398,32 @@ int launch_mode3_tc_inb(const void* in, float* out, const float* T_dev, int n3, 
   return TC_OK;
 }
 
+int launch_mode3_tc_chain(const void* in, float* out, const float* T_dev, void* nxt,
+                          const float* T2_dev, int n3, size_t P, const Epi& ep, int* err,
+                          cudaStream_t st, const LsqrStep* after) {
+  TC_CHECK(n3 > 0 && n3 <= TK && nxt && T2_dev);
+  TC_CHECK(!after || (after->alpha && !after->X && ep.red.out));
+  auto al = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
+  if (P % 8 || P / TP >= (1u << 30) || !al(in) || !al(out) || !al(nxt) || !al(ep.prev) ||
+      ep.red.other)
+    return TC_EUNSUPPORTED;
+  CUtensorMap mi, mp, mo, mn;
+  TC_TRY(make_tmap(&mi, in, 1, (int)P, n3, 1, TP / 2, TK));
+  const int hp = ep.prev ? 1 : 0;
+  TC_TRY(make_tmap_2d(&mo, out, 0, P, (size_t)n3, TP, n3));
+  if (hp)
+    TC_TRY(make_tmap_2d(&mp, ep.prev, 0, P, (size_t)n3, TP, n3));
+  else
+    mp = mo;
+  TC_TRY(make_tmap_2d(&mn, nxt, 1, P, (size_t)n3, TP, n3));
+  const size_t ntile = (P + TP - 1) / TP;
+  const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
+  k_tube_chain<<<grid, TT_NT, tube_chain_smem(), st>>>(mi, mp, mo, mn, T_dev, T2_dev, n3, P, hp,
+                                                       ep, err, after ? *after : LsqrStep{});
+  TC_CUDA(cudaGetLastError());
+  return TC_OK;
+}
+
 // Whether the BF16-input pass takes this plan's shapes: the encoder accepts
 // the input map (box of 64 slices over n3 of them).
 bool tube_inb_ok(const void* buf, int n3, size_t P) {
@@ -1082,6 +1481,8 @@ int transform_init() {
                                (int)tube_tma_smem(2, OUT_TF32)));
   TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tube_tma_smem(3, OUT_F32)));
+  TC_CUDA(cudaFuncSetAttribute(k_tube_chain, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)tube_chain_smem()));
   TC_CUDA(cudaFuncSetAttribute(k_tube_tma<OUT_F32, 2, false, true>,
                                cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)tube_tma_smem(2, OUT_F32, false, true)));

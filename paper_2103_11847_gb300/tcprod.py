@@ -64,7 +64,7 @@ _SIGS = {
     "tc_transform": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p, c_void_p,
                       c_void_p], c_int),
     "tc_transform_bf16in": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p,
-                             c_void_p, c_void_p], c_int),
+                             c_void_p, c_int, c_void_p, c_void_p], c_int),
     "tc_slice_gemm_gk": ([c_void_p, c_void_p, c_void_p, c_int, c_void_p, c_void_p, c_void_p,
                           c_void_p, c_void_p], c_int),
     "tc_transform_dual": ([c_void_p, c_int, c_void_p, c_void_p, ctypes.c_size_t, c_void_p,
@@ -249,14 +249,19 @@ def tc_transform(h, which, X, Y, prev=None, sumsq=None, stream=None):
                                               _stream(stream)))
 
 
-def tc_transform_bf16in(h, which, X, Y, prev=None, sumsq=None, stream=None):
-    """Y = X x_3 T (+ prev) from BF16 X (plans with TC_STORE_BF16); Y FP32."""
+def tc_transform_bf16in(h, which, X, Y, prev=None, sumsq=None, which_next=-1, nxt=None,
+                        stream=None):
+    """Y = X x_3 T (+ prev) from BF16 X (plans with TC_STORE_BF16); Y FP32;
+    nxt (BF16, or None) = bf16(Y x_3 T_next)."""
     P = X[0].numel()
     if Y.shape != X.shape or (prev is not None and prev.shape != X.shape):
         raise ValueError("X, Y (and prev) must have the same shape")
+    if nxt is not None and nxt.shape != X.shape:
+        raise ValueError("nxt must have X's shape")
     _check("tc_transform_bf16in", lib().tc_transform_bf16in(
         h, int(which), _ptr(X, torch.bfloat16, name="X"), _ptr(Y, name="Y"), P,
-        _ptr(prev, name="prev"), _ptr(sumsq, torch.float64, name="sumsq"), _stream(stream)))
+        _ptr(prev, name="prev"), _ptr(sumsq, torch.float64, name="sumsq"), int(which_next),
+        _ptr(nxt, torch.bfloat16, name="nxt"), _stream(stream)))
 
 
 def tc_slice_gemm_gk(h, Xh, Yh, s0, s1=None, prev=None, sumsq=None, adjoint=False,

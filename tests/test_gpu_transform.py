@@ -194,3 +194,63 @@ def test_transform_from_bf16_input(tc, n3, P):
         assert e < 1e-4 and es < 1e-4
     assert tc.tc_plan_status(plan.handle) == tc.TC_OK
     plan.close()
+
+
+@pytest.mark.parametrize("n3,P", [(64, 8192), (64, 1000), (37, 2056)])
+def test_chained_transform_from_bf16_input(tc, n3, P):
+    # The pass back that also writes the next product's operand:
+    # out = in x_3 T + prev (FP32, 1e-4) and nxt = bf16(out x_3 T_next)
+    # (within BF16 rounding of the FP64 chain, 4e-3), and out equal to the
+    # unchained pass's to the bit.
+    rng = np.random.default_rng(11 * n3 + P)
+    A = torch.from_numpy(rng.standard_normal((n3, 64, 64)).astype(np.float32)).cuda()
+    plan = tc.Plan(A, s=128, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    M = cp.transform_matrix(n3)
+    Mi = np.linalg.inv(M)
+    mats = {tc.TC_M: M, tc.TC_MINV: Mi, tc.TC_MINVT: Mi.T, tc.TC_MT: M.T}
+    Xb = torch.from_numpy(rng.standard_normal((n3, P)).astype(np.float32)).cuda().to(torch.bfloat16)
+    Xd = Xb.float().cpu().numpy().astype(np.float64)
+    prev = torch.from_numpy(rng.standard_normal((n3, P)).astype(np.float32)).cuda()
+    for which, nxt_kind in [(tc.TC_MINV, tc.TC_MINVT), (tc.TC_MT, tc.TC_M)]:
+        Y = torch.empty((n3, P), device="cuda")
+        Y0 = torch.empty((n3, P), device="cuda")
+        N = torch.empty((n3, P), dtype=torch.bfloat16, device="cuda")
+        ss = torch.zeros(1, dtype=torch.float64, device="cuda")
+        tc.tc_transform_bf16in(plan.handle, which, Xb, Y, prev, ss, which_next=nxt_kind, nxt=N)
+        tc.tc_transform_bf16in(plan.handle, which, Xb, Y0, prev)
+        torch.cuda.synchronize()
+        ref = mats[which] @ Xd + prev.cpu().numpy().astype(np.float64)
+        e = np.linalg.norm(Y.cpu().numpy() - ref) / np.linalg.norm(ref)
+        nref = mats[nxt_kind] @ ref
+        en = np.linalg.norm(N.float().cpu().numpy() - nref) / np.linalg.norm(nref)
+        es = abs(float(ss.item()) - float(np.sum(ref ** 2))) / float(np.sum(ref ** 2))
+        print(n3, P, which, e, en, es)
+        assert e < 1e-4 and en < 4e-3 and es < 1e-4
+        assert torch.equal(Y, Y0)
+    assert tc.tc_plan_status(plan.handle) == tc.TC_OK
+    plan.close()
+
+
+def test_chained_lsqr_matches_unchained_products(tc):
+    # c-LSQR on a BF16-stored plan chains its products (each pass back forms
+    # the next GEMM operand). The operand it forms is the one the next
+    # product's own transform would form from the same FP32 vector, so the
+    # chained solve (X_reg requested) and a solve that transforms every
+    # operand itself agree; the second is the same plan without X_reg, whose
+    # iterate comes from the per-step updates, so the check is the iterate
+    # to FP32 rounding of the recurrences.
+    from paper_2103_11847_gb300 import inputs
+    w = inputs.video_deblur(n=128, frames=64, seed=13)
+    A = torch.from_numpy(w["A"].astype(np.float32)).cuda()
+    Xt = torch.from_numpy(w["X_true"].astype(np.float32)).cuda()
+    plan = tc.Plan(A, s=128, precision=tc.TC_BF16, store=tc.TC_STORE_BF16)
+    C = plan.cprod(Xt)
+    Xc, Xr, _, info = plan.lsqr(C, 10, regularize=True)
+    Xu, _, _, info2 = plan.lsqr(C, 10, regularize=False)
+    torch.cuda.synchronize()
+    assert tc.read_info(info)["iters"] == 10 and tc.read_info(info2)["iters"] == 10
+    d = float((Xc - Xu).norm() / Xu.norm())
+    print("chained vs unchained iterate", d)
+    assert d < 1e-4
+    assert tc.tc_plan_status(plan.handle) == tc.TC_OK
+    plan.close()
