@@ -975,6 +975,7 @@ def run_gpu(args):
             line["two_sided_256"] = two_sided_form(dev, peaks, src_peaks)
             line["batched_form"] = batched_form(dev)
             line["learned_form"] = learned_form()
+            line["paper_shaped"] = paper_shaped()
         if not args.no_cpu_baseline and world == 1:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
