@@ -17,18 +17,18 @@
 // is scarce on GB300.
 //
 // Search: the same three nested 200-point log grids as the general path
-// (first level [1e-10 s, s] with s = ||C~_k||_F). Each point of a level runs on
-// its own CTA, so the serial O(k) FP64 chains of the 200 points spread over
-// the SMs (packing several points per SM measured slower: they share the
-// SM's narrow FP64 pipe).
+// (first level [1e-10 s, s] with s = ||C~_k||_F). Each lane of a warp runs one
+// point's serial O(k) FP64 chain, 32 points a warp: the SM's narrow FP64 pipe
+// takes a warp instruction at the same cost whether one lane or all 32 are
+// active, so one point a warp (an earlier form) kept the pipe 87% busy on
+// 1/32 of the work when the batched form's 128 problems filled the GPU.
 #include "gcv_eval.cuh"
 
 namespace {
 
 constexpr int NGRID = 200;
 constexpr int NLEVEL = 3;
-constexpr int PPC = 1;  // grid points (warps) per CTA: FP64 throughput per SM bounds
-                        // the chains, so one point per CTA spreads them widest
+constexpr int PPW = 32;  // grid points a warp (one a lane); one warp a CTA
 
 // First index of the smallest of v[0..n) over one warp (ties to the lower index).
 __device__ int warp_argmin(const double* v, int n) {
@@ -48,7 +48,7 @@ __device__ int warp_argmin(const double* v, int n) {
   return bi < n ? bi : 0;
 }
 
-// One level of the search: warp w of CTA b evaluates grid point PPC b + w.
+// One level of the search: lane l of CTA b evaluates grid point PPW b + l.
 // Grouped launches (grid.y = problems): problem blockIdx.y's doubles are ps
 // and its ints fsi further on (0 for a single problem).
 __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const double* alpha, const double* beta,
@@ -60,10 +60,9 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
     if (kdev) kdev += (size_t)blockIdx.y * fsi;
   }
   const int k = kdev ? min(*kdev, kmax) : kmax;
-  const int i = blockIdx.x * PPC + (threadIdx.x >> 5);
-  if (i >= NGRID) return;
+  const int i = blockIdx.x * PPW + (int)threadIdx.x;
   if (k <= 0) {
-    if ((threadIdx.x & 31) == 0) {
+    if (i < NGRID) {
       lams[level * NGRID + i] = nan("");
       vals[level * NGRID + i] = nan("");
     }
@@ -84,7 +83,7 @@ __global__ void k_gcv_bd_level(const double* rg, const double* phibar, const dou
     lo = log(pl[max(b - 1, 0)]);
     hi = log(pl[min(b + 1, NGRID - 1)]);
   }
-  if ((threadIdx.x & 31) != 0) return;
+  if (i >= NGRID) return;  // after the warp-wide bounds above
   const double step = (hi - lo) / (NGRID - 1);
   const double lam = exp(i == NGRID - 1 ? hi : lo + i * step);
   const double pb = phibar[k];
@@ -230,7 +229,7 @@ int launch_gcv_bidiag_group(const double* rg, const double* phibar, const double
   double* vals = work + NLEVEL * NGRID;
   if (!(lambda_in >= 0.0)) {
     for (int level = 0; level < NLEVEL; ++level) {
-      k_gcv_bd_level<<<dim3((NGRID + PPC - 1) / PPC, count), 32 * PPC, 0, st>>>(
+      k_gcv_bd_level<<<dim3((NGRID + PPW - 1) / PPW, count), PPW, 0, st>>>(
           rg, phibar, alpha, beta, kdev, kmax, variant, level, lams, vals, ps, fsi);
       TC_CUDA(cudaGetLastError());
     }
@@ -251,7 +250,7 @@ int launch_gcv_bidiag(const double* rg, const double* phibar, const double* alph
   double* vals = work + NLEVEL * NGRID;
   if (!(lambda_in >= 0.0)) {
     for (int level = 0; level < NLEVEL; ++level) {
-      k_gcv_bd_level<<<(NGRID + PPC - 1) / PPC, 32 * PPC, 0, st>>>(
+      k_gcv_bd_level<<<(NGRID + PPW - 1) / PPW, PPW, 0, st>>>(
           rg, phibar, alpha, beta, kdev, kmax, variant, level, lams, vals);
       TC_CUDA(cudaGetLastError());
     }
