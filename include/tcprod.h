@@ -84,7 +84,9 @@ typedef enum {
  *   TC_ROUTE_AUTO: ORTHODCT plans off the fused route iterate on dct(C)
  *     (Definition 2.2's norms are the DCT's); every other solve is spatial.
  *   TC_ROUTE_SPATIAL: every product transforms its operand in and its result
- *     out (Algorithm 1), and the iteration runs on spatial tensors.
+ *     out (Algorithm 1), and the iteration runs on spatial tensors. (With
+ *     TC_STORE_BF16, c-LSQR solves that keep the basis form each product's
+ *     BF16 operand in the pass back of the product before it.)
  *   TC_ROUTE_DUAL: as AUTO, except that solves that keep the basis (X_reg
  *     requested) on BF16 plans of the TH product, one-sided, 32 < n3 <= 64,
  *     iterate in the transform domains (the dual-domain route): V as
@@ -92,8 +94,9 @@ typedef enum {
  *     Krylov update in its store plus one tube pass by G = M^{-T} M^{-1} (or
  *     G^{-1} = M M^T) that writes the next GEMM's BF16 operand and the norm of
  *     the spatial tensor; X and X_reg are transformed back once (by M^T) at
- *     the end. It moves fewer bytes than the spatial route, and measures as
- *     fast on the 512 x 512 x 64 video, so AUTO keeps the spatial one. */
+ *     the end. On the 512 x 512 x 64 video it measures as fast as the spatial
+ *     route with FP32-stored products and slower than the spatial route with
+ *     BF16-stored, chained products (tc_store), so AUTO keeps the spatial one. */
 typedef enum { TC_ROUTE_AUTO = 0, TC_ROUTE_SPATIAL = 1, TC_ROUTE_DUAL = 2 } tc_route;
 
 /* How the tensor-core slice products reach the transform back (Algorithm 1,
