@@ -1058,35 +1058,45 @@ WORKLOAD_NAMES = {
 
 
 def run_reference(args):
-    """The oracle as the reference arm: each step one bounded sample of the
-    workload (CPU_SAMPLE iterations from X_0 = 0) on the host cores; the run
-    stops early, after at least two steps, once about two minutes have gone."""
+    """The oracle as the reference arm, on all the host's cores: each step
+    one bounded sample of the workload (CPU_SAMPLE iterations from X_0 = 0)
+    by one single-threaded run a core, all started together (the oracle's
+    einsums use one core each); value = the iterations of all runs over the
+    steps' wall time. The run stops early, after at least two steps, once
+    about two minutes have gone."""
     rank, _, world = dist_env()
     if rank != 0:
         return
     wl = WORKLOADS[args.workload]
     sample = CPU_SAMPLE.get(args.workload, 2)
     t0 = time.perf_counter()
-    out = cpu_run(args.workload, sample, max(args.steps, 1), args.ref_budget)
+    walls, runs, cores = [], 0, 1
+    for step in range(max(args.steps, 1)):
+        cores, times, wall = cpu_run_all_cores(args.workload, sample)
+        walls.append(wall)
+        runs += len(times)
+        if step >= 1 and time.perf_counter() - t0 > args.ref_budget:
+            break
     el = time.perf_counter() - t0
-    times = out["times"]
-    value = sample * len(times) / sum(times)
+    value = sample * runs / sum(walls)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "LSQR iterations/s",
-        "n_gpus": world, "steps": len(times), "steps_requested": args.steps,
-        "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sum(times) / len(times),
+        "n_gpus": world, "steps": len(walls), "steps_requested": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": 1000.0 * sum(walls) / len(walls),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded video/image + Gaussian Toeplitz blurs + 1e-3 noise)",
         "config": {"workload": f"{args.workload}: c-LSQR (FP64 NumPy oracle on the host cores); "
                                f"each step a bounded sample of {sample} iterations of the "
-                               f"{wl['iters']}-iteration solve",
+                               f"{wl['iters']}-iteration solve, one single-threaded run a "
+                               f"core",
                    "wall_s": el},
-        "cpu_baseline": {"kind": "oracle", "cores": out["cores_used"],
-                         "cores_available": out["cores_available"], "value": value,
+        "cpu_baseline": {"kind": "oracle", "cores": cores,
+                         "cores_available": len(os.sched_getaffinity(0)), "value": value,
                          "unit": "LSQR iterations/s",
-                         "sample": f"{len(times)} runs of {sample} c-LSQR iterations from X_0 = 0 "
-                                   f"(start-up product and norms included), "
-                                   f"{sum(times):.1f} s"},
+                         "sample": f"{len(walls)} steps of {cores} concurrent runs of {sample} "
+                                   f"c-LSQR iterations from X_0 = 0 (start-up product and "
+                                   f"norms included, process start included), "
+                                   f"{sum(walls):.1f} s"},
         "e2e": {"value": value, "unit": "LSQR iterations/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
