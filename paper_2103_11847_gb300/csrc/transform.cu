@@ -1379,7 +1379,8 @@ int launch_mode3_tc_inb(const void* in, float* out, const float* T_dev, int n3, 
   TC_CHECK(n3 > 0 && n3 <= TK);
   TC_CHECK(!after || (after->alpha && !after->X && ep.red.out));
   auto al = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  if (P % 8 || P / TP >= (1u << 30) || !al(in) || !al(out) || !al(ep.prev) || ep.red.other)
+  // the input map's inner extent is an int: P < 2^31
+  if (P % 8 || P >= (1u << 31) || !al(in) || !al(out) || !al(ep.prev) || ep.red.other)
     return TC_EUNSUPPORTED;
   CUtensorMap mi, mp, mo;
   // BF16 input as a 3-D map (P, n3, 1), box 64 pixels x 64 slices, 128-byte
@@ -1404,7 +1405,7 @@ int launch_mode3_tc_chain(const void* in, float* out, const float* T_dev, void* 
   TC_CHECK(n3 > 0 && n3 <= TK && nxt && T2_dev);
   TC_CHECK(!after || (after->alpha && !after->X && ep.red.out));
   auto al = [](const void* q) { return q == nullptr || (reinterpret_cast<uintptr_t>(q) & 15) == 0; };
-  if (P % 8 || P / TP >= (1u << 30) || !al(in) || !al(out) || !al(nxt) || !al(ep.prev) ||
+  if (P % 8 || P >= (1u << 31) || !al(in) || !al(out) || !al(nxt) || !al(ep.prev) ||
       ep.red.other)
     return TC_EUNSUPPORTED;
   CUtensorMap mi, mp, mo, mn;
@@ -1427,7 +1428,7 @@ int launch_mode3_tc_chain(const void* in, float* out, const float* T_dev, void* 
 // Whether the BF16-input pass takes this plan's shapes: the encoder accepts
 // the input map (box of 64 slices over n3 of them).
 bool tube_inb_ok(const void* buf, int n3, size_t P) {
-  if (n3 <= TC_TUBE_MIN_N3 || n3 > TK || P % 8 || P / TP >= (1u << 30)) return false;
+  if (n3 <= TC_TUBE_MIN_N3 || n3 > TK || P % 8 || P >= (1u << 31)) return false;
   if (reinterpret_cast<uintptr_t>(buf) & 15) return false;
   CUtensorMap m;
   return make_tmap(&m, buf, 1, (int)P, n3, 1, TP / 2, TK) == TC_OK;
