@@ -924,25 +924,28 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
 // y = ca (in x_3 T) + cp prev, written in FP32 with its norm, and in the same
 // pass nxt = bf16(y x_3 T2), the next product's GEMM operand (the transform
 // that product would start with), so that product skips its own first pass.
-// Roles (608 threads, one CTA a SM):
+// Roles (640 threads, one CTA a SM):
 //   warp 0 (one lane): BF16 input by TMA straight into the A1 operand;
-//   warp 2 (one lane): prev into the y ring;
+//   warp 2 (one lane): the y ring: the first CH_NO prev loads, then per tile
+//     the TMA store of y and, once the store and the splitters have read the
+//     slot (two arrivals), the prev load CH_NO tiles ahead into it;
 //   warp 1 (one lane): MMA1 (A1 x T, two passes) into acc1[i & 1], then
 //     MMA2 of the previous tile (A2 x T2, three passes) into acc2;
 //   warps 11..18: epilogue: y from acc1 and prev over prev in the y slot,
-//     norm; one thread stores the slot by TMA;
+//     norm;
 //   warps 3..10: split y (FP32, from the y slot) into the two BF16 planes of
-//     A2; drain acc2 of the tile before to BF16 into the nxt slot, which one
-//     thread stores by TMA.
-// A y slot goes back to the prev producer once its store has read it and the
-// splitters have read it (two arrivals).
-constexpr int CH_NI = 3, CH_NO = 3;
+//     A2; drain acc2 of the tile before to BF16 into the nxt slot;
+//   warp 19 (one lane): the TMA store of the nxt slot, which it frees once
+//     the store has read it.
+// Both store threads wait for their store's reads at once: a split or a
+// drain that waited for them instead held up the tile after it (measured).
+constexpr int CH_NI = 3, CH_NO = 3, CH_NT = TT_NT + 32;
 constexpr size_t tube_chain_smem() {
   return 1024 + CH_NI * TA_BYTES + CH_NO * TT_SLOT + 2 * TA_BYTES + TT_SLOT / 2 +
          4 * TB_BYTES + (3 * CH_NI + 3 * CH_NO + 16) * 8 + 16;
 }
 
-__global__ void __launch_bounds__(TT_NT, 1)
+__global__ void __launch_bounds__(CH_NT, 1)
 k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUtensorMap tmPrev,
              const __grid_constant__ CUtensorMap tmOut, const __grid_constant__ CUtensorMap tmNxt,
              const float* __restrict__ T, const float* __restrict__ T2, int n3, size_t P,
@@ -1059,22 +1062,48 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
       }
     }
   } else if (warp == 2) {
-    if (lane == 0) {
-      int i = 0;
-      for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++i) {
-        const int s = i % CH_NO;
-        if (!mbar_wait(oempty + s, ((uint32_t)(i / CH_NO) & 1u) ^ 1u)) {
-          *vfail = 1;
-          break;
-        }
+    if (lane == 0) {  // the y ring: prev loads CH_NO tiles ahead of the stores of y
+      const int nmine = (int)blockIdx.x < ntile
+                            ? (ntile - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x
+                            : 0;
+      auto load = [&](int k) -> bool {
+        const int s = k % CH_NO;
+        if (!mbar_wait(oempty + s, ((uint32_t)(k / CH_NO) & 1u) ^ 1u)) return false;
         if (has_prev) {
           mbar_expect_tx(ofull + s, box);
-          tma_load_2d(sy + s * TT_SLOT, &tmPrev, t * TP, 0, ofull + s);
-          issued_p = i + 1;
+          tma_load_2d(sy + s * TT_SLOT, &tmPrev, ((int)blockIdx.x + k * (int)gridDim.x) * TP, 0,
+                      ofull + s);
+          issued_p = k + 1;
         } else {
           mbar_arrive(ofull + s);
         }
+        return true;
+      };
+      int il = 0;
+      for (; il < CH_NO && il < nmine; ++il)
+        if (!load(il)) {
+          *vfail = 1;
+          break;
+        }
+      for (int i = 0; i < nmine && !*vfail; ++i) {
+        const int s = i % CH_NO;
+        if (!mbar_wait(owrit + s, (uint32_t)(i / CH_NO) & 1u)) {
+          *vfail = 1;
+          break;
+        }
+        tma_store_2d(&tmOut, ((int)blockIdx.x + i * (int)gridDim.x) * TP, 0, sy + s * TT_SLOT);
+        bulk_commit();
+        bulk_wait_read();
+        mbar_arrive(oempty + s);
+        if (il < nmine) {
+          if (!load(il)) {
+            *vfail = 1;
+            break;
+          }
+          ++il;
+        }
       }
+      bulk_wait_all();
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -1130,7 +1159,7 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
   } else if (warp < 11) {  // splitters / nxt drain
     const int ct = tid - 96;
     const int qd = warp & 3, hh = (warp - 3) >> 2, px = 32 * qd + lane;
-    auto drain = [&](int k, int tk) -> bool {  // tile k (tile index tk) of acc2 to nxt
+    auto drain = [&](int k) -> bool {  // tile k of acc2 to nxt
       const int e = k & 1;
       bool ok = mbar_wait(efull + e, (uint32_t)(k >> 1) & 1u);
       ok = ok && (k == 0 || mbar_wait(nfree, (uint32_t)(k - 1) & 1u));  // sN read by its store
@@ -1149,19 +1178,9 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(nwrit);
-      bool stored = true;
-      if (ct == 0) {  // every splitter warp wrote its part: store, then free the slot
-        stored = mbar_wait(nwrit, (uint32_t)k & 1u);
-        if (stored) {
-          tma_store_2d(&tmNxt, tk * TP, 0, sN);
-          bulk_commit();
-          bulk_wait_read();
-          mbar_arrive(nfree);
-        }
-      }
-      return __all_sync(0xffffffffu, stored);
+      return true;
     };
-    int i = 0, tprev = -1;
+    int i = 0;
     for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
       if (__any_sync(0xffffffffu, *vfail)) break;
       const int s = i % CH_NO;
@@ -1201,16 +1220,14 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
         else
           *vfail = 1;
       }
-      if (i > 0 && !drain(i - 1, tprev)) {
+      if (i > 0 && !drain(i - 1)) {
         *vfail = 1;
         break;
       }
-      tprev = t;
     }
-    if (i > 0 && !*vfail && !drain(i - 1, tprev)) *vfail = 1;
-    if (ct == 0) bulk_wait_all();
-  } else {  // epilogue warps 11..18
-    const int qd = warp & 3, hh = (warp - 11) >> 2, px = 32 * qd + lane, et = tid - 352;
+    if (i > 0 && !*vfail && !drain(i - 1)) *vfail = 1;
+  } else if (warp < 19) {  // epilogue warps 11..18
+    const int qd = warp & 3, hh = (warp - 11) >> 2, px = 32 * qd + lane;
     const float ca = sh_coef[0], cp = sh_coef[1];
     int i = 0;
     for (int t = blockIdx.x; t < ntile; t += gridDim.x, ++i) {
@@ -1243,23 +1260,20 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
       if (lane == 0) mbar_arrive(owrit + s);
-      if (et == 0) {  // one store in flight; a slot goes back once stored and split
-        if (mbar_wait(owrit + s, (uint32_t)(i / CH_NO) & 1u)) {
-          tma_store_2d(&tmOut, t * TP, 0, f);
-          bulk_commit();
-          if (i > 0) {
-            bulk_wait_read1();
-            mbar_arrive(oempty + (i - 1) % CH_NO);
-          }
-        } else {
-          *vfail = 1;
-        }
+    }
+  } else if (lane == 0) {  // warp 19: the nxt stores, one tile at a time
+    int k = 0;
+    for (int t = blockIdx.x; t < ntile && !*vfail; t += gridDim.x, ++k) {
+      if (!mbar_wait(nwrit, (uint32_t)k & 1u)) {
+        *vfail = 1;
+        break;
       }
+      tma_store_2d(&tmNxt, t * TP, 0, sN);
+      bulk_commit();
+      bulk_wait_read();
+      mbar_arrive(nfree);
     }
-    if (et == 0) {
-      bulk_wait_all();
-      if (i > 0 && !*vfail) mbar_arrive(oempty + (i - 1) % CH_NO);
-    }
+    bulk_wait_all();
   }
 
   __syncthreads();
@@ -1419,7 +1433,7 @@ int launch_mode3_tc_chain(const void* in, float* out, const float* T_dev, void* 
   TC_TRY(make_tmap_2d(&mn, nxt, 1, P, (size_t)n3, TP, n3));
   const size_t ntile = (P + TP - 1) / TP;
   const unsigned grid = (unsigned)(ntile < (size_t)g_tube_sms ? ntile : (size_t)g_tube_sms);
-  k_tube_chain<<<grid, TT_NT, tube_chain_smem(), st>>>(mi, mp, mo, mn, T_dev, T2_dev, n3, P, hp,
+  k_tube_chain<<<grid, CH_NT, tube_chain_smem(), st>>>(mi, mp, mo, mn, T_dev, T2_dev, n3, P, hp,
                                                        ep, err, after ? *after : LsqrStep{});
   TC_CUDA(cudaGetLastError());
   return TC_OK;
