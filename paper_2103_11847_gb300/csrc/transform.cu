@@ -927,8 +927,9 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
 // Roles (640 threads, one CTA a SM):
 //   warp 0 (one lane): BF16 input by TMA straight into the A1 operand;
 //   warp 2 (one lane): the y ring: the first CH_NO prev loads, then per tile
-//     the TMA store of y and, once the store and the splitters have read the
-//     slot (two arrivals), the prev load CH_NO tiles ahead into it;
+//     the TMA store of y and, once the store and the eight splitter warps
+//     have read the slot (nine arrivals), the prev load CH_NO tiles ahead
+//     into it;
 //   warp 1 (one lane): MMA1 (A1 x T, two passes) into acc1[i & 1], then
 //     MMA2 of the previous tile (A2 x T2, three passes) into acc2;
 //   warps 11..18: epilogue: y from acc1 and prev over prev in the y slot,
@@ -937,8 +938,10 @@ k_tube_tma(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ CUt
 //     A2; drain acc2 of the tile before to BF16 into the nxt slot;
 //   warp 19 (one lane): the TMA store of the nxt slot, which it frees once
 //     the store has read it.
-// Both store threads wait for their store's reads at once: a split or a
-// drain that waited for them instead held up the tile after it (measured).
+// Both store threads wait for their store's reads at once, and each splitter
+// warp hands its part of the y slot back itself: a split or a drain that
+// waited for a store or for the other warps held up the tile after it
+// (measured).
 constexpr int CH_NI = 3, CH_NO = 3, CH_NT = TT_NT + 32;
 constexpr size_t tube_chain_smem() {
   return 1024 + CH_NI * TA_BYTES + CH_NO * TT_SLOT + 2 * TA_BYTES + TT_SLOT / 2 +
@@ -993,7 +996,7 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
     }
     for (int b = 0; b < CH_NO; ++b) {
       mbar_init(ofull + b, 1);
-      mbar_init(oempty + b, 2);
+      mbar_init(oempty + b, 9);
       mbar_init(owrit + b, 8);
     }
     for (int b = 0; b < 2; ++b) {
@@ -1213,12 +1216,9 @@ k_tube_chain(const __grid_constant__ CUtensorMap tmIn, const __grid_constant__ C
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(a2full);
-      if (ct == 0) {  // all eight splitter warps have read this y slot: let it go
-        if (mbar_wait(a2full, (uint32_t)i & 1u))
-          mbar_arrive(oempty + s);
-        else
-          *vfail = 1;
+      if (lane == 0) {
+        mbar_arrive(a2full);
+        mbar_arrive(oempty + s);  // this warp has read its part of the y slot
       }
       if (i > 0 && !drain(i - 1)) {
         *vfail = 1;
